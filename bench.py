@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the Rotne-Prager-Blake Brownian-dynamics hot path on GB300.
+
+One step = one stochastic Adams-Bashforth step (Eq. AB) of a synthetic roller monolayer: forces,
+the fused wall-RPY product M_tt F + M_tr T, Philox noise, Lanczos M^{1/2} W, the RFD drift and the
+update -- every part in the CUDA library, called through its C ABI.
+
+Default workload: the large monolayer, N = 65536 spheres (a = eta = kT = 1, area fraction 0.4,
+z = a + Exp(0.5 a)), gravity -1 z, torque +1 y, soft repulsion U0 = 1, b = 0.1 a, dt = 0.01,
+Lanczos tol 1e-3, float32 pair arithmetic with float64 Lanczos.
+
+Prints one JSON line (rank 0).  value = wall-RPY pair evaluations per second over the whole step
+(N^2 per pair pass; a step makes 3 + m passes: the fused product, m Lanczos products and two RFD
+products), summed over ranks.  --impl reference times the FP64 CPU oracle instead (a bounded
+sample of the same workload on the host cores).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "wall-RPY matvec Gpairs/s; BD steps/s at N=65536; p50/p99 solve latency"
+FLOPS_TT = 126      # algorithmic flops per pair, translation-translation block applied to a vector
+FLOPS_FUSED = 185   # ... plus the translation-rotation block (counts derived in the design doc)
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=65536)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--dt", type=float, default=0.01)
+    ap.add_argument("--delta", type=float, default=None,
+                    help="RFD length; default 1e-6 a (fp64) or 5e-3 a (fp32: delta ~ eps^(1/3) a, Sec. II.A)")
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def workload_name(args):
+    return (f"roller monolayer N={args.N} (phi=0.4, z=a+Exp(0.5a), gravity -1 z, torque +1 y, U0=1, b=0.1a), "
+            f"AB step dt={args.dt}, RFD delta={args.delta}, Lanczos tol={args.tol}, {args.precision} pairs")
+
+
+def oracle_sample(N, seed, seconds):
+    """Time the FP64 oracle's fused product on a row sample of the workload; returns Gpairs/s and info."""
+    import oracle as O
+    from paper_1612_00474_gb300 import inputs
+
+    pos = inputs.monolayer(N, seed=seed)
+    F = np.tile([0.0, 0.0, -1.0], (N, 1))
+    T = np.tile([0.0, 1.0, 0.0], (N, 1))
+    rows = 8
+    t0 = time.perf_counter()
+    O.mobility_apply(pos, F, T, rows=(0, rows))
+    dt = time.perf_counter() - t0
+    rows = int(max(8, min(N, rows * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    O.mobility_apply(pos, F, T, rows=(0, rows))
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return rows * N / dt / 1e9, dict(rows=rows, seconds=dt, cores=cores)
+
+
+def clocks_start(device_index):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                                 "-i", str(device_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except (FileNotFoundError, OSError):
+        return None
+
+
+def clocks_stop(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    N = args.N
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        v, info = oracle_sample(N, args.seed, per_step)
+        if k >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    sample = (f"fused M_tt F + M_tr T of the N={N} monolayer on {info['rows']} target rows x {N} sources "
+              f"per step (FP64 oracle, OpenMP over target rows)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": info["seconds"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args), "N": N},
+        "cpu_baseline": {"value": value, "unit": "Gpairs/s", "cores": info["cores"], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Gpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1612_00474_gb300 import inputs, rpb
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+
+    N = args.N
+    seed = args.seed + rank  # independent replicas, one suspension per rank
+    ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=64)
+    pos0 = inputs.monolayer(N, seed=seed)
+    q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
+    Up = torch.zeros_like(q)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+    kw = dict(dt=args.dt, delta=args.delta, tol=args.tol, max_iter=64)
+
+    step = 0
+    for _ in range(args.warmup):
+        ctx.ab_step(q, Up, step, seed, **kw)
+        step += 1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    clk = clocks_start(local_rank)
+    launches0 = rpb.launch_count()
+    ms, ms_list = [], []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.ab_step(q, Up, step, seed, **kw)
+        e1.record(stream)
+        ms.append((e0, e1))
+        ms_list.append(st["m"])
+        step += 1
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = rpb.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ms]
+    total_s = sum(step_ms) / 1e3
+    pairs = float(N) * N * sum(3 + m for m in ms_list)
+
+    # end to end through the C ABI with host buffers: copy state in, step, copy state out
+    h_q = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+    h_U = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+    h_q.copy_(q)
+    h_U.copy_(Up)
+    e2e_ms, e2e_m = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q.copy_(h_q, non_blocking=True)
+        Up.copy_(h_U, non_blocking=True)
+        st = ctx.ab_step(q, Up, step, seed, **kw)
+        h_q.copy_(q, non_blocking=True)
+        h_U.copy_(Up, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        e2e_m.append(st["m"])
+        step += 1
+    clocks = clocks_stop(clk)
+    e2e_pairs = float(N) * N * sum(3 + m for m in e2e_m)
+    e2e_s = sum(e2e_ms) / 1e3
+
+    # dominant kernel: the translation-translation pair pass (m + 2 of the 3 + m passes per step),
+    # timed live through the C ABI on this stream; and the fused pass for reference
+    def time_product(F, T, reps=3):
+        out = torch.empty_like(q)
+        ctx.mobility_apply(q, F, T, out=out)
+        durs = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.mobility_apply(q, F, T, out=out)
+            b.record(stream)
+            b.synchronize()
+            durs.append(a.elapsed_time(b) / 1e3)
+        return statistics.mean(durs)
+
+    W = ctx.philox_normal(N, seed, 0, 0)
+    Tq = torch.tensor(inputs.to_soa(np.tile([0.0, 1.0, 0.0], (N, 1))), dtype=torch.float64, device="cuda")
+    t_tt = time_product(W, None)
+    t_fused = time_product(W, Tq)
+
+    # max over ranks
+    res = torch.tensor([total_s, e2e_s, pairs, e2e_pairs], dtype=torch.float64, device="cuda")
+    if dist:
+        tmax = res[:2].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        psum = res[2:].clone()
+        dist.all_reduce(psum, op=dist.ReduceOp.SUM)
+        total_s, e2e_s = float(tmax[0]), float(tmax[1])
+        pairs, e2e_pairs = float(psum[0]), float(psum[1])
+        dist.barrier()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, info = oracle_sample(N, args.seed, args.cpu_seconds)
+        cpu = {"value": v, "unit": "Gpairs/s", "cores": info["cores"], "kind": "oracle",
+               "sample": (f"fused M_tt F + M_tr T of the N={N} monolayer on {info['rows']} target rows x {N} "
+                          f"sources ({info['seconds']:.1f} s, FP64 oracle, OpenMP over target rows)")}
+
+    if rank == 0:
+        sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        flops_tt = float(N) * N * FLOPS_TT
+        achieved = flops_tt / t_tt / 1e12
+        value = pairs / total_s / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args), "N": N, "precision": args.precision,
+                       "pair_arith": args.precision, "lanczos_arith": "f64", "parallelism": f"replicas x{world}",
+                       "l2": "256 MB buffer written between timed steps"},
+            "steps_per_s": args.steps * world / total_s,
+            "lanczos_m": ms_list,
+            "step_ms": [round(x, 3) for x in step_ms],
+            "matvec": {"tt_ms": t_tt * 1e3, "fused_ms": t_fused * 1e3,
+                       "tt_gpairs_s": N * N / t_tt / 1e9, "fused_gpairs_s": N * N / t_fused / 1e9},
+            "roofline": {"bound": "alu", "kernel": f"pair_{args.precision[2:]}_kernel (translation-translation)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
+                                       if args.precision == "fp32" else "fp32 lanes (fp64 path: see DESIGN.md)",
+                         "flops_per_pair": FLOPS_TT, "traffic": None},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": "Gpairs/s", "h2d_bytes_per_step": 2 * 3 * N * 8,
+                    "d2h_bytes_per_step": 2 * 3 * N * 8},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.delta is None:
+        args.delta = 1e-6 if args.precision == "fp64" else 5e-3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * rpb.h -- C ABI of the GB300 (sm_103a) Rotne-Prager-Blake Brownian-dynamics library.
+ *
+ * The library computes the hot path of Brownian dynamics of spheres (radius a) above a
+ * no-slip wall at z = 0 (Balboa Usabiaga, Delmotte & Donev, "Brownian dynamics of confined
+ * suspensions of active microrollers", 2017):
+ *   - the matrix-free product U = M_tt F + M_tr T with the wall-corrected Rotne-Prager-
+ *     Yamakawa (Rotne-Prager-Blake) mobility, regularised for wall overlaps (Sec. II.B,
+ *     Sec. III, Appendix A);
+ *   - the Lanczos approximation g_m ~ M^{1/2} W (Sec. II.C);
+ *   - the random-finite-difference drift (Sec. II.A);
+ *   - one stochastic Adams-Bashforth step (Eq. AB) with gravity, soft steric forces and a
+ *     constant torque (Sec. III).
+ *
+ * Conventions for every entry point
+ *   - All vector arguments are DEVICE pointers to float64 arrays in structure-of-arrays layout
+ *     of length 3N: [x_0 .. x_{N-1} | y_0 .. y_{N-1} | z_0 .. z_{N-1}].  Base addresses must be
+ *     8-byte aligned.  The caller owns every input and output buffer; the library never frees
+ *     them.  Output buffers must not alias inputs unless stated.
+ *   - A context owns its scratch memory (allocated once in rpb_create for up to max_N
+ *     particles) and a CUDA stream (the caller's; the library never creates or destroys one).
+ *     Calls are stream-ordered: they enqueue work on the context's stream and may return before
+ *     the results exist, except where a result is returned through a host pointer (iteration
+ *     counts, errors, statistics): those calls synchronise the stream before returning.
+ *     A context must not be used from two host threads at once.
+ *   - Return value: RPB_OK (0) or one of the error codes below; no exception crosses the ABI.
+ *     rpb_last_error() gives a message for the calling thread's most recent failure.
+ *   - Noise: the Philox counter index of a Gaussian is the particle-major index k = 3 i + c
+ *     (the paper orders q = {q_1 .. q_N}, Sec. II), independent of the SoA layout above.
+ */
+#ifndef RPB_H
+#define RPB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RPB_OK 0
+#define RPB_EINVAL 1    /* null pointer, N <= 0 or N > max_N, bad parameter, misaligned pointer */
+#define RPB_ENOMEM 2    /* device allocation failed in rpb_create */
+#define RPB_ECUDA 3     /* a CUDA runtime call or kernel launch failed (message has the CUDA error) */
+#define RPB_ENOCONV 4   /* Lanczos reached max_iter with eps > tol: results are still written */
+
+#define RPB_FP64 0      /* pair arithmetic in float64 */
+#define RPB_FP32 1      /* pair arithmetic in float32 (hi/lo split positions, compensated tile sums,
+                           float64 self terms and cross-chunk sums); Lanczos always float64 */
+
+typedef struct rpb_ctx rpb_ctx;
+
+/* Physical and numerical parameters of a context. */
+typedef struct {
+    double a;        /* sphere radius (> 0) */
+    double eta;      /* viscosity (> 0) */
+    double kT;       /* thermal energy (>= 0) */
+    int precision;   /* RPB_FP64 or RPB_FP32 */
+} rpb_params;
+
+/* Deterministic forcing of Sec. III: gravity -weight z_hat on every sphere, the soft steric
+ * potential of Eq. (soft_potential) between spheres (d = 2a, centre distance) and with the wall
+ * (d = a, height), and the same torque on every sphere. */
+typedef struct {
+    double weight;     /* buoyant weight m g (force along -z) */
+    double U0;         /* steric energy scale */
+    double b;          /* steric range (> 0) */
+    double torque[3];  /* constant torque on every sphere */
+} rpb_force_params;
+
+/* Statistics of one Adams-Bashforth step (valid when rpb_ab_step returns). */
+typedef struct {
+    int lanczos_iters;    /* m: matvecs used for M^{1/2} W */
+    double lanczos_err;   /* eps_m, the paper's relative-difference estimate (-1 if m < 2) */
+    int converged;        /* 1 if eps_m <= tol or the Krylov space became invariant */
+} rpb_step_stats;
+
+/* Create a context for up to max_N spheres and Lanczos runs of up to max_iter iterations.
+ * stream: a cudaStream_t (NULL = legacy default stream).  The device is the current one.
+ * Allocates all scratch now (about (max_iter + 12) * 24 * max_N bytes plus partial-sum
+ * buffers); returns RPB_ENOMEM if that fails.  *ctx is NULL on failure. */
+int rpb_create(rpb_ctx **ctx, const rpb_params *p, int64_t max_N, int max_iter, void *stream);
+
+/* Free the context's scratch (after synchronising its stream).  NULL is accepted. */
+int rpb_destroy(rpb_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+int rpb_set_stream(rpb_ctx *ctx, void *stream);
+
+/* U = M_tt F + M_tr T  (Sec. II.B Eq. mobilityDifferential and mobilityOverlap; Sec. III Eq.
+ * mobilityDifferentialTR; regularisation M = B Mtilde B of Appendix A Eq. effMob, applied to
+ * both blocks).  pos: 3N positions.  F, T: 3N forces and torques; either may be NULL (treated
+ * as zero; both NULL gives U = 0).  U: 3N output, must not alias pos, F or T.  Direct O(N^2)
+ * summation over all ordered pairs including the self terms. */
+int rpb_mobility_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
+                       double *U);
+
+/* g ~ M_tt^{1/2} W by the Lanczos method (Sec. II.C; error estimate eps_m = |g_m - g_{m-1}| /
+ * |g_{m-1}|).  Full reorthogonalisation (classical Gram-Schmidt twice) and the tridiagonal
+ * square root are float64 in both precisions.  Stops at the first m >= 2 with eps_m <= tol; if
+ * tol <= 0, runs exactly max_iter iterations (for comparisons at equal m).  Stops early (exact
+ * result) if the Krylov space becomes invariant.  max_iter must be in [1, context max_iter].
+ * W = 0 gives g = 0, m = 0.  W, g: 3N; g must not alias W or pos.  iters_out, err_out: host
+ * pointers (may be NULL).  Synchronises the stream once per iteration.  Returns RPB_ENOCONV
+ * if tol > 0 and max_iter was reached without convergence (g is still written). */
+int rpb_lanczos_sqrt_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g,
+                           double tol, int max_iter, int *iters_out, double *err_out);
+
+/* Random finite difference (Sec. II.A, last term of Eq. EM/AB without the dt factor):
+ * drift = (kT/delta) [ M_tt(q + delta/2 Wt) Wt - M_tt(q - delta/2 Wt) Wt ], both displaced
+ * configurations regularised anew.  Wt, drift: 3N; delta > 0.  The two matvecs run in the
+ * context's pair precision (use RPB_FP64 when the drift must be accurate: its error is the
+ * matvec error times a/delta). */
+int rpb_rfd_drift(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta,
+                  double *drift);
+
+/* F = -weight z_hat + steric forces (Sec. III, Eq. soft_potential).  Pairs farther apart than
+ * 2a + 50 b are skipped (their force is below 2e-22 U0/b).  A coincident pair exerts nothing. */
+int rpb_forces(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_params *fp, double *F);
+
+/* Standard normals from Philox4x32-10 (Salmon et al., SC'11): key = (seed low, seed high 32
+ * bits), counter = (k / 2, step, stream_id, instance); two 53-bit uniforms in (0, 1] per counter
+ * and the Box-Muller transform give normals k and k + 1.  out: 3N in SoA layout, out[c N + i]
+ * holding index k = 3 i + c.  stream_id 0 is the Lanczos noise W, 1 the RFD noise W~. */
+int rpb_philox_normal(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t stream_id,
+                      uint32_t instance, double *out);
+
+/* One stochastic Adams-Bashforth step (Eq. AB), in place:
+ *   q <- q + dt (3/2 U^n - 1/2 U^{n-1}) + sqrt(2 kT dt) g + dt drift,   U^{n-1} <- U^n,
+ * with U^n = M_tt F(q) + M_tr T, g = lanczos(W), drift = rfd(W~, delta), W and W~ from
+ * rpb_philox_normal(seed, step, 0 / 1).  step == 0 is the first step: U^{n-1} is ignored and
+ * taken equal to U^n (Euler-Maruyama).  pos, U_prev: 3N, in/out.  stats: host pointer (may be
+ * NULL).  Synchronises the stream (Lanczos).  RPB_ENOCONV as for rpb_lanczos_sqrt_apply (the
+ * step is still taken). */
+int rpb_ab_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed,
+                double dt, double delta, double tol, int max_iter, const rpb_force_params *fp,
+                rpb_step_stats *stats);
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+const char *rpb_last_error(void);
+
+/* Total number of CUDA kernel launches this library has enqueued since it was loaded (all contexts,
+ * all threads); for accounting of device work, e.g. launches per step. */
+uint64_t rpb_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPB_H */

@@ -1,0 +1,328 @@
+// api.cu -- the extern "C" entry points declared in include/rpb.h: argument checks, context and
+// scratch management, and the sequence of the Adams-Bashforth step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+
+#include "rpb_internal.cuh"
+
+namespace rpb {
+
+static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(int n)
+{
+    g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+}
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return RPB_OK;
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return RPB_ECUDA;
+}
+
+int fill_torque(rpb_ctx *ctx, int64_t N, const double *t, double *T);
+
+static bool aligned8(const void *p)
+{
+    return ((uintptr_t)p & 7u) == 0;
+}
+
+static int check_ctx_N(rpb_ctx *ctx, int64_t N)
+{
+    if (!ctx) {
+        set_error("null context");
+        return RPB_EINVAL;
+    }
+    if (N <= 0 || N > ctx->max_N) {
+        set_error("N=%lld outside [1, max_N=%lld]", (long long)N, (long long)ctx->max_N);
+        return RPB_EINVAL;
+    }
+    return RPB_OK;
+}
+
+static int check_vec(const void *p, const char *name, bool nullable)
+{
+    if (!p) {
+        if (nullable) return RPB_OK;
+        set_error("%s is null", name);
+        return RPB_EINVAL;
+    }
+    if (!aligned8(p)) {
+        set_error("%s is not 8-byte aligned", name);
+        return RPB_EINVAL;
+    }
+    return RPB_OK;
+}
+
+static void free_ws(Workspace &w)
+{
+    void *dev[] = {w.src, w.partial, w.V, w.w, w.red, w.lz, w.pos_a, w.pos_b,
+                   w.vec_a, w.vec_b, w.vec_c, w.vec_d, w.vec_e, w.vec_f, w.vec_g};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (w.host_status) cudaFreeHost(w.host_status);
+    w = Workspace();
+}
+
+}  // namespace rpb
+
+using namespace rpb;
+
+extern "C" {
+
+const char *rpb_last_error(void)
+{
+    return g_err;
+}
+
+uint64_t rpb_launch_count(void)
+{
+    return (uint64_t)g_launches.load(std::memory_order_relaxed);
+}
+
+int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, void *stream)
+{
+    g_err[0] = 0;
+    if (!out || !p) {
+        set_error("null argument to rpb_create");
+        return RPB_EINVAL;
+    }
+    *out = nullptr;
+    if (!(p->a > 0.0) || !(p->eta > 0.0) || !(p->kT >= 0.0) || (p->precision != RPB_FP64 && p->precision != RPB_FP32)) {
+        set_error("bad parameters (a=%g eta=%g kT=%g precision=%d)", p->a, p->eta, p->kT, p->precision);
+        return RPB_EINVAL;
+    }
+    if (max_N <= 0 || max_N > (int64_t)1 << 28) {
+        set_error("max_N=%lld outside [1, 2^28]", (long long)max_N);
+        return RPB_EINVAL;
+    }
+    if (max_iter < 1 || max_iter > 64) {
+        set_error("max_iter=%d outside [1, 64]", max_iter);
+        return RPB_EINVAL;
+    }
+    rpb_ctx *c = new (std::nothrow) rpb_ctx();
+    if (!c) {
+        set_error("host allocation failed");
+        return RPB_ENOMEM;
+    }
+    c->p = *p;
+    c->max_N = max_N;
+    c->max_iter = max_iter;
+    c->stream = (cudaStream_t)stream;
+    int rc;
+    if ((rc = cuda_fail(cudaGetDevice(&c->device), "cudaGetDevice")) ||
+        (rc = cuda_fail(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device),
+                        "cudaDeviceGetAttribute"))) {
+        delete c;
+        return rc;
+    }
+    Workspace &w = c->ws;
+    const size_t n3 = (size_t)3 * max_N;
+    const size_t vb = n3 * sizeof(double);
+    w.partial_bytes = pair_partial_bytes(max_N, c->num_sms);
+    w.red_elems = lanczos_red_elems(max_iter);
+    struct {
+        void **ptr;
+        size_t bytes;
+    } allocs[] = {
+        {&w.src, (size_t)max_N * sizeof(SrcF64)},
+        {&w.partial, w.partial_bytes},
+        {(void **)&w.V, vb * (size_t)(max_iter + 1)},
+        {(void **)&w.w, vb},
+        {(void **)&w.red, w.red_elems * sizeof(double)},
+        {(void **)&w.lz, lanczos_state_elems(max_iter) * sizeof(double)},
+        {(void **)&w.pos_a, vb},
+        {(void **)&w.pos_b, vb},
+        {(void **)&w.vec_a, vb},
+        {(void **)&w.vec_b, vb},
+        {(void **)&w.vec_c, vb},
+        {(void **)&w.vec_d, vb},
+        {(void **)&w.vec_e, vb},
+        {(void **)&w.vec_f, vb},
+        {(void **)&w.vec_g, vb},
+    };
+    for (auto &a : allocs) {
+        cudaError_t e = cudaMalloc(a.ptr, a.bytes);
+        if (e != cudaSuccess) {
+            set_error("cudaMalloc of %zu bytes failed: %s", a.bytes, cudaGetErrorString(e));
+            cudaGetLastError();
+            free_ws(w);
+            delete c;
+            return RPB_ENOMEM;
+        }
+    }
+    if (cudaMallocHost((void **)&w.host_status, 8 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("pinned host allocation failed");
+        free_ws(w);
+        delete c;
+        return RPB_ENOMEM;
+    }
+    if ((rc = cuda_fail(cudaMemsetAsync(w.lz, 0, lanczos_state_elems(max_iter) * sizeof(double), c->stream),
+                        "memset"))) {
+        free_ws(w);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return RPB_OK;
+}
+
+int rpb_destroy(rpb_ctx *ctx)
+{
+    if (!ctx) return RPB_OK;
+    g_err[0] = 0;
+    int rc = cuda_fail(cudaStreamSynchronize(ctx->stream), "rpb_destroy sync");
+    free_ws(ctx->ws);
+    delete ctx;
+    return rc;
+}
+
+int rpb_set_stream(rpb_ctx *ctx, void *stream)
+{
+    if (!ctx) {
+        set_error("null context");
+        return RPB_EINVAL;
+    }
+    ctx->stream = (cudaStream_t)stream;
+    return RPB_OK;
+}
+
+int rpb_mobility_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T, double *U)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(F, "F", true)) ||
+        (rc = check_vec(T, "T", true)) || (rc = check_vec(U, "U", false)))
+        return rc;
+    if (U == pos || U == F || U == T) {
+        set_error("U aliases an input");
+        return RPB_EINVAL;
+    }
+    if (!F && !T) return cuda_fail(cudaMemsetAsync(U, 0, 3 * N * sizeof(double), ctx->stream), "memset U");
+    return mobility_apply_impl(ctx, N, pos, F, T, U);
+}
+
+int rpb_lanczos_sqrt_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol,
+                           int max_iter, int *iters_out, double *err_out)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(W, "W", false)) ||
+        (rc = check_vec(g, "g", false)))
+        return rc;
+    if (max_iter < 1 || max_iter > ctx->max_iter) {
+        set_error("max_iter=%d outside [1, %d]", max_iter, ctx->max_iter);
+        return RPB_EINVAL;
+    }
+    if (g == W || g == pos) {
+        set_error("g aliases an input");
+        return RPB_EINVAL;
+    }
+    return lanczos_impl(ctx, N, pos, W, g, tol, max_iter, iters_out, err_out, nullptr);
+}
+
+int rpb_rfd_drift(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(Wt, "Wt", false)) ||
+        (rc = check_vec(drift, "drift", false)))
+        return rc;
+    if (!(delta > 0.0)) {
+        set_error("delta must be > 0");
+        return RPB_EINVAL;
+    }
+    if (drift == Wt || drift == pos) {
+        set_error("drift aliases an input");
+        return RPB_EINVAL;
+    }
+    return rfd_impl(ctx, N, pos, Wt, delta, drift);
+}
+
+int rpb_forces(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_params *fp, double *F)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(F, "F", false)))
+        return rc;
+    if (!fp || !(fp->b > 0.0)) {
+        set_error("force parameters missing or b <= 0");
+        return RPB_EINVAL;
+    }
+    if (F == pos) {
+        set_error("F aliases pos");
+        return RPB_EINVAL;
+    }
+    return forces_impl(ctx, N, pos, fp, F);
+}
+
+int rpb_philox_normal(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t stream_id, uint32_t instance,
+                      double *out)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(out, "out", false))) return rc;
+    return philox_impl(ctx, N, seed, step, stream_id, instance, out);
+}
+
+int rpb_ab_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed, double dt,
+                double delta, double tol, int max_iter, const rpb_force_params *fp, rpb_step_stats *stats)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(U_prev, "U_prev", false)))
+        return rc;
+    if (!fp || !(fp->b > 0.0) || !(dt > 0.0) || !(delta > 0.0) || step < 0 || step > 0xffffffffLL) {
+        set_error("bad step arguments (dt=%g delta=%g step=%lld)", dt, delta, (long long)step);
+        return RPB_EINVAL;
+    }
+    if (max_iter < 1 || max_iter > ctx->max_iter) {
+        set_error("max_iter=%d outside [1, %d]", max_iter, ctx->max_iter);
+        return RPB_EINVAL;
+    }
+    if (U_prev == pos) {
+        set_error("U_prev aliases pos");
+        return RPB_EINVAL;
+    }
+    Workspace &w = ctx->ws;
+    double *F = w.vec_a, *T = w.vec_b, *Un = w.vec_c, *W = w.vec_d, *Wt = w.vec_e, *g = w.vec_f, *drift = w.vec_g;
+    if ((rc = forces_impl(ctx, N, pos, fp, F))) return rc;
+    if ((rc = fill_torque(ctx, N, fp->torque, T))) return rc;
+    if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
+    if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 0u, 0u, W))) return rc;
+    if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 1u, 0u, Wt))) return rc;
+    int iters = 0, conv = 0;
+    double err = -1.0;
+    const int lrc = lanczos_impl(ctx, N, pos, W, g, tol, max_iter, &iters, &err, &conv);
+    if (lrc != RPB_OK && lrc != RPB_ENOCONV) return lrc;
+    if ((rc = rfd_impl(ctx, N, pos, Wt, delta, drift))) return rc;
+    const double noise = sqrt(2.0 * ctx->p.kT * dt);
+    if ((rc = ab_update_impl(ctx, N, pos, U_prev, Un, g, drift, dt, noise, step == 0 ? 1 : 0))) return rc;
+    if (stats) {
+        stats->lanczos_iters = iters;
+        stats->lanczos_err = err;
+        stats->converged = conv;
+    }
+    if (lrc == RPB_ENOCONV) {
+        set_error("lanczos: no convergence in %d iterations (eps=%g, tol=%g)", iters, err, tol);
+        return RPB_ENOCONV;
+    }
+    return RPB_OK;
+}
+
+}  // extern "C"

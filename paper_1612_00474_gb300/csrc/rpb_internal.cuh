@@ -1,0 +1,124 @@
+// rpb_internal.cuh -- shared declarations of the CUDA translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rpb.h"
+
+namespace rpb {
+
+constexpr int kTile = 128;        // sources staged per shared-memory tile = targets per block
+constexpr int kPairThreads = 128; // threads per pair-kernel block (one target each)
+constexpr double kPi = 3.14159265358979323846;
+
+// Packed source records, built once per product from the float64 SoA inputs.
+// s_j = H0(z_j / a) is folded into F and T; z is the clamped height max(z, a) (Appendix A).
+struct alignas(16) SrcF32 {
+    float4 p;  // x_hi, y_hi, x_lo, y_lo   (x = x_hi + x_lo exactly to ~2^-48 relative)
+    float4 f;  // z~, s Fx, s Fy, s Fz
+    float4 t;  // s Tx, s Ty, s Tz, 0
+};
+struct alignas(16) SrcF64 {
+    double2 p;  // x, y
+    double2 q;  // z~, s Fx
+    double2 r;  // s Fy, s Fz
+    double2 s;  // s Tx, s Ty
+    double2 u;  // s Tz, 0
+};
+
+// Geometry constants of the pair formula, in units where velocities carry 1/(8 pi eta).
+template <typename R>
+struct PairConsts {
+    R two_a;        // 2a
+    R two_a2;       // 2a^2
+    R two_3_a2;     // 2a^2/3
+    R a2;           // a^2
+    R near_c1;      // 4/(3a)          (mu0 in units of 1/(8 pi eta))
+    R near_r;       // 9/(32a)
+    R near_c2;      // 1/(8 a^2)
+    R near_tr;      // 1/(2 a^3)
+    R near_tr_r;    // 3/(8a)
+};
+
+template <typename R>
+inline PairConsts<R> make_consts(double a)
+{
+    PairConsts<R> c;
+    c.two_a = (R)(2.0 * a);
+    c.two_a2 = (R)(2.0 * a * a);
+    c.two_3_a2 = (R)(2.0 * a * a / 3.0);
+    c.a2 = (R)(a * a);
+    c.near_c1 = (R)(4.0 / (3.0 * a));
+    c.near_r = (R)(9.0 / (32.0 * a));
+    c.near_c2 = (R)(1.0 / (8.0 * a * a));
+    c.near_tr = (R)(1.0 / (2.0 * a * a * a));
+    c.near_tr_r = (R)(3.0 / (8.0 * a));
+    return c;
+}
+
+// Scratch owned by a context.
+struct Workspace {
+    void *src = nullptr;          // packed sources, max_N records (SrcF64 size)
+    void *partial = nullptr;      // pair-kernel partial sums
+    size_t partial_bytes = 0;
+    double *V = nullptr;          // Lanczos basis, (max_iter + 1) x 3 max_N
+    double *w = nullptr;          // Lanczos work vector, 3 max_N
+    double *red = nullptr;        // reduction partials
+    size_t red_elems = 0;
+    double *lz = nullptr;         // Lanczos small state (alpha, beta, y, y_prev, coefficients, status)
+    double *pos_a = nullptr;      // displaced positions (RFD), 3 max_N
+    double *pos_b = nullptr;
+    double *vec_a = nullptr;      // 3 max_N scratch vectors for the AB step
+    double *vec_b = nullptr;
+    double *vec_c = nullptr;
+    double *vec_d = nullptr;
+    double *vec_e = nullptr;
+    double *vec_f = nullptr;
+    double *vec_g = nullptr;
+    double *host_status = nullptr; // pinned host copy of the Lanczos status word
+};
+
+}  // namespace rpb
+
+struct rpb_ctx {
+    rpb_params p;
+    int64_t max_N;
+    int max_iter;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    rpb::Workspace ws;
+};
+
+namespace rpb {
+
+// Error reporting (thread-local message).
+void set_error(const char *fmt, ...);
+// Count kernel launches enqueued by the library (reported by rpb_launch_count).
+void count_launches(int n);
+int cuda_fail(cudaError_t e, const char *what);
+
+// Pair product: U = M_tt F + M_tr T with the context's precision.  F or T may be null.
+// All pointers device, SoA float64.  Enqueued on ctx->stream.
+int mobility_apply_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
+                        double *U);
+
+// Number of column splits and chunk length the pair kernel uses for N targets.
+void pair_grid(int64_t N, int num_sms, int precision, int *splits, int64_t *chunk);
+size_t pair_partial_bytes(int64_t max_N, int num_sms);
+
+int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_params *fp, double *F);
+int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t stream_id, uint32_t instance,
+                double *out);
+int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol, int max_iter,
+                 int *iters_out, double *err_out, int *converged_out);
+int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift);
+int ab_update_impl(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, const double *Un, const double *g,
+                   const double *drift, double dt, double noise_scale, int first);
+
+// Sizes of the Lanczos small-state block (doubles) for max_iter.
+size_t lanczos_state_elems(int max_iter);
+size_t lanczos_red_elems(int max_iter);
+
+}  // namespace rpb

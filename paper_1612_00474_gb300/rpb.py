@@ -1,0 +1,230 @@
+"""Python binding of the C ABI in include/rpb.h (argument marshalling only).
+
+Every computation runs in the CUDA library librpb.so; this module only checks tensor
+shapes/dtypes/devices, passes raw device pointers and the current torch CUDA stream, and turns
+error codes into exceptions.  There is no CPU fallback: if the library cannot be built or loaded,
+load() raises.
+
+Vectors are torch float64 CUDA tensors of shape (3N,) in structure-of-arrays layout
+[x_0..x_{N-1} | y_0..y_{N-1} | z_0..z_{N-1}] (use inputs.to_soa / from_soa to convert from the
+particle-major (N, 3) arrays of the paper's notation).
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+RPB_OK, RPB_EINVAL, RPB_ENOMEM, RPB_ECUDA, RPB_ENOCONV = 0, 1, 2, 3, 4
+RPB_FP64, RPB_FP32 = 0, 1
+PRECISIONS = {"fp64": RPB_FP64, "fp32": RPB_FP32}
+
+# Every entry point the header declares (checked by the tests against include/rpb.h).
+EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", "rpb_lanczos_sqrt_apply",
+           "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
+           "rpb_launch_count")
+
+
+class RpbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rpb error {code}: {msg}")
+        self.code = code
+
+
+class NoConvergence(RpbError):
+    pass
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("eta", ctypes.c_double), ("kT", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class ForceParams(ctypes.Structure):
+    _fields_ = [("weight", ctypes.c_double), ("U0", ctypes.c_double), ("b", ctypes.c_double),
+                ("torque", ctypes.c_double * 3)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("lanczos_iters", ctypes.c_int), ("lanczos_err", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load librpb.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; build it with paper_1612_00474_gb300/build.py")
+    L = ctypes.CDLL(path)
+    vp, i64, i32, d, u32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_uint32, \
+        ctypes.c_uint64
+    L.rpb_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), i64, i32, vp]
+    L.rpb_destroy.argtypes = [vp]
+    L.rpb_set_stream.argtypes = [vp, vp]
+    L.rpb_mobility_apply.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.rpb_lanczos_sqrt_apply.argtypes = [vp, i64, vp, vp, vp, d, i32, ctypes.POINTER(i32), ctypes.POINTER(d)]
+    L.rpb_rfd_drift.argtypes = [vp, i64, vp, vp, d, vp]
+    L.rpb_forces.argtypes = [vp, i64, vp, ctypes.POINTER(ForceParams), vp]
+    L.rpb_philox_normal.argtypes = [vp, i64, u64, u32, u32, u32, vp]
+    L.rpb_ab_step.argtypes = [vp, i64, vp, vp, i64, u64, d, d, d, i32, ctypes.POINTER(ForceParams),
+                              ctypes.POINTER(StepStats)]
+    L.rpb_last_error.argtypes = []
+    L.rpb_last_error.restype = ctypes.c_char_p
+    L.rpb_launch_count.argtypes = []
+    L.rpb_launch_count.restype = ctypes.c_uint64
+    for name in EXPORTS:
+        if name not in ("rpb_last_error", "rpb_launch_count"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def last_error():
+    return load().rpb_last_error().decode()
+
+
+def launch_count():
+    """Kernel launches the library has enqueued so far (rpb_launch_count)."""
+    return int(load().rpb_launch_count())
+
+
+def _check(rc):
+    if rc == RPB_OK:
+        return
+    msg = last_error()
+    if rc == RPB_ENOCONV:
+        raise NoConvergence(rc, msg)
+    raise RpbError(rc, msg)
+
+
+def _ptr(t, n=None, name="tensor"):
+    """Device pointer of a contiguous float64 CUDA tensor (None passes through as NULL)."""
+    if t is None:
+        return None
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _force_params(weight, U0, b, torque):
+    fp = ForceParams()
+    fp.weight, fp.U0, fp.b = float(weight), float(U0), float(b)
+    for k in range(3):
+        fp.torque[k] = float(torque[k])
+    return fp
+
+
+class Context:
+    """A library context (rpb_create) bound to the current CUDA device."""
+
+    def __init__(self, max_N, a=1.0, eta=1.0, kT=1.0, precision="fp64", max_iter=64):
+        L = load()
+        p = Params(float(a), float(eta), float(kT), PRECISIONS[precision])
+        h = ctypes.c_void_p()
+        _check(L.rpb_create(ctypes.byref(h), ctypes.byref(p), int(max_N), int(max_iter), _stream()))
+        self._h = h
+        self.max_N = int(max_N)
+        self.max_iter = int(max_iter)
+        self.params = dict(a=a, eta=eta, kT=kT, precision=precision)
+
+    def close(self):
+        if self._h:
+            _check(load().rpb_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self):
+        _check(load().rpb_set_stream(self._h, _stream()))
+
+    @staticmethod
+    def _empty(n, like):
+        import torch
+
+        return torch.empty(n, dtype=torch.float64, device=like.device)
+
+    def mobility_apply(self, pos, F=None, T=None, out=None):
+        """U = M_tt F + M_tr T (rpb_mobility_apply)."""
+        n = pos.numel()
+        out = self._empty(n, pos) if out is None else out
+        self._bind_stream()
+        _check(load().rpb_mobility_apply(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(F, n, "F"), _ptr(T, n, "T"),
+                                         _ptr(out, n, "U")))
+        return out
+
+    def lanczos_sqrt_apply(self, pos, W, tol=1e-3, max_iter=None, out=None, raise_on_noconv=True):
+        """g ~ M^{1/2} W (rpb_lanczos_sqrt_apply); returns (g, iterations, eps, converged)."""
+        n = pos.numel()
+        out = self._empty(n, pos) if out is None else out
+        it = ctypes.c_int(0)
+        err = ctypes.c_double(0.0)
+        self._bind_stream()
+        rc = load().rpb_lanczos_sqrt_apply(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(W, n, "W"), _ptr(out, n, "g"),
+                                           float(tol), int(max_iter or self.max_iter), ctypes.byref(it),
+                                           ctypes.byref(err))
+        if rc == RPB_ENOCONV and not raise_on_noconv:
+            return out, it.value, err.value, False
+        _check(rc)
+        return out, it.value, err.value, True
+
+    def rfd_drift(self, pos, Wt, delta=1e-6, out=None):
+        n = pos.numel()
+        out = self._empty(n, pos) if out is None else out
+        self._bind_stream()
+        _check(load().rpb_rfd_drift(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(Wt, n, "Wt"), float(delta),
+                                    _ptr(out, n, "drift")))
+        return out
+
+    def forces(self, pos, weight=1.0, U0=1.0, b=0.1, torque=(0.0, 1.0, 0.0), out=None):
+        n = pos.numel()
+        out = self._empty(n, pos) if out is None else out
+        fp = _force_params(weight, U0, b, torque)
+        self._bind_stream()
+        _check(load().rpb_forces(self._h, n // 3, _ptr(pos, n, "pos"), ctypes.byref(fp), _ptr(out, n, "F")))
+        return out
+
+    def philox_normal(self, N, seed, step, stream_id, instance=0, out=None, device="cuda"):
+        import torch
+
+        out = torch.empty(3 * N, dtype=torch.float64, device=device) if out is None else out
+        self._bind_stream()
+        _check(load().rpb_philox_normal(self._h, int(N), int(seed), int(step), int(stream_id), int(instance),
+                                        _ptr(out, 3 * N, "out")))
+        return out
+
+    def ab_step(self, pos, U_prev, step, seed, dt=0.01, delta=1e-6, tol=1e-3, max_iter=None, weight=1.0, U0=1.0,
+                b=0.1, torque=(0.0, 1.0, 0.0), raise_on_noconv=True):
+        """One stochastic Adams-Bashforth step in place (rpb_ab_step); returns the step statistics."""
+        n = pos.numel()
+        fp = _force_params(weight, U0, b, torque)
+        stats = StepStats()
+        self._bind_stream()
+        rc = load().rpb_ab_step(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(U_prev, n, "U_prev"), int(step),
+                                int(seed), float(dt), float(delta), float(tol), int(max_iter or self.max_iter),
+                                ctypes.byref(fp), ctypes.byref(stats))
+        if not (rc == RPB_ENOCONV and not raise_on_noconv):
+            _check(rc)
+        return dict(m=stats.lanczos_iters, eps=stats.lanczos_err, converged=bool(stats.converged))
