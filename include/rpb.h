@@ -142,6 +142,32 @@ const char *rpb_last_error(void);
  * all threads); for accounting of device work, e.g. launches per step. */
 uint64_t rpb_launch_count(void);
 
+/* Largest N accepted by rpb_mobility_apply_noalloc. */
+#define RPB_NOALLOC_MAX_N 16384
+
+/* U = M_tt F + M_tr T like rpb_mobility_apply, but without a context and without allocating.
+ * The paper has no counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc -- for example a host application that hands out all device memory from its own
+ * pool and allows no other allocation, or code running where the device-wide synchronisation an
+ * allocation may cause is not acceptable.  rpb_create allocates a context's scratch, so such
+ * callers cannot use rpb_mobility_apply.
+ *   - Scratch: a fixed array of about 7.6 MB in the library's device image (packed sources for
+ *     RPB_NOALLOC_MAX_N spheres plus the partial sums), present on every GPU that loads the
+ *     library until the process exits.  The caller still passes pos, F, T and U (device pointers,
+ *     SoA, as for rpb_mobility_apply); F or T may be NULL.
+ *   - p: a, eta and precision are used (kT is ignored).  stream: a cudaStream_t (NULL = legacy
+ *     default stream), on the current device.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents behind; each call
+ *     overwrites all of the scratch it reads, so nothing has to be cleared in between.  Calls
+ *     whose kernels may overlap on the GPU (different streams, or different host threads) race on
+ *     the array: order them on one stream or synchronise between them.
+ *   - Errors: RPB_EINVAL for N <= 0 or N > RPB_NOALLOC_MAX_N (message states the limit), bad
+ *     parameters, null pos or U, misaligned or aliasing pointers; RPB_ECUDA for CUDA failures. */
+int rpb_mobility_apply_noalloc(int64_t N, const double *pos, const double *F, const double *T, double *U,
+                               const rpb_params *p, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

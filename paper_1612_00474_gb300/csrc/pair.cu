@@ -455,3 +455,119 @@ int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_para
 }
 
 }  // namespace rpb
+
+// ------------------------------------------------------------------ allocation-free product
+// rpb_mobility_apply_noalloc: the same pack / pair / reduce kernels as rpb_mobility_apply, with their
+// scratch (packed sources, then the per-chunk partial sums) in a fixed array of the library's device
+// image instead of a context's cudaMalloc'd workspace.  The array is created with the module on
+// every device that loads the library and lives until the process exits.
+#include <mutex>
+
+namespace rpb {
+
+constexpr int64_t kNoAllocSrcBytes = (int64_t)RPB_NOALLOC_MAX_N * (int64_t)sizeof(SrcF64);
+constexpr int64_t kNoAllocPartialElems = (int64_t)16 * 3 * RPB_NOALLOC_MAX_N;  // 16 chunks at the maximum N
+constexpr int64_t kNoAllocBytes = kNoAllocSrcBytes + kNoAllocPartialElems * (int64_t)sizeof(double);
+static_assert(kNoAllocSrcBytes % 256 == 0, "partials must start 256-byte aligned");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[kNoAllocMaxDevices];
+static int g_noalloc_sms[kNoAllocMaxDevices];
+
+// Device address of the scratch array on the current device (looked up once per device).
+static int noalloc_setup(void **ptr, int *sms)
+{
+    int dev = 0;
+    int rc;
+    if ((rc = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("device ordinal %d outside [0, %d)", dev, kNoAllocMaxDevices);
+        return RPB_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if ((rc = cuda_fail(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)"))) return rc;
+        int n = 0;
+        if ((rc = cuda_fail(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev), "SM count"))) return rc;
+        g_noalloc_sms[dev] = n;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
+    return RPB_OK;
+}
+
+}  // namespace rpb
+
+extern "C" int rpb_mobility_apply_noalloc(int64_t N64, const double *pos, const double *F, const double *T, double *U,
+                                          const rpb_params *p, void *stream)
+{
+    using namespace rpb;
+    if (!p || !(p->a > 0.0) || !(p->eta > 0.0) || (p->precision != RPB_FP64 && p->precision != RPB_FP32)) {
+        set_error("rpb_mobility_apply_noalloc: missing or bad parameters");
+        return RPB_EINVAL;
+    }
+    if (N64 <= 0 || N64 > RPB_NOALLOC_MAX_N) {
+        set_error("rpb_mobility_apply_noalloc: N=%lld outside [1, %d] (the size of its fixed scratch)", (long long)N64,
+                  RPB_NOALLOC_MAX_N);
+        return RPB_EINVAL;
+    }
+    const void *ptrs[] = {pos, F, T, U};
+    for (const void *q : ptrs)
+        if (q && ((uintptr_t)q & 7u)) {
+            set_error("rpb_mobility_apply_noalloc: pointer not 8-byte aligned");
+            return RPB_EINVAL;
+        }
+    if (!pos || !U) {
+        set_error("rpb_mobility_apply_noalloc: pos and U must not be null");
+        return RPB_EINVAL;
+    }
+    if (U == pos || U == F || U == T) {
+        set_error("rpb_mobility_apply_noalloc: U aliases an input");
+        return RPB_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = (int)N64;
+    if (!F && !T) return cuda_fail(cudaMemsetAsync(U, 0, 3 * N64 * sizeof(double), st), "memset U");
+    void *base = nullptr;
+    int sms = 0;
+    int rc;
+    if ((rc = noalloc_setup(&base, &sms))) return rc;
+    int splits;
+    int64_t chunk;
+    pair_grid(N64, sms, p->precision, &splits, &chunk);
+    const int64_t max_splits = kNoAllocPartialElems / (3 * N64);
+    if (splits > max_splits) {
+        chunk = ((N64 + max_splits - 1) / max_splits + kTile - 1) / kTile * kTile;
+        splits = (int)((N64 + chunk - 1) / chunk);
+    }
+    double *part = (double *)((unsigned char *)base + kNoAllocSrcBytes);
+    const int pb = 256;
+    const dim3 grid((unsigned)((N + kPairThreads - 1) / kPairThreads), (unsigned)splits);
+    const double a = p->a;
+    if (p->precision == RPB_FP32) {
+        SrcF32 *src = (SrcF32 *)base;
+        pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, src);
+        const PairConsts<float> c = make_consts<float>(a);
+        if (T)
+            pair_f32_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+        else
+            pair_f32_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+    } else {
+        SrcF64 *src = (SrcF64 *)base;
+        pack_f64_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, src);
+        const PairConsts<double> c = make_consts<double>(a);
+        if (T)
+            pair_f64_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+        else
+            pair_f64_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+    }
+    pair_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(part, splits, N, pos, F, T, make_consts<double>(a), a,
+                                                          1.0 / (8.0 * kPi * p->eta), U);
+    count_launches(3);
+    return cuda_fail(cudaGetLastError(), "rpb_mobility_apply_noalloc kernels");
+}

@@ -21,7 +21,8 @@ PRECISIONS = {"fp64": RPB_FP64, "fp32": RPB_FP32}
 # Every entry point the header declares (checked by the tests against include/rpb.h).
 EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", "rpb_lanczos_sqrt_apply",
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
-           "rpb_launch_count")
+           "rpb_launch_count", "rpb_mobility_apply_noalloc")
+NOALLOC_MAX_N = 16384
 
 
 class RpbError(RuntimeError):
@@ -81,6 +82,7 @@ def load(build_if_missing=True):
     L.rpb_last_error.restype = ctypes.c_char_p
     L.rpb_launch_count.argtypes = []
     L.rpb_launch_count.restype = ctypes.c_uint64
+    L.rpb_mobility_apply_noalloc.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp]
     for name in EXPORTS:
         if name not in ("rpb_last_error", "rpb_launch_count"):
             getattr(L, name).restype = ctypes.c_int
@@ -95,6 +97,20 @@ def last_error():
 def launch_count():
     """Kernel launches the library has enqueued so far (rpb_launch_count)."""
     return int(load().rpb_launch_count())
+
+
+def mobility_apply_noalloc(pos, F=None, T=None, a=1.0, eta=1.0, precision="fp64", out=None):
+    """U = M_tt F + M_tr T without a context and without any allocation in the library
+    (rpb_mobility_apply_noalloc), for callers that cannot allocate device memory; N <= NOALLOC_MAX_N.
+    out must be given by such callers (it is allocated here only as a convenience)."""
+    import torch
+
+    n = pos.numel()
+    out = torch.empty(n, dtype=torch.float64, device=pos.device) if out is None else out
+    p = Params(float(a), float(eta), 0.0, PRECISIONS[precision])
+    _check(load().rpb_mobility_apply_noalloc(n // 3, _ptr(pos, n, "pos"), _ptr(F, n, "F"), _ptr(T, n, "T"),
+                                             _ptr(out, n, "U"), ctypes.byref(p), _stream()))
+    return out
 
 
 def _check(rc):
