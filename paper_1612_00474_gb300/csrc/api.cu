@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <atomic>
 #include <new>
@@ -123,6 +124,10 @@ int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, 
     c->max_N = max_N;
     c->max_iter = max_iter;
     c->stream = (cudaStream_t)stream;
+    {
+        const char *v = getenv("RPB_FP32_PAIR");
+        c->fp32_variant = (v && strcmp(v, "scalar") == 0) ? 0 : 1;
+    }
     int rc;
     if ((rc = cuda_fail(cudaGetDevice(&c->device), "cudaGetDevice")) ||
         (rc = cuda_fail(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device),

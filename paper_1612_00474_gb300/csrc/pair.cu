@@ -103,6 +103,213 @@ __device__ __forceinline__ void pair_velocity(R rx, R ry, R zi, R zj, R Fx, R Fy
     }
 }
 
+// Float32 form of pair_velocity for the hot loop, hand-fused and algebraically rearranged (same
+// mathematics): the wall terms use the unnormalised image vector R, the free-space c1 and wall A/|R|
+// share one multiply-add into F, r.F and R.F share their in-plane part, the free-space rotlet
+// c_t T x r and the wall's -|R|^-3 T x R share their z component, and the overlap branch (r < 2a,
+// rare) is evaluated only when some lane of the warp needs it.  Must be called by all 32 lanes.
+template <bool TORQUE>
+__device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, float zj, float Fx, float Fy,
+                                                  float Fz, float Tx, float Ty, float Tz, const PairConsts<float> &c,
+                                                  float &ux, float &uy, float &uz)
+{
+    // ---- free-space RPY, far branch by default
+    const float rz = zi - zj;
+    const float rho2 = fmaf(rx, rx, ry * ry);
+    const float r2 = fmaf(rz, rz, rho2);
+    const float inv_r = rsqrtf(r2);
+    const float inv_r2 = inv_r * inv_r;
+    const float ir3 = inv_r * inv_r2;
+    float c1 = inv_r * fmaf(c.two_3_a2, inv_r2, 1.f);
+    float c2 = ir3 * fmaf(-c.two_a2, inv_r2, 1.f);
+    float ct = ir3;
+    const bool near = r2 < c.four_a2;
+    if (__any_sync(0xffffffffu, near)) {
+        if (near) {  // overlap branch; r = 0 (coincident spheres) gives the self form
+            const float r = r2 > 0.f ? r2 * inv_r : 0.f;
+            const float ir = r2 > 0.f ? inv_r : 0.f;
+            c1 = c.near_c1 * fmaf(-c.near_r, r, 1.f);
+            c2 = c.near_c2 * ir;
+            ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
+        }
+    }
+    // ---- wall correction
+    const float Rz = zi + zj;
+    const float invR = rsqrtf(fmaf(Rz, Rz, rho2));
+    const float invR2 = invR * invR;
+    const float ez = Rz * invR;
+    const float t = zj * invR;
+    const float s = c.a2 * invR2;
+    const float ez2 = ez * ez, t2 = t * t, et = ez * t, s2 = s * s;
+    const float d = t2 - et;
+    const float A = fmaf(s2, fmaf(-10.f / 3.f, ez2, 2.f / 3.f), fmaf(s, fmaf(2.f, ez2, -2.f / 3.f), fmaf(2.f, d, -1.f)));
+    const float B = fmaf(s2, fmaf(70.f / 3.f, ez2, -10.f / 3.f), fmaf(s, fmaf(-10.f, ez2, 2.f), fmaf(-6.f, d, -1.f)));
+    const float C =
+        fmaf(ez, fmaf(s2, fmaf(-140.f / 3.f, ez2, 40.f / 3.f), s * fmaf(20.f, ez2, -4.f)), t * fmaf(12.f, et - ez2, 2.f));
+    const float D = fmaf(-20.f / 3.f, s2 * ez, t + t);
+    const float E = fmaf(s2, fmaf(20.f, ez2, -8.f / 3.f), -4.f * fmaf(s, ez2, t2));
+    const float pF = fmaf(rx, Fx, ry * Fy);
+    const float q = fmaf(Rz, Fz, pF) * invR;          // e.F
+    const float k2 = c2 * fmaf(rz, Fz, pF);           // free-space c2 (r.F)
+    const float ke = fmaf(B, q, C * Fz) * invR2;      // multiplies R
+    const float kz = fmaf(D, q, E * Fz) * invR;       // multiplies z_hat
+    const float cF = fmaf(A, invR, c1);               // multiplies F
+    const float kk = k2 + ke;
+    ux = fmaf(cF, Fx, fmaf(kk, rx, ux));
+    uy = fmaf(cF, Fy, fmaf(kk, ry, uy));
+    uz = fmaf(cF, Fz, fmaf(k2, rz, fmaf(ke, Rz, uz + kz)));
+    if (TORQUE) {
+        // c_t T x r - p T x R + |R|^-2 [c_z T x z + (c_e e + 2 s z) (z x e).T],  p = |R|^-3
+        const float p = invR2 * invR;
+        const float dcp = ct - p;
+        const float m1 = fmaf(ct, rz, -(p * Rz));
+        const float tz3 = fmaf(Tx, ry, -(Ty * rx));   // (T x r)_z = (T x R)_z
+        const float se = s * ez;
+        const float m2 = fmaf(t + se, invR2 + invR2, m1);
+        const float ce = fmaf(-10.f, se, 6.f * (ez - t));
+        const float w = -tz3 * invR;                   // (z x e).T
+        const float cw = ce * w * p;                   // multiplies R
+        const float dTz = dcp * Tz;
+        ux = fmaf(Ty, m2, fmaf(-dTz, ry, fmaf(cw, rx, ux)));
+        uy = fmaf(-Tx, m2, fmaf(dTz, rx, fmaf(cw, ry, uy)));
+        uz = fmaf(dcp, tz3, fmaf(cw, Rz, fmaf((s + s) * invR2, w, uz)));
+    }
+}
+
+// ---- two pairs per lane with packed float32x2 arithmetic (FFMA2/FMUL2/FADD2 on sm_100+)
+// The same formulation as pair_velocity_f32, evaluated for two sources at once: every quantity is a
+// float2 whose halves belong to two independent pairs, so one packed instruction does the work of
+// two scalar ones.  Constants are passed as float2 pairs in the kernel parameters.
+struct X2Consts {
+    float2 one, two_3_a2, m_two_a2, a2;
+    float2 m10_3, c2_3, two, m2_3, m1, c70_3, m10, m6, m140_3, c40_3, c20, m4, c12, m20_3, m8_3, c6;
+    float four_a2, near_c1, near_r, near_c2, near_tr, near_tr_r;
+};
+
+inline X2Consts make_x2_consts(double a)
+{
+    auto p = [](double v) { return make_float2((float)v, (float)v); };
+    X2Consts c;
+    c.one = p(1.0);
+    c.two_3_a2 = p(2.0 * a * a / 3.0);
+    c.m_two_a2 = p(-2.0 * a * a);
+    c.a2 = p(a * a);
+    c.m10_3 = p(-10.0 / 3.0);
+    c.c2_3 = p(2.0 / 3.0);
+    c.two = p(2.0);
+    c.m2_3 = p(-2.0 / 3.0);
+    c.m1 = p(-1.0);
+    c.c70_3 = p(70.0 / 3.0);
+    c.m10 = p(-10.0);
+    c.m6 = p(-6.0);
+    c.m140_3 = p(-140.0 / 3.0);
+    c.c40_3 = p(40.0 / 3.0);
+    c.c20 = p(20.0);
+    c.m4 = p(-4.0);
+    c.c12 = p(12.0);
+    c.m20_3 = p(-20.0 / 3.0);
+    c.m8_3 = p(-8.0 / 3.0);
+    c.c6 = p(6.0);
+    c.four_a2 = (float)(4.0 * a * a);
+    c.near_c1 = (float)(4.0 / (3.0 * a));
+    c.near_r = (float)(9.0 / (32.0 * a));
+    c.near_c2 = (float)(1.0 / (8.0 * a * a));
+    c.near_tr = (float)(1.0 / (2.0 * a * a * a));
+    c.near_tr_r = (float)(3.0 / (8.0 * a));
+    return c;
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    return __ffma2_rn(a, b, c);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    return __fmul2_rn(a, b);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    return __fadd2_rn(a, b);
+}
+__device__ __forceinline__ float2 neg2(float2 a)
+{
+    return make_float2(-a.x, -a.y);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __fadd2_rn(a, neg2(b));
+}
+
+__device__ __forceinline__ void near_fix(float r2, float inv_r, const X2Consts &c, float &c1, float &c2, float &ct)
+{
+    const float r = r2 > 0.f ? r2 * inv_r : 0.f;
+    const float ir = r2 > 0.f ? inv_r : 0.f;
+    c1 = c.near_c1 * fmaf(-c.near_r, r, 1.f);
+    c2 = c.near_c2 * ir;
+    ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
+}
+
+template <bool TORQUE>
+__device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi, float2 zj, float2 Fx, float2 Fy,
+                                                 float2 Fz, float2 Tx, float2 Ty, float2 Tz, const X2Consts &c,
+                                                 float2 &ux, float2 &uy, float2 &uz)
+{
+    const float2 rz = sub2(zi, zj);
+    const float2 rho2 = fma2(rx, rx, mul2(ry, ry));
+    const float2 r2 = fma2(rz, rz, rho2);
+    const float2 inv_r = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 inv_r2 = mul2(inv_r, inv_r);
+    const float2 ir3 = mul2(inv_r, inv_r2);
+    float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
+    float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
+    float2 ct = ir3;
+    const bool n0 = r2.x < c.four_a2, n1 = r2.y < c.four_a2;
+    if (__any_sync(0xffffffffu, n0 || n1)) {
+        if (n0) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
+        if (n1) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
+    }
+    const float2 Rz = add2(zi, zj);
+    const float2 R2 = fma2(Rz, Rz, rho2);
+    const float2 invR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+    const float2 invR2 = mul2(invR, invR);
+    const float2 ez = mul2(Rz, invR);
+    const float2 t = mul2(zj, invR);
+    const float2 s = mul2(c.a2, invR2);
+    const float2 ez2 = mul2(ez, ez), t2 = mul2(t, t), et = mul2(ez, t), s2 = mul2(s, s);
+    const float2 d = sub2(t2, et);
+    const float2 A = fma2(s2, fma2(c.m10_3, ez2, c.c2_3), fma2(s, fma2(c.two, ez2, c.m2_3), fma2(c.two, d, c.m1)));
+    const float2 B = fma2(s2, fma2(c.c70_3, ez2, c.m10_3), fma2(s, fma2(c.m10, ez2, c.two), fma2(c.m6, d, c.m1)));
+    const float2 C = fma2(ez, fma2(s2, fma2(c.m140_3, ez2, c.c40_3), mul2(s, fma2(c.c20, ez2, c.m4))),
+                          mul2(t, fma2(c.c12, sub2(et, ez2), c.two)));
+    const float2 D = fma2(c.m20_3, mul2(s2, ez), add2(t, t));
+    const float2 E = fma2(s2, fma2(c.c20, ez2, c.m8_3), mul2(c.m4, fma2(s, ez2, t2)));
+    const float2 pF = fma2(rx, Fx, mul2(ry, Fy));
+    const float2 q = mul2(fma2(Rz, Fz, pF), invR);
+    const float2 k2 = mul2(c2, fma2(rz, Fz, pF));
+    const float2 ke = mul2(fma2(B, q, mul2(C, Fz)), invR2);
+    const float2 kz = mul2(fma2(D, q, mul2(E, Fz)), invR);
+    const float2 cF = fma2(A, invR, c1);
+    const float2 kk = add2(k2, ke);
+    ux = fma2(cF, Fx, fma2(kk, rx, ux));
+    uy = fma2(cF, Fy, fma2(kk, ry, uy));
+    uz = fma2(cF, Fz, fma2(k2, rz, fma2(ke, Rz, add2(uz, kz))));
+    if (TORQUE) {
+        const float2 p = mul2(invR2, invR);
+        const float2 dcp = sub2(ct, p);
+        const float2 m1 = fma2(ct, rz, neg2(mul2(p, Rz)));
+        const float2 tz3 = fma2(Tx, ry, neg2(mul2(Ty, rx)));
+        const float2 se = mul2(s, ez);
+        const float2 m2 = fma2(add2(t, se), add2(invR2, invR2), m1);
+        const float2 ce = fma2(c.m10, se, mul2(c.c6, sub2(ez, t)));
+        const float2 w = mul2(neg2(tz3), invR);
+        const float2 cw = mul2(mul2(ce, w), p);
+        const float2 dTz = mul2(dcp, Tz);
+        ux = fma2(Ty, m2, fma2(neg2(dTz), ry, fma2(cw, rx, ux)));
+        uy = fma2(neg2(Tx), m2, fma2(dTz, rx, fma2(cw, ry, uy)));
+        uz = fma2(dcp, tz3, fma2(cw, Rz, fma2(mul2(add2(s, s), invR2), w, uz)));
+    }
+}
+
 __device__ __forceinline__ double H0(double x)
 {
     return x > 1.0 ? 1.0 : (x >= 0.0 ? x : 0.0);
@@ -183,7 +390,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32_kernel(const SrcF32 *__
                 const float4 q = TORQUE ? st[k] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float rx = (tp.x - p.x) + (tp.z - p.z);
                 const float ry = (tp.y - p.y) + (tp.w - p.w);
-                pair_velocity<float, TORQUE>(rx, ry, tz, f.x, f.y, f.z, f.w, q.x, q.y, q.z, c, ux, uy, uz);
+                pair_velocity_f32<TORQUE>(rx, ry, tz, f.x, f.y, f.z, f.w, q.x, q.y, q.z, c, ux, uy, uz);
             }
         } else {
             for (int k = 0; k < cnt; ++k) {
@@ -193,7 +400,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32_kernel(const SrcF32 *__
                 const float rx = (tp.x - p.x) + (tp.z - p.z);
                 const float ry = (tp.y - p.y) + (tp.w - p.w);
                 float dx = 0.f, dy = 0.f, dz = 0.f;
-                pair_velocity<float, TORQUE>(rx, ry, tz, f.x, f.y, f.z, f.w, q.x, q.y, q.z, c, dx, dy, dz);
+                pair_velocity_f32<TORQUE>(rx, ry, tz, f.x, f.y, f.z, f.w, q.x, q.y, q.z, c, dx, dy, dz);
                 if (k != tid) {
                     ux += dx;
                     uy += dy;
@@ -211,6 +418,129 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32_kernel(const SrcF32 *__
             cy = (tv - sy) - yv;
             sy = tv;
             yv = uz - cz;
+            tv = sz + yv;
+            cz = (tv - sz) - yv;
+            sz = tv;
+        }
+        __syncthreads();
+    }
+    if (i < N) {
+        const size_t o = (size_t)blockIdx.y * 3 * N;
+        part[o + i] = (double)sx - (double)cx;
+        part[o + N + i] = (double)sy - (double)cy;
+        part[o + 2 * N + i] = (double)sz - (double)cz;
+    }
+}
+
+// Float32 pair pass evaluating two sources per lane and iteration with packed float32x2 arithmetic.
+// The shared tile holds the 128 sources as 64 interleaved pairs: float4 (x_hi[2p], x_hi[2p+1],
+// y_hi[2p], y_hi[2p+1]), (x_lo.., y_lo..), (z~.., Fx..), (Fy.., Fz..), and for torques (Tx.., Ty..)
+// and (Tz[2p], Tz[2p+1]).  Slots past the chunk's end hold a distant source with zero load, whose
+// contribution is exactly zero, so every tile is a full 64 iterations.
+template <bool TORQUE>
+__global__ void __launch_bounds__(kPairThreads) pair_f32x2_kernel(const SrcF32 *__restrict__ src, int N, int chunk,
+                                                                   X2Consts c, double *__restrict__ part)
+{
+    constexpr int P = kTile / 2;
+    __shared__ float4 sA[P], sB[P], sC[P], sD[P];
+    __shared__ float4 sE[TORQUE ? P : 1];
+    __shared__ float2 sG[TORQUE ? P : 1];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kPairThreads + tid;
+    const int j0 = blockIdx.y * chunk;
+    const int j1 = min(N, j0 + chunk);
+    float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float tz = 1.f;
+    if (i < N) {
+        tp = src[i].p;
+        tz = src[i].f.x;
+    }
+    const float2 txh = make_float2(tp.x, tp.x), tyh = make_float2(tp.y, tp.y);
+    const float2 txl = make_float2(tp.z, tp.z), tyl = make_float2(tp.w, tp.w);
+    const float2 tz2 = make_float2(tz, tz);
+    const float2 zero2 = make_float2(0.f, 0.f);
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    const int diag = blockIdx.x * kTile;
+    const int pp = tid >> 1, hh = tid & 1;
+    float *fA = reinterpret_cast<float *>(sA);
+    float *fB = reinterpret_cast<float *>(sB);
+    float *fC = reinterpret_cast<float *>(sC);
+    float *fD = reinterpret_cast<float *>(sD);
+    float *fE = reinterpret_cast<float *>(sE);
+    float *fG = reinterpret_cast<float *>(sG);
+    for (int base = j0; base < j1; base += kTile) {
+        const int j = base + tid;
+        float4 sp_ = make_float4(1e18f, 0.f, 0.f, 0.f), sf_ = make_float4(1.f, 0.f, 0.f, 0.f);
+        float4 st_ = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < j1) {
+            sp_ = src[j].p;
+            sf_ = src[j].f;
+            if (TORQUE) st_ = src[j].t;
+        }
+        fA[4 * pp + hh] = sp_.x;
+        fA[4 * pp + 2 + hh] = sp_.y;
+        fB[4 * pp + hh] = sp_.z;
+        fB[4 * pp + 2 + hh] = sp_.w;
+        fC[4 * pp + hh] = sf_.x;
+        fC[4 * pp + 2 + hh] = sf_.y;
+        fD[4 * pp + hh] = sf_.z;
+        fD[4 * pp + 2 + hh] = sf_.w;
+        if (TORQUE) {
+            fE[4 * pp + hh] = st_.x;
+            fE[4 * pp + 2 + hh] = st_.y;
+            fG[2 * pp + hh] = st_.z;
+        }
+        __syncthreads();
+        float2 ux = zero2, uy = zero2, uz = zero2;
+        if (base != diag) {
+#pragma unroll 2
+            for (int k = 0; k < P; ++k) {
+                const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
+                const float4 e = TORQUE ? sE[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float2 g = TORQUE ? sG[k] : zero2;
+                const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
+                const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
+                pair_velocity_x2<TORQUE>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
+                                         make_float2(d.x, d.y), make_float2(d.z, d.w), make_float2(e.x, e.y),
+                                         make_float2(e.z, e.w), g, c, ux, uy, uz);
+            }
+        } else {
+            for (int k = 0; k < P; ++k) {
+                const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
+                const float4 e = TORQUE ? sE[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float2 g = TORQUE ? sG[k] : zero2;
+                const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
+                const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
+                float2 dx = zero2, dy = zero2, dz = zero2;
+                pair_velocity_x2<TORQUE>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
+                                         make_float2(d.x, d.y), make_float2(d.z, d.w), make_float2(e.x, e.y),
+                                         make_float2(e.z, e.w), g, c, dx, dy, dz);
+                if (k == pp) {  // source 2k + hh is this thread's own sphere
+                    if (hh == 0) {
+                        dx.x = 0.f;
+                        dy.x = 0.f;
+                        dz.x = 0.f;
+                    } else {
+                        dx.y = 0.f;
+                        dy.y = 0.f;
+                        dz.y = 0.f;
+                    }
+                }
+                ux = add2(ux, dx);
+                uy = add2(uy, dy);
+                uz = add2(uz, dz);
+            }
+        }
+        {
+            const float tx = ux.x + ux.y, ty = uy.x + uy.y, tzs = uz.x + uz.y;
+            float yv = tx - cx, tv = sx + yv;
+            cx = (tv - sx) - yv;
+            sx = tv;
+            yv = ty - cy;
+            tv = sy + yv;
+            cy = (tv - sy) - yv;
+            sy = tv;
+            yv = tzs - cz;
             tv = sz + yv;
             cz = (tv - sz) - yv;
             sz = tv;
@@ -366,11 +696,19 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
     if (ctx->p.precision == RPB_FP32) {
         SrcF32 *src = (SrcF32 *)ctx->ws.src;
         pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, src);
-        const PairConsts<float> c = make_consts<float>(a);
-        if (torque)
-            pair_f32_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
-        else
-            pair_f32_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+        if (ctx->fp32_variant == 1) {
+            const X2Consts c = make_x2_consts(a);
+            if (torque)
+                pair_f32x2_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+            else
+                pair_f32x2_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+        } else {
+            const PairConsts<float> c = make_consts<float>(a);
+            if (torque)
+                pair_f32_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+            else
+                pair_f32_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+        }
     } else {
         SrcF64 *src = (SrcF64 *)ctx->ws.src;
         pack_f64_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, src);

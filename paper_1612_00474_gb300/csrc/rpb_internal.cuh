@@ -39,6 +39,7 @@ struct PairConsts {
     R near_c2;      // 1/(8 a^2)
     R near_tr;      // 1/(2 a^3)
     R near_tr_r;    // 3/(8a)
+    R four_a2;      // 4a^2 (overlap test on r^2)
 };
 
 template <typename R>
@@ -54,6 +55,7 @@ inline PairConsts<R> make_consts(double a)
     c.near_c2 = (R)(1.0 / (8.0 * a * a));
     c.near_tr = (R)(1.0 / (2.0 * a * a * a));
     c.near_tr_r = (R)(3.0 / (8.0 * a));
+    c.four_a2 = (R)(4.0 * a * a);
     return c;
 }
 
@@ -88,6 +90,7 @@ struct rpb_ctx {
     cudaStream_t stream;
     int device;
     int num_sms;
+    int fp32_variant;  // float32 pair kernel: 1 = packed float32x2 (default), 0 = scalar; env RPB_FP32_PAIR
     rpb::Workspace ws;
 };
 
