@@ -142,6 +142,36 @@ const char *rpb_last_error(void);
  * all threads); for accounting of device work, e.g. launches per step. */
 uint64_t rpb_launch_count(void);
 
+/* ---------------------------------------------------------------- ragged batches
+ * Many independent suspensions of different sizes advanced by one call (the same method per
+ * suspension: Sec. II-III and Appendix A as above).  Every instance keeps its state in its own
+ * device buffers (SoA, 3 N_b doubles each); a call gathers them into the batch context's packed
+ * scratch, runs each stage for all instances together, and scatters the results back.  Instance b
+ * is computed the same way whatever the other instances are (its tiles, reductions and noise do
+ * not depend on them), so its result alone and inside a batch agree to rounding. */
+typedef struct rpb_batch rpb_batch;
+
+/* Create a batch context for at most max_B instances totalling at most max_total_N spheres.
+ * Allocates all scratch now (about (max_iter + 14) * 24 * max_total_N bytes). */
+int rpb_batch_create(rpb_batch **bt, const rpb_params *p, int64_t max_total_N, int max_B, int max_iter,
+                     void *stream);
+int rpb_batch_destroy(rpb_batch *bt);
+int rpb_batch_set_stream(rpb_batch *bt, void *stream);
+
+/* U_b = M_tt F_b + M_tr T_b for b = 0 .. B-1.  N: host array of B sizes; pos, F, T, U: host arrays
+ * of B device pointers (F or T may be NULL as a whole, i.e. zero for every instance). */
+int rpb_batch_mobility_apply(rpb_batch *bt, int B, const int64_t *N, const double *const *pos,
+                             const double *const *F, const double *const *T, double *const *U);
+
+/* One stochastic Adams-Bashforth step (Eq. AB, as rpb_ab_step) for each instance, in place.
+ * steps, seeds: host arrays of B per-instance step counters and Philox seeds (steps[b] == 0 is that
+ * instance's first, Euler-Maruyama, step); instance b draws exactly the noise rpb_ab_step would
+ * draw with seeds[b] and steps[b].  stats: host array of B entries (or NULL).  Synchronises the
+ * stream.  RPB_ENOCONV if some instance's Lanczos did not converge (all steps are still taken). */
+int rpb_batch_ab_step(rpb_batch *bt, int B, const int64_t *N, double *const *pos, double *const *U_prev,
+                      const int64_t *steps, const uint64_t *seeds, double dt, double delta, double tol,
+                      int max_iter, const rpb_force_params *fp, rpb_step_stats *stats);
+
 /* Largest N accepted by rpb_mobility_apply_noalloc. */
 #define RPB_NOALLOC_MAX_N 16384
 

@@ -1,0 +1,306 @@
+// pair_math.cuh -- device arithmetic of one Rotne-Prager-Blake pair (shared by the single-suspension
+// and batched kernels).
+//
+// Mobility (Sec. II.B Eq. mobilityDifferential / mobilityOverlap, Sec. III Eq.
+// mobilityDifferentialTR, Appendix A Eq. effMob):
+//   M_ij = s_i s_j Mtilde(q~_i, q~_j),  s = H0(z/a),  q~ = (x, y, max(z, a)),
+//   Mtilde = free-space RPY (overlap branch for r < 2a) + wall correction.
+// The wall correction is the Faxen-operated image system of Blake's half-space Green's function,
+// written in closed form on the basis {I, e e, e z, z e, z z} (translation) and
+// {T x e, T x z, e (z x e).T, z (z x e).T} (rotation), with R = x_i - x_j* (source mirrored in
+// the wall), e = R/|R|, t = z~_j/|R|, s = a^2/|R|^2.  The coefficients were obtained by
+// decomposing the Faxen-operated image tensors onto that basis; they reproduce the published
+// near-wall self mobilities 1 - 9/(16h) + 1/(8h^3) - 1/(16h^5) and 1 - 9/(8h) + 1/(2h^3) - 1/(8h^5).
+#pragma once
+
+#include "rpb_internal.cuh"
+
+namespace rpb {
+
+template <typename R>
+__device__ __forceinline__ R rsq(R x);
+template <>
+__device__ __forceinline__ float rsq<float>(float x)
+{
+    return rsqrtf(x);
+}
+template <>
+__device__ __forceinline__ double rsq<double>(double x)
+{
+    return rsqrt(x);
+}
+
+// Velocity of the target from one source, in units of 1/(8 pi eta), before the target's s_i.
+// rx, ry: in-plane offset target - source; zi, zj: clamped heights; F, T: source force and torque
+// with s_j folded in.  Accumulates into (ux, uy, uz).  Valid for r = 0 (self pair: mu0 F + wall).
+template <typename R, bool TORQUE>
+__device__ __forceinline__ void pair_velocity(R rx, R ry, R zi, R zj, R Fx, R Fy, R Fz, R Tx, R Ty, R Tz,
+                                              const PairConsts<R> &c, R &ux, R &uy, R &uz)
+{
+    // ---- free-space RPY
+    const R rz = zi - zj;
+    const R rho2 = rx * rx + ry * ry;
+    const R r2 = rho2 + rz * rz;
+    const R inv_r = r2 > R(0) ? rsq<R>(r2) : R(0);
+    const R r = r2 * inv_r;
+    const R inv_r2 = inv_r * inv_r;
+    const bool far = r >= c.two_a;
+    const R c1 = far ? inv_r * (R(1) + c.two_3_a2 * inv_r2) : c.near_c1 * (R(1) - c.near_r * r);
+    const R c2 = far ? inv_r * inv_r2 * (R(1) - c.two_a2 * inv_r2) : c.near_c2 * inv_r;
+    const R k2 = c2 * (rx * Fx + ry * Fy + rz * Fz);
+    ux += c1 * Fx + k2 * rx;
+    uy += c1 * Fy + k2 * ry;
+    uz += c1 * Fz + k2 * rz;
+    if (TORQUE) {
+        const R ct = far ? inv_r * inv_r2 : c.near_tr * (R(1) - c.near_tr_r * r);
+        ux += ct * (Ty * rz - Tz * ry);
+        uy += ct * (Tz * rx - Tx * rz);
+        uz += ct * (Tx * ry - Ty * rx);
+    }
+    // ---- wall correction (image of the source below z = 0)
+    const R Rz = zi + zj;
+    const R invR = rsq<R>(rho2 + Rz * Rz);
+    const R ex = rx * invR, ey = ry * invR, ez = Rz * invR;
+    const R t = zj * invR;
+    const R s = c.a2 * invR * invR;
+    const R ez2 = ez * ez;
+    const R t2 = t * t;
+    const R et = ez * t;
+    const R s2 = s * s;
+    const R A = R(-1) - R(2) * et + R(2) * t2 + s * (R(2) * ez2 - R(2.0 / 3.0)) + s2 * (R(2.0 / 3.0) - R(10.0 / 3.0) * ez2);
+    const R B = R(-1) + R(6) * et - R(6) * t2 + s * (R(2) - R(10) * ez2) + s2 * (R(70.0 / 3.0) * ez2 - R(10.0 / 3.0));
+    const R C = t * (R(2) - R(12) * ez2) + R(12) * et * t +
+                ez * (s * (R(20) * ez2 - R(4)) + s2 * (R(40.0 / 3.0) - R(140.0 / 3.0) * ez2));
+    const R D = R(2) * t - R(20.0 / 3.0) * s2 * ez;
+    const R E = R(-4) * t2 - R(4) * s * ez2 + s2 * (R(20) * ez2 - R(8.0 / 3.0));
+    const R eF = ex * Fx + ey * Fy + ez * Fz;
+    const R ke = (B * eF + C * Fz) * invR;
+    const R kz = (D * eF + E * Fz) * invR;
+    const R kA = A * invR;
+    ux += kA * Fx + ke * ex;
+    uy += kA * Fy + ke * ey;
+    uz += kA * Fz + ke * ez + kz;
+    if (TORQUE) {
+        const R invR2 = invR * invR;
+        const R cz = R(2) * (t + s * ez);                 // coefficient of T x z
+        const R ce = R(6) * (ez - t) - R(10) * s * ez;   // coefficient of e (z x e).T
+        const R w = ex * Ty - ey * Tx;                    // (z x e) . T
+        ux += invR2 * (-(Ty * ez - Tz * ey) + cz * Ty + ce * w * ex);
+        uy += invR2 * (-(Tz * ex - Tx * ez) - cz * Tx + ce * w * ey);
+        uz += invR2 * (-(Tx * ey - Ty * ex) + (ce * ez + R(2) * s) * w);
+    }
+}
+
+// Float32 form of pair_velocity for the hot loop, hand-fused and algebraically rearranged (same
+// mathematics): the wall terms use the unnormalised image vector R, the free-space c1 and wall A/|R|
+// share one multiply-add into F, r.F and R.F share their in-plane part, the free-space rotlet
+// c_t T x r and the wall's -|R|^-3 T x R share their z component, and the overlap branch (r < 2a,
+// rare) is evaluated only when some lane of the warp needs it.  Must be called by all 32 lanes.
+template <bool TORQUE>
+__device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, float zj, float Fx, float Fy,
+                                                  float Fz, float Tx, float Ty, float Tz, const PairConsts<float> &c,
+                                                  float &ux, float &uy, float &uz)
+{
+    // ---- free-space RPY, far branch by default
+    const float rz = zi - zj;
+    const float rho2 = fmaf(rx, rx, ry * ry);
+    const float r2 = fmaf(rz, rz, rho2);
+    const float inv_r = rsqrtf(r2);
+    const float inv_r2 = inv_r * inv_r;
+    const float ir3 = inv_r * inv_r2;
+    float c1 = inv_r * fmaf(c.two_3_a2, inv_r2, 1.f);
+    float c2 = ir3 * fmaf(-c.two_a2, inv_r2, 1.f);
+    float ct = ir3;
+    const bool near = r2 < c.four_a2;
+    if (__any_sync(0xffffffffu, near)) {
+        if (near) {  // overlap branch; r = 0 (coincident spheres) gives the self form
+            const float r = r2 > 0.f ? r2 * inv_r : 0.f;
+            const float ir = r2 > 0.f ? inv_r : 0.f;
+            c1 = c.near_c1 * fmaf(-c.near_r, r, 1.f);
+            c2 = c.near_c2 * ir;
+            ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
+        }
+    }
+    // ---- wall correction
+    const float Rz = zi + zj;
+    const float invR = rsqrtf(fmaf(Rz, Rz, rho2));
+    const float invR2 = invR * invR;
+    const float ez = Rz * invR;
+    const float t = zj * invR;
+    const float s = c.a2 * invR2;
+    const float ez2 = ez * ez, t2 = t * t, et = ez * t, s2 = s * s;
+    const float d = t2 - et;
+    const float A = fmaf(s2, fmaf(-10.f / 3.f, ez2, 2.f / 3.f), fmaf(s, fmaf(2.f, ez2, -2.f / 3.f), fmaf(2.f, d, -1.f)));
+    const float B = fmaf(s2, fmaf(70.f / 3.f, ez2, -10.f / 3.f), fmaf(s, fmaf(-10.f, ez2, 2.f), fmaf(-6.f, d, -1.f)));
+    const float C =
+        fmaf(ez, fmaf(s2, fmaf(-140.f / 3.f, ez2, 40.f / 3.f), s * fmaf(20.f, ez2, -4.f)), t * fmaf(12.f, et - ez2, 2.f));
+    const float D = fmaf(-20.f / 3.f, s2 * ez, t + t);
+    const float E = fmaf(s2, fmaf(20.f, ez2, -8.f / 3.f), -4.f * fmaf(s, ez2, t2));
+    const float pF = fmaf(rx, Fx, ry * Fy);
+    const float q = fmaf(Rz, Fz, pF) * invR;          // e.F
+    const float k2 = c2 * fmaf(rz, Fz, pF);           // free-space c2 (r.F)
+    const float ke = fmaf(B, q, C * Fz) * invR2;      // multiplies R
+    const float kz = fmaf(D, q, E * Fz) * invR;       // multiplies z_hat
+    const float cF = fmaf(A, invR, c1);               // multiplies F
+    const float kk = k2 + ke;
+    ux = fmaf(cF, Fx, fmaf(kk, rx, ux));
+    uy = fmaf(cF, Fy, fmaf(kk, ry, uy));
+    uz = fmaf(cF, Fz, fmaf(k2, rz, fmaf(ke, Rz, uz + kz)));
+    if (TORQUE) {
+        // c_t T x r - p T x R + |R|^-2 [c_z T x z + (c_e e + 2 s z) (z x e).T],  p = |R|^-3
+        const float p = invR2 * invR;
+        const float dcp = ct - p;
+        const float m1 = fmaf(ct, rz, -(p * Rz));
+        const float tz3 = fmaf(Tx, ry, -(Ty * rx));   // (T x r)_z = (T x R)_z
+        const float se = s * ez;
+        const float m2 = fmaf(t + se, invR2 + invR2, m1);
+        const float ce = fmaf(-10.f, se, 6.f * (ez - t));
+        const float w = -tz3 * invR;                   // (z x e).T
+        const float cw = ce * w * p;                   // multiplies R
+        const float dTz = dcp * Tz;
+        ux = fmaf(Ty, m2, fmaf(-dTz, ry, fmaf(cw, rx, ux)));
+        uy = fmaf(-Tx, m2, fmaf(dTz, rx, fmaf(cw, ry, uy)));
+        uz = fmaf(dcp, tz3, fmaf(cw, Rz, fmaf((s + s) * invR2, w, uz)));
+    }
+}
+
+// ---- two pairs per lane with packed float32x2 arithmetic (FFMA2/FMUL2/FADD2 on sm_100+)
+// The same formulation as pair_velocity_f32, evaluated for two sources at once: every quantity is a
+// float2 whose halves belong to two independent pairs, so one packed instruction does the work of
+// two scalar ones.  Constants are passed as float2 pairs in the kernel parameters.
+struct X2Consts {
+    float2 one, two_3_a2, m_two_a2, a2;
+    float2 m10_3, c2_3, two, m2_3, m1, c70_3, m10, m6, m140_3, c40_3, c20, m4, c12, m20_3, m8_3, c6;
+    float four_a2, near_c1, near_r, near_c2, near_tr, near_tr_r;
+};
+
+inline X2Consts make_x2_consts(double a)
+{
+    auto p = [](double v) { return make_float2((float)v, (float)v); };
+    X2Consts c;
+    c.one = p(1.0);
+    c.two_3_a2 = p(2.0 * a * a / 3.0);
+    c.m_two_a2 = p(-2.0 * a * a);
+    c.a2 = p(a * a);
+    c.m10_3 = p(-10.0 / 3.0);
+    c.c2_3 = p(2.0 / 3.0);
+    c.two = p(2.0);
+    c.m2_3 = p(-2.0 / 3.0);
+    c.m1 = p(-1.0);
+    c.c70_3 = p(70.0 / 3.0);
+    c.m10 = p(-10.0);
+    c.m6 = p(-6.0);
+    c.m140_3 = p(-140.0 / 3.0);
+    c.c40_3 = p(40.0 / 3.0);
+    c.c20 = p(20.0);
+    c.m4 = p(-4.0);
+    c.c12 = p(12.0);
+    c.m20_3 = p(-20.0 / 3.0);
+    c.m8_3 = p(-8.0 / 3.0);
+    c.c6 = p(6.0);
+    c.four_a2 = (float)(4.0 * a * a);
+    c.near_c1 = (float)(4.0 / (3.0 * a));
+    c.near_r = (float)(9.0 / (32.0 * a));
+    c.near_c2 = (float)(1.0 / (8.0 * a * a));
+    c.near_tr = (float)(1.0 / (2.0 * a * a * a));
+    c.near_tr_r = (float)(3.0 / (8.0 * a));
+    return c;
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    return __ffma2_rn(a, b, c);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    return __fmul2_rn(a, b);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    return __fadd2_rn(a, b);
+}
+__device__ __forceinline__ float2 neg2(float2 a)
+{
+    return make_float2(-a.x, -a.y);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __fadd2_rn(a, neg2(b));
+}
+
+__device__ __forceinline__ void near_fix(float r2, float inv_r, const X2Consts &c, float &c1, float &c2, float &ct)
+{
+    const float r = r2 > 0.f ? r2 * inv_r : 0.f;
+    const float ir = r2 > 0.f ? inv_r : 0.f;
+    c1 = c.near_c1 * fmaf(-c.near_r, r, 1.f);
+    c2 = c.near_c2 * ir;
+    ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
+}
+
+template <bool TORQUE>
+__device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi, float2 zj, float2 Fx, float2 Fy,
+                                                 float2 Fz, float2 Tx, float2 Ty, float2 Tz, const X2Consts &c,
+                                                 float2 &ux, float2 &uy, float2 &uz)
+{
+    const float2 rz = sub2(zi, zj);
+    const float2 rho2 = fma2(rx, rx, mul2(ry, ry));
+    const float2 r2 = fma2(rz, rz, rho2);
+    const float2 inv_r = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 inv_r2 = mul2(inv_r, inv_r);
+    const float2 ir3 = mul2(inv_r, inv_r2);
+    float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
+    float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
+    float2 ct = ir3;
+    const bool n0 = r2.x < c.four_a2, n1 = r2.y < c.four_a2;
+    if (__any_sync(0xffffffffu, n0 || n1)) {
+        if (n0) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
+        if (n1) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
+    }
+    const float2 Rz = add2(zi, zj);
+    const float2 R2 = fma2(Rz, Rz, rho2);
+    const float2 invR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+    const float2 invR2 = mul2(invR, invR);
+    const float2 ez = mul2(Rz, invR);
+    const float2 t = mul2(zj, invR);
+    const float2 s = mul2(c.a2, invR2);
+    const float2 ez2 = mul2(ez, ez), t2 = mul2(t, t), et = mul2(ez, t), s2 = mul2(s, s);
+    const float2 d = sub2(t2, et);
+    const float2 A = fma2(s2, fma2(c.m10_3, ez2, c.c2_3), fma2(s, fma2(c.two, ez2, c.m2_3), fma2(c.two, d, c.m1)));
+    const float2 B = fma2(s2, fma2(c.c70_3, ez2, c.m10_3), fma2(s, fma2(c.m10, ez2, c.two), fma2(c.m6, d, c.m1)));
+    const float2 C = fma2(ez, fma2(s2, fma2(c.m140_3, ez2, c.c40_3), mul2(s, fma2(c.c20, ez2, c.m4))),
+                          mul2(t, fma2(c.c12, sub2(et, ez2), c.two)));
+    const float2 D = fma2(c.m20_3, mul2(s2, ez), add2(t, t));
+    const float2 E = fma2(s2, fma2(c.c20, ez2, c.m8_3), mul2(c.m4, fma2(s, ez2, t2)));
+    const float2 pF = fma2(rx, Fx, mul2(ry, Fy));
+    const float2 q = mul2(fma2(Rz, Fz, pF), invR);
+    const float2 k2 = mul2(c2, fma2(rz, Fz, pF));
+    const float2 ke = mul2(fma2(B, q, mul2(C, Fz)), invR2);
+    const float2 kz = mul2(fma2(D, q, mul2(E, Fz)), invR);
+    const float2 cF = fma2(A, invR, c1);
+    const float2 kk = add2(k2, ke);
+    ux = fma2(cF, Fx, fma2(kk, rx, ux));
+    uy = fma2(cF, Fy, fma2(kk, ry, uy));
+    uz = fma2(cF, Fz, fma2(k2, rz, fma2(ke, Rz, add2(uz, kz))));
+    if (TORQUE) {
+        const float2 p = mul2(invR2, invR);
+        const float2 dcp = sub2(ct, p);
+        const float2 m1 = fma2(ct, rz, neg2(mul2(p, Rz)));
+        const float2 tz3 = fma2(Tx, ry, neg2(mul2(Ty, rx)));
+        const float2 se = mul2(s, ez);
+        const float2 m2 = fma2(add2(t, se), add2(invR2, invR2), m1);
+        const float2 ce = fma2(c.m10, se, mul2(c.c6, sub2(ez, t)));
+        const float2 w = mul2(neg2(tz3), invR);
+        const float2 cw = mul2(mul2(ce, w), p);
+        const float2 dTz = mul2(dcp, Tz);
+        ux = fma2(Ty, m2, fma2(neg2(dTz), ry, fma2(cw, rx, ux)));
+        uy = fma2(neg2(Tx), m2, fma2(dTz, rx, fma2(cw, ry, uy)));
+        uz = fma2(dcp, tz3, fma2(cw, Rz, fma2(mul2(add2(s, s), invR2), w, uz)));
+    }
+}
+
+__device__ __forceinline__ double H0(double x)
+{
+    return x > 1.0 ? 1.0 : (x >= 0.0 ? x : 0.0);
+}
+
+}  // namespace rpb

@@ -107,6 +107,12 @@ int cuda_fail(cudaError_t e, const char *what);
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
                         double *U);
 
+// Packed source records from float64 SoA inputs (pair.cu); also used by the batched path.
+__global__ void pack_f32_kernel(const double *__restrict__ pos, const double *__restrict__ F,
+                                const double *__restrict__ T, int N, double a, SrcF32 *__restrict__ out);
+__global__ void pack_f64_kernel(const double *__restrict__ pos, const double *__restrict__ F,
+                                const double *__restrict__ T, int N, double a, SrcF64 *__restrict__ out);
+
 // Number of column splits and chunk length the pair kernel uses for N targets.
 void pair_grid(int64_t N, int num_sms, int precision, int *splits, int64_t *chunk);
 size_t pair_partial_bytes(int64_t max_N, int num_sms);

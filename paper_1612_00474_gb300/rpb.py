@@ -21,7 +21,8 @@ PRECISIONS = {"fp64": RPB_FP64, "fp32": RPB_FP32}
 # Every entry point the header declares (checked by the tests against include/rpb.h).
 EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", "rpb_lanczos_sqrt_apply",
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
-           "rpb_launch_count", "rpb_mobility_apply_noalloc")
+           "rpb_launch_count", "rpb_mobility_apply_noalloc", "rpb_batch_create", "rpb_batch_destroy",
+           "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step")
 NOALLOC_MAX_N = 16384
 
 
@@ -83,6 +84,13 @@ def load(build_if_missing=True):
     L.rpb_launch_count.argtypes = []
     L.rpb_launch_count.restype = ctypes.c_uint64
     L.rpb_mobility_apply_noalloc.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp]
+    pi64 = ctypes.POINTER(i64)
+    L.rpb_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), i64, i32, i32, vp]
+    L.rpb_batch_destroy.argtypes = [vp]
+    L.rpb_batch_set_stream.argtypes = [vp, vp]
+    L.rpb_batch_mobility_apply.argtypes = [vp, i32, pi64, vp, vp, vp, vp]
+    L.rpb_batch_ab_step.argtypes = [vp, i32, pi64, vp, vp, pi64, ctypes.POINTER(u64), d, d, d, i32,
+                                    ctypes.POINTER(ForceParams), ctypes.POINTER(StepStats)]
     for name in EXPORTS:
         if name not in ("rpb_last_error", "rpb_launch_count"):
             getattr(L, name).restype = ctypes.c_int
@@ -244,3 +252,74 @@ class Context:
         if not (rc == RPB_ENOCONV and not raise_on_noconv):
             _check(rc)
         return dict(m=stats.lanczos_iters, eps=stats.lanczos_err, converged=bool(stats.converged))
+
+
+class BatchContext:
+    """A ragged-batch context (rpb_batch_create): one call advances many independent suspensions,
+    each kept in its own (3 N_b,) float64 CUDA tensors."""
+
+    def __init__(self, max_total_N, max_B, a=1.0, eta=1.0, kT=1.0, precision="fp32", max_iter=64):
+        L = load()
+        p = Params(float(a), float(eta), float(kT), PRECISIONS[precision])
+        h = ctypes.c_void_p()
+        _check(L.rpb_batch_create(ctypes.byref(h), ctypes.byref(p), int(max_total_N), int(max_B), int(max_iter),
+                                  _stream()))
+        self._h = h
+        self.max_total_N = int(max_total_N)
+        self.max_B = int(max_B)
+        self.max_iter = int(max_iter)
+        self.params = dict(a=a, eta=eta, kT=kT, precision=precision)
+
+    def close(self):
+        if self._h:
+            _check(load().rpb_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self):
+        _check(load().rpb_batch_set_stream(self._h, _stream()))
+
+    @staticmethod
+    def _ptrs(ts, name, nullable=False):
+        if ts is None:
+            if nullable:
+                return None
+            raise ValueError(f"{name} is required")
+        arr = (ctypes.c_void_p * len(ts))()
+        for k, t in enumerate(ts):
+            arr[k] = _ptr(t, None, f"{name}[{k}]").value
+        return arr
+
+    def mobility_apply(self, pos, F=None, T=None, out=None):
+        """U_b = M_tt F_b + M_tr T_b for each instance (rpb_batch_mobility_apply); lists of tensors."""
+        import torch
+
+        B = len(pos)
+        Ns = (ctypes.c_int64 * B)(*[p.numel() // 3 for p in pos])
+        out = [torch.empty_like(p) for p in pos] if out is None else out
+        self._bind_stream()
+        _check(load().rpb_batch_mobility_apply(self._h, B, Ns, self._ptrs(pos, "pos"), self._ptrs(F, "F", True),
+                                               self._ptrs(T, "T", True), self._ptrs(out, "U")))
+        return out
+
+    def ab_step(self, pos, U_prev, steps, seeds, dt=0.01, delta=1e-6, tol=1e-3, max_iter=None, weight=1.0, U0=1.0,
+                b=0.1, torque=(0.0, 1.0, 0.0), raise_on_noconv=True):
+        """One AB step of every instance in place (rpb_batch_ab_step); returns per-instance statistics."""
+        B = len(pos)
+        Ns = (ctypes.c_int64 * B)(*[p.numel() // 3 for p in pos])
+        st = (ctypes.c_int64 * B)(*[int(s) for s in steps])
+        sd = (ctypes.c_uint64 * B)(*[int(s) for s in seeds])
+        stats = (StepStats * B)()
+        fp = _force_params(weight, U0, b, torque)
+        self._bind_stream()
+        rc = load().rpb_batch_ab_step(self._h, B, Ns, self._ptrs(pos, "pos"), self._ptrs(U_prev, "U_prev"), st, sd,
+                                      float(dt), float(delta), float(tol), int(max_iter or self.max_iter),
+                                      ctypes.byref(fp), stats)
+        if not (rc == RPB_ENOCONV and not raise_on_noconv):
+            _check(rc)
+        return [dict(m=s.lanczos_iters, eps=s.lanczos_err, converged=bool(s.converged)) for s in stats]
