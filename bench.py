@@ -50,6 +50,13 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--workload", choices=["monolayer", "batched", "serving"], default="monolayer")
+    ap.add_argument("--B", type=int, default=512, help="batched: number of suspensions")
+    ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--load", type=float, default=0.85, help="serving: offered load relative to measured capacity")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: device-memory budget for resident state")
+    ap.add_argument("--max-batch", type=int, default=256, help="serving: requests per batched step")
+    ap.add_argument("--max-spheres", type=int, default=262144, help="serving: spheres per batched step")
     return ap.parse_args()
 
 
@@ -144,17 +151,38 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(dist, max_vals, sum_vals, device="cpu"):
+    """Combine per-rank measurements: the maximum over ranks of each entry of max_vals (times) and
+    the sum of each entry of sum_vals (work).  dist is torch.distributed (initialised) or None."""
+    import torch
+
+    mx = [float(v) for v in max_vals]
+    sm = [float(v) for v in sum_vals]
+    if dist is None:
+        return mx, sm
+    a = torch.tensor(mx, dtype=torch.float64, device=device)
+    b = torch.tensor(sm, dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return a.cpu().tolist(), b.cpu().tolist()
+
+
+def init_dist(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group("nccl", init_method="env://")
+    return dist
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
     from paper_1612_00474_gb300 import inputs, rpb
 
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", init_method="env://")
+    dist = init_dist(world)
 
     N = args.N
     seed = args.seed + rank  # independent replicas, one suspension per rank
@@ -242,15 +270,9 @@ def run_ours(args, rank, world, local_rank):
     t_tt = time_product(W, None)
     t_fused = time_product(W, Tq)
 
-    # max over ranks
-    res = torch.tensor([total_s, e2e_s, pairs, e2e_pairs], dtype=torch.float64, device="cuda")
+    # max of the times and sum of the work over ranks
+    (total_s, e2e_s), (pairs, e2e_pairs) = aggregate(dist, [total_s, e2e_s], [pairs, e2e_pairs], device="cuda")
     if dist:
-        tmax = res[:2].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        psum = res[2:].clone()
-        dist.all_reduce(psum, op=dist.ReduceOp.SUM)
-        total_s, e2e_s = float(tmax[0]), float(tmax[1])
-        pairs, e2e_pairs = float(psum[0]), float(psum[1])
         dist.barrier()
 
     cpu = None
@@ -297,6 +319,164 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def _base_line(args, world, metric_value, unit, ms_per_step, dtype, config):
+    return {"metric": METRIC, "value": metric_value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+
+
+def run_batched(args, rank, world, local_rank):
+    """512 independent suspensions, N log-uniform in [64, 2048] (seeds 0..511), advanced together by
+    rpb_batch_ab_step; compared with a loop over the single-suspension rpb_ab_step."""
+    import torch
+
+    from paper_1612_00474_gb300 import inputs, rpb
+
+    torch.cuda.set_device(local_rank)
+    dist = init_dist(world)
+    B = args.B
+    sizes = [int(n) for n in inputs.batch_sizes(B, seed=args.seed)]
+    seeds = [args.seed + rank * B + k for k in range(B)]
+    bt = rpb.BatchContext(max_total_N=sum(sizes), max_B=B, precision=args.precision, max_iter=64)
+    q = [torch.tensor(inputs.to_soa(inputs.monolayer(N, seed=s)), dtype=torch.float64, device="cuda")
+         for N, s in zip(sizes, seeds)]
+    U = [torch.zeros_like(t) for t in q]
+    kw = dict(dt=args.dt, delta=args.delta, tol=args.tol, max_iter=64)
+    stream = torch.cuda.current_stream()
+    step = 0
+    for _ in range(args.warmup):
+        bt.ab_step(q, U, [step] * B, seeds, **kw)
+        step += 1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks_start(local_rank)
+    launches0 = rpb.launch_count()
+    pairs, ms = 0.0, []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = bt.ab_step(q, U, [step] * B, seeds, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        pairs += sum(float(N) * N * (3 + s["m"]) for N, s in zip(sizes, st))
+        step += 1
+    clocks = clocks_stop(clk)
+    launches = rpb.launch_count() - launches0
+    total_s = sum(ms) / 1e3
+    # the same instances, one rpb_ab_step call each (one step of all B)
+    ctx = rpb.Context(max_N=max(sizes), precision=args.precision, max_iter=64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(B):
+        ctx.ab_step(q[k], U[k], step, seeds[k], **kw)
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    ctx.close()
+    bt.close()
+    (total_s, loop_s), (pairs,) = aggregate(dist, [total_s, loop_s], [pairs], device="cuda")
+    if rank == 0:
+        inst_steps = B * args.steps * world / total_s
+        line = _base_line(args, world, pairs / total_s / 1e9, "Gpairs/s", total_s * 1e3 / args.steps,
+                          "f32" if args.precision == "fp32" else "f64",
+                          {"workload": f"batched: {B} suspensions, N log-uniform in [64, 2048] (sum N = {sum(sizes)}), "
+                                       f"AB step dt={args.dt}, delta={args.delta}, tol={args.tol}, "
+                                       f"{args.precision} pairs", "B": B, "sum_N": sum(sizes),
+                           "sum_N2": sum(N * N for N in sizes), "parallelism": f"replicas x{world}"})
+        line.update({"instance_steps_per_s": inst_steps,
+                     "loop_instance_steps_per_s": B * world / loop_s,
+                     "speedup_vs_loop": inst_steps / (B * world / loop_s),
+                     "step_ms": [round(x, 3) for x in ms], "gpu_launches": int(launches), "clocks": clocks})
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_serving(args, rank, world, local_rank):
+    """Poisson arrivals of trajectory requests (N log-uniform in [128, 32768], 10-200 steps), served by
+    continuous batching with state resident in HBM and admission by a device-memory budget; p50/p99
+    request latency and throughput, beside a serial FP64 single-suspension server simulated from
+    measured per-step times of that path."""
+    import torch
+
+    from paper_1612_00474_gb300 import inputs, rpb, serve
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    # calibrate: batched throughput on a mixed sample, to pick an arrival rate near 85% utilisation
+    sample = serve.poisson_requests(16, rate=1.0, seed=args.seed + 99)
+    srv = serve.GpuServer(max_batch=args.max_batch, max_spheres=args.max_spheres, precision=args.precision,
+                          delta=args.delta, tol=args.tol, dt=args.dt)
+    act = []
+    for r in sample[:12]:
+        r.state = srv.allocate(r)
+        act.append(r)
+    srv.step(act)
+    torch.cuda.synchronize()
+    srv.pairs = 0.0
+    t0 = time.perf_counter()
+    for _ in range(3):
+        srv.step(act)
+    torch.cuda.synchronize()
+    thr = srv.pairs / (time.perf_counter() - t0)              # pairs/s when busy
+    reqs = serve.poisson_requests(args.requests, rate=1.0, seed=args.seed)
+    mean_work = statistics.mean(r.N * r.N * 11.0 * r.steps for r in reqs)
+    rate = args.load * thr / mean_work
+    reqs = serve.poisson_requests(args.requests, rate=rate, seed=args.seed)
+    for r in reqs:  # the client supplies the initial configuration with the request
+        r.pos0 = inputs.monolayer(r.N, seed=r.seed)
+    srv.pairs = 0.0
+    sched = serve.Scheduler(budget_bytes=int(args.budget_gb * 1e9), max_batch=args.max_batch,
+                            max_spheres=args.max_spheres)
+    launches0 = rpb.launch_count()
+    clk = clocks_start(local_rank)
+    fin, busy, total = serve.run(reqs, sched, srv.step, srv.allocate, srv.finalize)
+    clocks = clocks_stop(clk)
+    launches = rpb.launch_count() - launches0
+    srv.close()
+    lat = [r.latency for r in fin]
+    req_steps = sum(r.steps for r in fin)
+    # serial FP64 reference server: per-step time of rpb_ab_step (FP64) measured at a few sizes,
+    # fitted as t(N) = c0 + c2 N^2, and a first-come-first-served queue over the same arrivals
+    ctx = rpb.Context(max_N=32768, precision="fp64", max_iter=64)
+    pts = []
+    for N in (128, 1024, 4096, 16384):
+        qq = torch.tensor(inputs.to_soa(inputs.monolayer(N, seed=5)), dtype=torch.float64, device="cuda")
+        UU = torch.zeros_like(qq)
+        ctx.ab_step(qq, UU, 0, 5, delta=1e-6, tol=args.tol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.ab_step(qq, UU, 1, 5, delta=1e-6, tol=args.tol)
+        torch.cuda.synchronize()
+        pts.append((N, time.perf_counter() - t0))
+    ctx.close()
+    A = np.array([[1.0, float(N) ** 2] for N, _ in pts])
+    coef = np.linalg.lstsq(A, np.array([t for _, t in pts]), rcond=None)[0]
+    tfree, lat64 = 0.0, []
+    for r in sorted(reqs, key=lambda r: r.arrival):
+        start = max(tfree, r.arrival)
+        tfree = start + r.steps * (coef[0] + coef[1] * r.N * r.N)
+        lat64.append(tfree - r.arrival)
+    line = _base_line(args, 1, srv.pairs / total / 1e9, "Gpairs/s", 1e3 * busy / max(1, len(fin)),
+                      "f32" if args.precision == "fp32" else "f64",
+                      {"workload": f"serving: {len(reqs)} Poisson requests at {rate:.3f}/s, N log-uniform in "
+                                   f"[128, 32768], 10-200 steps, budget {args.budget_gb} GB, batch <= "
+                                   f"{args.max_batch} requests / {args.max_spheres} spheres, {args.precision} pairs",
+                       "requests": len(reqs), "rate_per_s": rate})
+    line.update({"p50_latency_s": serve.percentile(lat, 50), "p99_latency_s": serve.percentile(lat, 99),
+                 "request_steps_per_s": req_steps / total, "gpu_busy_frac": busy / total, "wall_s": total,
+                 "serial_fp64": {"p50_latency_s": serve.percentile(lat64, 50),
+                                 "p99_latency_s": serve.percentile(lat64, 99),
+                                 "request_steps_per_s": req_steps / max(tfree, 1e-9),
+                                 "step_time_fit_s": {"c0": coef[0], "c2": coef[1]},
+                                 "basis": "FCFS queue simulated from rpb_ab_step FP64 step times measured at "
+                                          "N = 128, 1024, 4096, 16384"},
+                 "gpu_launches": int(launches), "clocks": clocks})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.delta is None:
@@ -307,7 +487,12 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
+    elif args.workload == "serving":
+        run_serving(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
 
 
 if __name__ == "__main__":
