@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "wall-RPY matvec Gpairs/s; BD steps/s at N=65536; p50/p99 solve latency"
 FLOPS_TT = 126      # algorithmic flops per pair, translation-translation block applied to a vector
 FLOPS_FUSED = 185   # ... plus the translation-rotation block (counts derived in the design doc)
+FLOPS_SYM = 171     # per unordered pair when the block is evaluated once and applied both ways (81 + 2 x 45)
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
@@ -285,7 +286,14 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
         peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        flops_tt = float(N) * N * FLOPS_TT
+        sym = args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256
+        if sym:  # each unordered pair once (171 flop) except inside the 128-wide diagonal tiles (126 flop each way)
+            diag = float(N) * 128
+            flops_tt = FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag
+            kernel = "pair_f32x2_sym_kernel (translation-translation, reciprocity)"
+        else:
+            flops_tt = float(N) * N * FLOPS_TT
+            kernel = f"pair_f{args.precision[2:]}_kernel<false> (translation-translation)"
         achieved = flops_tt / t_tt / 1e12
         value = pairs / total_s / 1e9
         line = {
@@ -301,11 +309,12 @@ def run_ours(args, rank, world, local_rank):
             "step_ms": [round(x, 3) for x in step_ms],
             "matvec": {"tt_ms": t_tt * 1e3, "fused_ms": t_fused * 1e3,
                        "tt_gpairs_s": N * N / t_tt / 1e9, "fused_gpairs_s": N * N / t_fused / 1e9},
-            "roofline": {"bound": "alu", "kernel": f"pair_f{args.precision[2:]}_kernel<false> (translation-translation)",
+            "roofline": {"bound": "alu", "kernel": kernel,
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
                                        if args.precision == "fp32" else "fp32 lanes (fp64 path: see DESIGN.md)",
-                         "flops_per_pair": FLOPS_TT, "traffic": None},
+                         "flops_per_launch": flops_tt,
+                         "flops_per_pair": FLOPS_SYM / 2 if sym else FLOPS_TT, "traffic": None},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": "Gpairs/s", "h2d_bytes_per_step": 2 * 3 * N * 8,
                     "d2h_bytes_per_step": 2 * 3 * N * 8},

@@ -72,7 +72,8 @@ static int check_vec(const void *p, const char *name, bool nullable)
 static void free_ws(Workspace &w)
 {
     void *dev[] = {w.src, w.partial, w.V, w.w, w.red, w.lz, w.pos_a, w.pos_b,
-                   w.vec_a, w.vec_b, w.vec_c, w.vec_d, w.vec_e, w.vec_f, w.vec_g};
+                   w.vec_a, w.vec_b, w.vec_c, w.vec_d, w.vec_e, w.vec_f, w.vec_g,
+                   w.sym_index, w.sym_tgt, w.sym_src};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (w.host_status) cudaFreeHost(w.host_status);
@@ -168,6 +169,27 @@ int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, 
             free_ws(w);
             delete c;
             return RPB_ENOMEM;
+        }
+    }
+    {
+        // the symmetric float32 translation-translation pass needs a triangle of column partials
+        // (~N^2/128 * 12 bytes); used when that stays below 8 GB and RPB_FP32_SYM is not "0"
+        const char *v = getenv("RPB_FP32_SYM");
+        const size_t src_bytes = sym_src_part_bytes(max_N);
+        c->sym_enabled = p->precision == RPB_FP32 && !(v && strcmp(v, "0") == 0) && max_N >= 2 * kTile &&
+                         src_bytes <= ((size_t)8 << 30);
+        if (c->sym_enabled) {
+            w.sym_index_ints = sym_index_ints(max_N, c->num_sms);
+            w.sym_tgt_bytes = sym_tgt_part_bytes(max_N, c->num_sms);
+            if (cudaMalloc(&w.sym_index, w.sym_index_ints * sizeof(int)) != cudaSuccess ||
+                cudaMalloc(&w.sym_tgt, w.sym_tgt_bytes) != cudaSuccess ||
+                cudaMalloc(&w.sym_src, src_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("cudaMalloc of the symmetric-pass scratch (%zu bytes) failed", src_bytes);
+                free_ws(w);
+                delete c;
+                return RPB_ENOMEM;
+            }
         }
     }
     if (cudaMallocHost((void **)&w.host_status, 8 * sizeof(double)) != cudaSuccess) {

@@ -22,8 +22,10 @@
 //   - float32 mode: positions split x = x_hi + x_lo (two floats), so near-pair offsets keep float32
 //     relative accuracy anywhere in a large box; per-tile float32 sums are added with Kahan
 //     compensation.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "pair_math.cuh"
 
@@ -269,6 +271,266 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32x2_kernel(const SrcF32 *
     }
 }
 
+// ------------------------------------------------------------------ symmetric tt pass
+// Translation-translation product evaluating each unordered pair once (reciprocity M_ji = M_ij^T).
+// CTA c covers target block b = ctas[c].b (128 targets) and source tiles [t0, t1) with t0 >= b of the
+// upper triangle.  The diagonal tile (t = b) is done one-directionally with the self pair excluded;
+// every other tile gives both u_i (target side, registers) and v_j (source side): each lane's v_j for
+// four sources are combined across the warp by a reduce-scatter (two exchange levels, then three
+// butterfly levels), the four warps' sums are added at the end of the tile, and the tile's source
+// sums go to src_part[col_start[t] + b].  The reduce kernel adds, for each sphere, its row's target
+// partials and its column's source partials in a fixed order.
+struct SymCta {
+    int b, t0, t1, pad;
+};
+
+__global__ void __launch_bounds__(kPairThreads) pair_f32x2_sym_kernel(const SrcF32 *__restrict__ src, int N,
+                                                                       const SymCta *__restrict__ ctas, X2Consts c,
+                                                                       const int *__restrict__ col_start,
+                                                                       double *__restrict__ tgt_part,
+                                                                       float *__restrict__ src_part)
+{
+    constexpr int P = kTile / 2;
+    __shared__ float4 sA[P], sB[P], sC[P], sD[P];
+    __shared__ float sv[4][3][kTile];
+    const SymCta cd = ctas[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i = cd.b * kTile + tid;
+    float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 tf = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (i < N) {
+        tp = src[i].p;
+        tf = src[i].f;
+    }
+    const float2 txh = make_float2(tp.x, tp.x), tyh = make_float2(tp.y, tp.y);
+    const float2 txl = make_float2(tp.z, tp.z), tyl = make_float2(tp.w, tp.w);
+    const float2 tz2 = make_float2(tf.x, tf.x);
+    const float2 Gx = make_float2(tf.y, tf.y), Gy = make_float2(tf.z, tf.z), Gz = make_float2(tf.w, tf.w);
+    const float2 zero2 = make_float2(0.f, 0.f);
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    const int pp = tid >> 1, hh = tid & 1;
+    const bool bit4 = (lane >> 4) & 1, bit3 = (lane >> 3) & 1;
+    float *fA = reinterpret_cast<float *>(sA);
+    float *fB = reinterpret_cast<float *>(sB);
+    float *fC = reinterpret_cast<float *>(sC);
+    float *fD = reinterpret_cast<float *>(sD);
+    for (int t = cd.t0; t < cd.t1; ++t) {
+        const int j = t * kTile + tid;
+        float4 sp_ = make_float4(1e18f, 0.f, 0.f, 0.f), sf_ = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (j < N) {
+            sp_ = src[j].p;
+            sf_ = src[j].f;
+        }
+        fA[4 * pp + hh] = sp_.x;
+        fA[4 * pp + 2 + hh] = sp_.y;
+        fB[4 * pp + hh] = sp_.z;
+        fB[4 * pp + 2 + hh] = sp_.w;
+        fC[4 * pp + hh] = sf_.x;
+        fC[4 * pp + 2 + hh] = sf_.y;
+        fD[4 * pp + hh] = sf_.z;
+        fD[4 * pp + 2 + hh] = sf_.w;
+        __syncthreads();
+        float2 ux = zero2, uy = zero2, uz = zero2;
+        if (t == cd.b) {
+            for (int k = 0; k < P; ++k) {
+                const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
+                const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
+                const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
+                float2 dx = zero2, dy = zero2, dz = zero2;
+                pair_velocity_x2<false>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
+                                        make_float2(d.x, d.y), make_float2(d.z, d.w), zero2, zero2, zero2, c, dx, dy,
+                                        dz);
+                if (k == pp) {
+                    if (hh == 0) {
+                        dx.x = 0.f;
+                        dy.x = 0.f;
+                        dz.x = 0.f;
+                    } else {
+                        dx.y = 0.f;
+                        dy.y = 0.f;
+                        dz.y = 0.f;
+                    }
+                }
+                ux = add2(ux, dx);
+                uy = add2(uy, dy);
+                uz = add2(uz, dz);
+            }
+        } else {
+            for (int k = 0; k < P; k += 2) {
+                float2 v[2][3];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float4 a = sA[k + h], b = sB[k + h], cc = sC[k + h], d = sD[k + h];
+                    const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
+                    const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
+                    pair_sym_x2(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), make_float2(d.x, d.y),
+                                make_float2(d.z, d.w), Gx, Gy, Gz, c, ux, uy, uz, v[h][0], v[h][1], v[h][2]);
+                }
+                // reduce-scatter of the four sources 2k .. 2k+3 over the warp: lane L ends with the
+                // sum for source 2k + 2 bit4(L) + bit3(L); lanes 0, 8, 16, 24 store it
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float2 keep = bit4 ? v[1][q] : v[0][q];
+                    const float2 send = bit4 ? v[0][q] : v[1][q];
+                    const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 16),
+                                                   __shfl_xor_sync(0xffffffffu, send.y, 16));
+                    const float2 w2 = add2(keep, got);
+                    float w = bit3 ? w2.y : w2.x;
+                    const float o = bit3 ? w2.x : w2.y;
+                    w += __shfl_xor_sync(0xffffffffu, o, 8);
+                    w += __shfl_xor_sync(0xffffffffu, w, 4);
+                    w += __shfl_xor_sync(0xffffffffu, w, 2);
+                    w += __shfl_xor_sync(0xffffffffu, w, 1);
+                    if ((lane & 7) == 0) sv[warp][q][2 * k + 2 * bit4 + bit3] = w;
+                }
+            }
+        }
+        {
+            const float tx = ux.x + ux.y, ty = uy.x + uy.y, tzs = uz.x + uz.y;
+            float yv = tx - cx, tv = sx + yv;
+            cx = (tv - sx) - yv;
+            sx = tv;
+            yv = ty - cy;
+            tv = sy + yv;
+            cy = (tv - sy) - yv;
+            sy = tv;
+            yv = tzs - cz;
+            tv = sz + yv;
+            cz = (tv - sz) - yv;
+            sz = tv;
+        }
+        __syncthreads();
+        if (t != cd.b) {
+            float *o = src_part + (size_t)(col_start[t] + cd.b) * 3 * kTile;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) o[q * kTile + tid] = (sv[0][q][tid] + sv[1][q][tid]) + (sv[2][q][tid] + sv[3][q][tid]);
+        }
+        __syncthreads();
+    }
+    double *o = tgt_part + (size_t)blockIdx.x * 3 * kTile;
+    o[tid] = (double)sx - (double)cx;
+    o[kTile + tid] = (double)sy - (double)cy;
+    o[2 * kTile + tid] = (double)sz - (double)cz;
+}
+
+// Row partials of the targets plus column partials of the sources, fixed order; float64 self term;
+// s_i / (8 pi eta).  Translation-translation only (no torque).
+__global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
+                                       const int *__restrict__ row_cta, const int *__restrict__ col_start, int N,
+                                       const double *__restrict__ pos, const double *__restrict__ F,
+                                       PairConsts<double> c, double a, double scale, double *__restrict__ U)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = i / kTile, l = i - b * kTile;
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int k = row_cta[b]; k < row_cta[b + 1]; ++k) {
+        const double *o = tgt_part + (size_t)k * 3 * kTile;
+        ux += o[l];
+        uy += o[kTile + l];
+        uz += o[2 * kTile + l];
+    }
+    for (int bb = 0; bb < b; ++bb) {
+        const float *o = src_part + (size_t)(col_start[b] + bb) * 3 * kTile;
+        ux += (double)o[l];
+        uy += (double)o[kTile + l];
+        uz += (double)o[2 * kTile + l];
+    }
+    const double z = pos[2 * N + i];
+    const double si = H0(z / a);
+    const double zc = fmax(z, a);
+    pair_velocity<double, false>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], 0.0, 0.0, 0.0, c, ux, uy,
+                                 uz);
+    const double k = si * scale;
+    U[i] = k * ux;
+    U[N + i] = k * uy;
+    U[2 * N + i] = k * uz;
+}
+
+// Upper-triangle schedule for N targets: rows split into runs of about (tiles / (8 SMs)) tiles.
+void sym_schedule(int64_t N, int num_sms, std::vector<int> &cta4, std::vector<int> &row_cta, std::vector<int> &col_start)
+{
+    const int nb = (int)((N + kTile - 1) / kTile);
+    const int64_t tiles = (int64_t)nb * (nb + 1) / 2;
+    int L = (int)((tiles + 8 * (int64_t)num_sms - 1) / (8 * (int64_t)num_sms));
+    if (L < 1) L = 1;
+    cta4.clear();
+    row_cta.assign(nb + 1, 0);
+    col_start.assign(nb, 0);
+    for (int t = 0; t < nb; ++t) col_start[t] = (int)((int64_t)t * (t - 1) / 2);
+    int n = 0;
+    for (int b = 0; b < nb; ++b) {
+        row_cta[b] = n;
+        for (int t0 = b; t0 < nb; t0 += L) {
+            cta4.push_back(b);
+            cta4.push_back(t0);
+            cta4.push_back(std::min(nb, t0 + L));
+            cta4.push_back(0);
+            ++n;
+        }
+    }
+    row_cta[nb] = n;
+}
+
+size_t sym_src_part_bytes(int64_t max_N)
+{
+    const int64_t nb = (max_N + kTile - 1) / kTile;
+    return (size_t)(nb * (nb - 1) / 2) * 3 * kTile * sizeof(float);
+}
+
+size_t sym_tgt_part_bytes(int64_t max_N, int num_sms)
+{
+    const int64_t nb = (max_N + kTile - 1) / kTile;
+    return (size_t)(2 * nb + 8 * (int64_t)num_sms + 8) * 3 * kTile * sizeof(double);
+}
+
+size_t sym_index_ints(int64_t max_N, int num_sms)
+{
+    const int64_t nb = (max_N + kTile - 1) / kTile;
+    return (size_t)4 * (2 * nb + 8 * (int64_t)num_sms + 8) + 2 * (nb + 1);
+}
+
+// Symmetric translation-translation product (float32 pairs); requires ctx->ws.sym_* scratch.
+static int mobility_tt_sym(rpb_ctx *ctx, int N, const double *pos, const double *F, double *U)
+{
+    cudaStream_t st = ctx->stream;
+    Workspace &w = ctx->ws;
+    if (w.sym_N != N) {
+        std::vector<int> cta4, row_cta, col_start;
+        sym_schedule(N, ctx->num_sms, cta4, row_cta, col_start);
+        const size_t need = cta4.size() + row_cta.size() + col_start.size();
+        if (need > w.sym_index_ints || cta4.size() / 4 * 3 * kTile * sizeof(double) > w.sym_tgt_bytes) {
+            set_error("internal: symmetric schedule larger than its scratch (N=%d)", N);
+            return RPB_EINVAL;
+        }
+        std::vector<int> host(need);
+        std::copy(cta4.begin(), cta4.end(), host.begin());
+        std::copy(row_cta.begin(), row_cta.end(), host.begin() + cta4.size());
+        std::copy(col_start.begin(), col_start.end(), host.begin() + cta4.size() + row_cta.size());
+        int rc;
+        if ((rc = cuda_fail(cudaMemcpyAsync(w.sym_index, host.data(), need * sizeof(int), cudaMemcpyHostToDevice, st),
+                            "symmetric schedule copy")))
+            return rc;
+        if ((rc = cuda_fail(cudaStreamSynchronize(st), "symmetric schedule copy"))) return rc;
+        w.sym_N = N;
+        w.sym_ncta = (int)(cta4.size() / 4);
+        w.sym_row_off = (int)cta4.size();
+        w.sym_col_off = (int)(cta4.size() + row_cta.size());
+    }
+    const double a = ctx->p.a;
+    SrcF32 *src = (SrcF32 *)w.src;
+    const int pb = 256;
+    pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, nullptr, N, a, src);
+    pair_f32x2_sym_kernel<<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, (const SymCta *)w.sym_index, make_x2_consts(a),
+                                                               w.sym_index + w.sym_col_off, w.sym_tgt, w.sym_src);
+    pair_sym_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
+                                                             w.sym_index + w.sym_col_off, N, pos, F,
+                                                             make_consts<double>(a), a, 1.0 / (8.0 * kPi * ctx->p.eta),
+                                                             U);
+    count_launches(3);
+    return cuda_fail(cudaGetLastError(), "symmetric pair kernels");
+}
+
 template <bool TORQUE>
 __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__restrict__ src, int N, int chunk,
                                                                  PairConsts<double> c, double *__restrict__ part)
@@ -394,6 +656,7 @@ size_t pair_partial_bytes(int64_t max_N, int num_sms)
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, double *U)
 {
     const int N = (int)N64;
+    if (ctx->sym_enabled && F && !T && N >= 2 * kTile) return mobility_tt_sym(ctx, N, pos, F, U);
     cudaStream_t st = ctx->stream;
     const double a = ctx->p.a;
     int splits;

@@ -298,6 +298,70 @@ __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi
     }
 }
 
+// Both directions of a translation-translation pair block, two pairs per lane (packed float32x2).
+// Reciprocity of the mobility (M_ji = M_ij^T) lets one evaluation of the pair geometry serve the
+// target (u_i += M_ij F_j, accumulated) and the source (v_j = M_ij^T F_i, returned): the free-space
+// block is symmetric, and the transposed wall block swaps the roles of C and D.
+__device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 zi, float2 zj, float2 Fx, float2 Fy,
+                                            float2 Fz, float2 Gx, float2 Gy, float2 Gz, const X2Consts &c,
+                                            float2 &ux, float2 &uy, float2 &uz, float2 &vx, float2 &vy, float2 &vz)
+{
+    const float2 rz = sub2(zi, zj);
+    const float2 rho2 = fma2(rx, rx, mul2(ry, ry));
+    const float2 r2 = fma2(rz, rz, rho2);
+    const float2 inv_r = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 inv_r2 = mul2(inv_r, inv_r);
+    const float2 ir3 = mul2(inv_r, inv_r2);
+    float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
+    float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
+    float2 ct = ir3;
+    const bool n0 = r2.x < c.four_a2, n1 = r2.y < c.four_a2;
+    if (__any_sync(0xffffffffu, n0 || n1)) {
+        if (n0) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
+        if (n1) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
+    }
+    const float2 Rz = add2(zi, zj);
+    const float2 R2 = fma2(Rz, Rz, rho2);
+    const float2 invR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+    const float2 invR2 = mul2(invR, invR);
+    const float2 ez = mul2(Rz, invR);
+    const float2 t = mul2(zj, invR);
+    const float2 s = mul2(c.a2, invR2);
+    const float2 ez2 = mul2(ez, ez), t2 = mul2(t, t), et = mul2(ez, t), s2 = mul2(s, s);
+    const float2 d = sub2(t2, et);
+    const float2 A = fma2(s2, fma2(c.m10_3, ez2, c.c2_3), fma2(s, fma2(c.two, ez2, c.m2_3), fma2(c.two, d, c.m1)));
+    const float2 B = fma2(s2, fma2(c.c70_3, ez2, c.m10_3), fma2(s, fma2(c.m10, ez2, c.two), fma2(c.m6, d, c.m1)));
+    const float2 C = fma2(ez, fma2(s2, fma2(c.m140_3, ez2, c.c40_3), mul2(s, fma2(c.c20, ez2, c.m4))),
+                          mul2(t, fma2(c.c12, sub2(et, ez2), c.two)));
+    const float2 D = fma2(c.m20_3, mul2(s2, ez), add2(t, t));
+    const float2 E = fma2(s2, fma2(c.c20, ez2, c.m8_3), mul2(c.m4, fma2(s, ez2, t2)));
+    const float2 cF = fma2(A, invR, c1);
+    // target side: M_ij F_j
+    {
+        const float2 pF = fma2(rx, Fx, mul2(ry, Fy));
+        const float2 q = mul2(fma2(Rz, Fz, pF), invR);
+        const float2 k2 = mul2(c2, fma2(rz, Fz, pF));
+        const float2 ke = mul2(fma2(B, q, mul2(C, Fz)), invR2);
+        const float2 kz = mul2(fma2(D, q, mul2(E, Fz)), invR);
+        const float2 kk = add2(k2, ke);
+        ux = fma2(cF, Fx, fma2(kk, rx, ux));
+        uy = fma2(cF, Fy, fma2(kk, ry, uy));
+        uz = fma2(cF, Fz, fma2(k2, rz, fma2(ke, Rz, add2(uz, kz))));
+    }
+    // source side: M_ij^T F_i (C and D exchanged)
+    {
+        const float2 pF = fma2(rx, Gx, mul2(ry, Gy));
+        const float2 q = mul2(fma2(Rz, Gz, pF), invR);
+        const float2 k2 = mul2(c2, fma2(rz, Gz, pF));
+        const float2 ke = mul2(fma2(B, q, mul2(D, Gz)), invR2);
+        const float2 kz = mul2(fma2(C, q, mul2(E, Gz)), invR);
+        const float2 kk = add2(k2, ke);
+        vx = fma2(cF, Gx, mul2(kk, rx));
+        vy = fma2(cF, Gy, mul2(kk, ry));
+        vz = fma2(cF, Gz, fma2(k2, rz, fma2(ke, Rz, kz)));
+    }
+}
+
 __device__ __forceinline__ double H0(double x)
 {
     return x > 1.0 ? 1.0 : (x >= 0.0 ? x : 0.0);

@@ -79,6 +79,13 @@ struct Workspace {
     double *vec_f = nullptr;
     double *vec_g = nullptr;
     double *host_status = nullptr; // pinned host copy of the Lanczos status word
+    // symmetric translation-translation pass (float32 contexts): schedule, row and column partials
+    int *sym_index = nullptr;      // CTA table (4 ints each), row_cta, col_start
+    size_t sym_index_ints = 0;
+    double *sym_tgt = nullptr;
+    size_t sym_tgt_bytes = 0;
+    float *sym_src = nullptr;
+    int sym_N = -1, sym_ncta = 0, sym_row_off = 0, sym_col_off = 0;
 };
 
 }  // namespace rpb
@@ -91,6 +98,7 @@ struct rpb_ctx {
     int device;
     int num_sms;
     int fp32_variant;  // float32 pair kernel: 1 = packed float32x2 (default), 0 = scalar; env RPB_FP32_PAIR
+    int sym_enabled;   // float32 translation-translation products use the symmetric pass; env RPB_FP32_SYM=0 off
     rpb::Workspace ws;
 };
 
@@ -116,6 +124,9 @@ __global__ void pack_f64_kernel(const double *__restrict__ pos, const double *__
 // Number of column splits and chunk length the pair kernel uses for N targets.
 void pair_grid(int64_t N, int num_sms, int precision, int *splits, int64_t *chunk);
 size_t pair_partial_bytes(int64_t max_N, int num_sms);
+size_t sym_src_part_bytes(int64_t max_N);
+size_t sym_tgt_part_bytes(int64_t max_N, int num_sms);
+size_t sym_index_ints(int64_t max_N, int num_sms);
 
 int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_params *fp, double *F);
 int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t stream_id, uint32_t instance,

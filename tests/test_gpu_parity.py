@@ -93,6 +93,19 @@ def test_mobility_fp32(ctx32, N):
     assert maxrel(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("N", [256, 300, 1000, 4096])
+def test_mobility_fp32_translation_only(ctx32, N):
+    """F only (the Lanczos and RFD products): the float32 context evaluates each unordered pair once
+    and applies it both ways; same tolerance, and deterministic."""
+    pos = overlapping(N, 300 + N) if N < 4096 else inputs.monolayer(N, seed=1)
+    F = inputs.vectors(N, 7)
+    ref = O.mobility_apply(pos, F, None)
+    a = ctx32.mobility_apply(dev(pos), dev(F))
+    b = ctx32.mobility_apply(dev(pos), dev(F))
+    assert torch.equal(a, b)
+    assert maxrel(host(a, N), ref) <= 1e-5
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_mobility_n4096_full(ctx64, ctx32, prec):
     N = 4096
