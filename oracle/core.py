@@ -39,6 +39,10 @@ def lib():
         L.oracle_wall_image_tt.argtypes = [d, d, d, d, d, dp]
         L.oracle_wall_image_tr.argtypes = [d, d, d, d, d, dp]
         L.oracle_matvec_rows.argtypes = [i64, i64, i64, dp, dp, dp, d, d, dp]
+        L.oracle_matvec_rows_w.argtypes = [i64, i64, i64, dp, dp, dp, d, d, ctypes.c_int, dp]
+        L.oracle_matvec_rows_w.restype = None
+        L.oracle_dense_w.argtypes = [i64, dp, d, d, ctypes.c_int, dp, dp]
+        L.oracle_dense_w.restype = None
         L.oracle_matvec.argtypes = [i64, dp, dp, dp, d, d, dp]
         L.oracle_dense.argtypes = [i64, dp, d, d, dp, dp]
         L.oracle_forces.argtypes = [i64, dp, d, d, d, d, dp]
@@ -116,27 +120,28 @@ def wall_image_tr(x, y, a=1.0):
 
 
 # ---------------------------------------------------------------- matvec and dense
-def mobility_apply(pos, F=None, T=None, a=1.0, eta=1.0, rows=None):
+def mobility_apply(pos, F=None, T=None, a=1.0, eta=1.0, rows=None, wall=True):
     """U = M_tt F + M_tr T (Sec. II.B direct summation, Sec. III torque coupling); shape (N, 3).
 
-    rows=(i0, i1) restricts the output to targets i0..i1-1 (all N sources are summed)."""
+    rows=(i0, i1) restricts the output to targets i0..i1-1 (all N sources are summed).
+    wall=False: the unbounded-domain RPY mobility (no wall terms, no regularisation)."""
     pos = _c3(pos)
     N = pos.shape[0]
     Fc = None if F is None else _c3(F)
     Tc = None if T is None else _c3(T)
     i0, i1 = (0, N) if rows is None else rows
     U = np.zeros((i1 - i0, 3))
-    lib().oracle_matvec_rows(N, i0, i1, _p(pos), _p(Fc), _p(Tc), a, eta, _p(U))
+    lib().oracle_matvec_rows_w(N, i0, i1, _p(pos), _p(Fc), _p(Tc), a, eta, int(bool(wall)), _p(U))
     return U
 
 
-def dense(pos, a=1.0, eta=1.0):
-    """Dense (M_tt, M_tr), each 3N x 3N, particle-major rows/columns."""
+def dense(pos, a=1.0, eta=1.0, wall=True):
+    """Dense (M_tt, M_tr), each 3N x 3N, particle-major rows/columns (wall=False: unbounded domain)."""
     pos = _c3(pos)
     N = pos.shape[0]
     tt = np.zeros((3 * N, 3 * N))
     tr = np.zeros((3 * N, 3 * N))
-    lib().oracle_dense(N, _p(pos), a, eta, _p(tt), _p(tr))
+    lib().oracle_dense_w(N, _p(pos), a, eta, int(bool(wall)), _p(tt), _p(tr))
     return tt, tr
 
 
@@ -163,7 +168,7 @@ def _tridiag_sqrt_e1(alpha, beta):
     return Q @ (np.sqrt(lam) * Q[0, :])
 
 
-def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.0, matvec=None):
+def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.0, matvec=None, wall=True):
     """g_m ~ M_tt^{1/2} W by m steps of Lanczos with full reorthogonalisation.
 
     Readings where the paper is silent (it cites the Krylov method of Ando et al.):
@@ -183,7 +188,7 @@ def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.
     n = w0.size
     if matvec is None:
         def matvec(v):
-            return mobility_apply(pos, v.reshape(-1, 3), None, a, eta).ravel()
+            return mobility_apply(pos, v.reshape(-1, 3), None, a, eta, wall=wall).ravel()
     nW = float(np.sqrt(w0 @ w0))
     if nW == 0.0:
         return np.zeros_like(w0).reshape(-1, 3), 0, float("nan"), True

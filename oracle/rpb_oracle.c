@@ -94,23 +94,35 @@ static void freespace_tr(const double *xi, const double *xj, double a, double et
     M[2 * 3 + 1] = -c * e[0];
 }
 
-/* Regularised pair blocks M_ij = s_i s_j Mtilde(q~_i, q~_j), tt and tr (Appendix A). */
-void oracle_pair_blocks(const double *qi, const double *qj, int same, double a, double eta, double *Mtt,
-                        double *Mtr)
+/* Regularised pair blocks M_ij = s_i s_j Mtilde(q~_i, q~_j), tt and tr (Appendix A).
+ * wall == 0 is the unbounded-domain mobility (no image terms, no clamp, s = 1), used to compare the
+ * Lanczos convergence without the wall's screening (Sec. II.C, inset of Fig. 1). */
+void oracle_pair_blocks_w(const double *qi, const double *qj, int same, double a, double eta, int wall, double *Mtt,
+                          double *Mtr)
 {
-    double xi[3] = {qi[0], qi[1], fmax(qi[2], a)};
-    double xj[3] = {qj[0], qj[1], fmax(qj[2], a)};
-    double si = H0(qi[2] / a), sj = H0(qj[2] / a);
+    double xi[3] = {qi[0], qi[1], wall ? fmax(qi[2], a) : qi[2]};
+    double xj[3] = {qj[0], qj[1], wall ? fmax(qj[2], a) : qj[2]};
+    double si = wall ? H0(qi[2] / a) : 1.0, sj = wall ? H0(qj[2] / a) : 1.0;
     double ftt[9], ftr[9], wtt[9], wtr[9];
     freespace_tt(xi, xj, a, eta, same, ftt);
     freespace_tr(xi, xj, a, eta, same, ftr);
-    wall_image_tt(xi[0] - xj[0], xi[1] - xj[1], xi[2], xj[2], a, wtt);
-    wall_image_tr(xi[0] - xj[0], xi[1] - xj[1], xi[2], xj[2], a, wtr);
+    if (wall) {
+        wall_image_tt(xi[0] - xj[0], xi[1] - xj[1], xi[2], xj[2], a, wtt);
+        wall_image_tr(xi[0] - xj[0], xi[1] - xj[1], xi[2], xj[2], a, wtr);
+    } else {
+        memset(wtt, 0, sizeof(wtt));
+        memset(wtr, 0, sizeof(wtr));
+    }
     const double inv8pe = 1.0 / (8.0 * M_PI * eta);
     for (int k = 0; k < 9; ++k) {
         if (Mtt) Mtt[k] = si * sj * (ftt[k] + inv8pe * wtt[k]);
         if (Mtr) Mtr[k] = si * sj * (ftr[k] + inv8pe * wtr[k]);
     }
+}
+
+void oracle_pair_blocks(const double *qi, const double *qj, int same, double a, double eta, double *Mtt, double *Mtr)
+{
+    oracle_pair_blocks_w(qi, qj, same, a, eta, 1, Mtt, Mtr);
 }
 
 /* Unregularised pieces, exposed for the pins. */
@@ -136,15 +148,15 @@ void oracle_wall_image_tr(double rx, double ry, double zi, double zj, double a, 
 }
 
 /* U = M_tt F + M_tr T over targets [i0, i1) (all N sources).  F or T may be NULL. */
-void oracle_matvec_rows(int64_t N, int64_t i0, int64_t i1, const double *pos, const double *F,
-                        const double *T, double a, double eta, double *U)
+void oracle_matvec_rows_w(int64_t N, int64_t i0, int64_t i1, const double *pos, const double *F,
+                          const double *T, double a, double eta, int wall, double *U)
 {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = i0; i < i1; ++i) {
         double u[3] = {0.0, 0.0, 0.0};
         for (int64_t j = 0; j < N; ++j) {
             double Mtt[9], Mtr[9];
-            oracle_pair_blocks(&pos[3 * i], &pos[3 * j], i == j, a, eta, Mtt, Mtr);
+            oracle_pair_blocks_w(&pos[3 * i], &pos[3 * j], i == j, a, eta, wall, Mtt, Mtr);
             for (int p = 0; p < 3; ++p)
                 for (int q = 0; q < 3; ++q) {
                     if (F) u[p] += Mtt[3 * p + q] * F[3 * j + q];
@@ -155,27 +167,38 @@ void oracle_matvec_rows(int64_t N, int64_t i0, int64_t i1, const double *pos, co
     }
 }
 
+void oracle_matvec_rows(int64_t N, int64_t i0, int64_t i1, const double *pos, const double *F,
+                        const double *T, double a, double eta, double *U)
+{
+    oracle_matvec_rows_w(N, i0, i1, pos, F, T, a, eta, 1, U);
+}
+
 void oracle_matvec(int64_t N, const double *pos, const double *F, const double *T, double a, double eta,
                    double *U)
 {
-    oracle_matvec_rows(N, 0, N, pos, F, T, a, eta, U);
+    oracle_matvec_rows_w(N, 0, N, pos, F, T, a, eta, 1, U);
 }
 
 /* Dense 3N x 3N matrices (row-major, particle-major indices 3i+c). Either output may be NULL. */
-void oracle_dense(int64_t N, const double *pos, double a, double eta, double *Mtt, double *Mtr)
+void oracle_dense_w(int64_t N, const double *pos, double a, double eta, int wall, double *Mtt, double *Mtr)
 {
     const int64_t n3 = 3 * N;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < N; ++i)
         for (int64_t j = 0; j < N; ++j) {
             double btt[9], btr[9];
-            oracle_pair_blocks(&pos[3 * i], &pos[3 * j], i == j, a, eta, btt, btr);
+            oracle_pair_blocks_w(&pos[3 * i], &pos[3 * j], i == j, a, eta, wall, btt, btr);
             for (int p = 0; p < 3; ++p)
                 for (int q = 0; q < 3; ++q) {
                     if (Mtt) Mtt[(3 * i + p) * n3 + 3 * j + q] = btt[3 * p + q];
                     if (Mtr) Mtr[(3 * i + p) * n3 + 3 * j + q] = btr[3 * p + q];
                 }
         }
+}
+
+void oracle_dense(int64_t N, const double *pos, double a, double eta, double *Mtt, double *Mtr)
+{
+    oracle_dense_w(N, pos, a, eta, 1, Mtt, Mtr);
 }
 
 /* -dU/dr for the soft potential of Eq. (soft_potential): U0/b on r < d, (U0/b) exp(-(r-d)/b) above. */

@@ -97,3 +97,19 @@ def test_single_roller_rolls():
     U = O.mobility_apply(np.array([[0.0, 0.0, 1.5]]), None, np.array([[0.0, 1.0, 0.0]]))
     assert U[0, 0] > 0 and U[0, 1] == 0 and U[0, 2] == 0
     assert math.isclose(U[0, 0], MU0 * 3 / (32 * 1.5**4), rel_tol=1e-14)
+
+
+def test_unbounded_mode():
+    """wall=False is the free-space RPY mobility (Sec. II.C compares Lanczos with and without the
+    wall): blocks equal the free-space ones, no clamp or H0, SPD."""
+    pos = _overlapping(20, 77)
+    tt, tr = O.dense(pos, wall=False)
+    for i, j in [(0, 1), (3, 3), (5, 12)]:
+        ref = O.freespace_tt(pos[i], pos[j], 1.0, 1.0, same=(i == j))
+        assert np.allclose(tt[3 * i:3 * i + 3, 3 * j:3 * j + 3], ref, rtol=0, atol=1e-17)
+        reft = O.freespace_tr(pos[i], pos[j], 1.0, 1.0, same=(i == j))
+        assert np.allclose(tr[3 * i:3 * i + 3, 3 * j:3 * j + 3], reft, rtol=0, atol=1e-17)
+    assert np.linalg.eigvalsh(tt).min() > 0
+    F = vectors(20, 3)
+    assert np.allclose(O.mobility_apply(pos, F, None, wall=False).ravel(), tt @ F.ravel(), rtol=0,
+                       atol=1e-14 * np.abs(tt @ F.ravel()).max())
