@@ -231,14 +231,19 @@ def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.
 
 
 # ---------------------------------------------------------------- RFD (Sec. II.A)
-def rfd_drift(pos, Wt, delta=1e-6, kT=1.0, a=1.0, eta=1.0, parts=False):
+def rfd_drift(pos, Wt, delta=1e-6, kT=1.0, a=1.0, eta=1.0, parts=False, one_sided=False):
     """(kT/delta)[M_tt(q + delta/2 W~) W~ - M_tt(q - delta/2 W~) W~]; the displaced configurations
     are regularised anew (clamp and H0 at the displaced heights).  parts=True also returns the two
-    matvecs."""
+    matvecs.  one_sided=True: (kT/delta)[M_tt(q + delta W~) W~ - M_tt(q) W~], the one-sided
+    difference Sec. II.A mentions."""
     pos = _c3(pos)
     Wt = _c3(Wt)
-    up = mobility_apply(pos + 0.5 * delta * Wt, Wt, None, a, eta)
-    um = mobility_apply(pos - 0.5 * delta * Wt, Wt, None, a, eta)
+    if one_sided:
+        up = mobility_apply(pos + delta * Wt, Wt, None, a, eta)
+        um = mobility_apply(pos, Wt, None, a, eta)
+    else:
+        up = mobility_apply(pos + 0.5 * delta * Wt, Wt, None, a, eta)
+        um = mobility_apply(pos - 0.5 * delta * Wt, Wt, None, a, eta)
     d = (kT / delta) * (up - um)
     if parts:
         return d, up, um
@@ -254,12 +259,15 @@ def noise(N, seed, step, stream, instance=0):
 
 # ---------------------------------------------------------------- AB step (Eq. AB)
 def ab_step(pos, U_prev, step, seed, dt=0.01, delta=1e-6, tol=1e-3, max_iter=100, kT=1.0, a=1.0, eta=1.0,
-            weight=1.0, torque=(0.0, 1.0, 0.0), U0=1.0, b=0.1, exact_iters=None, detail=False):
-    """One stochastic Adams-Bashforth step.
+            weight=1.0, torque=(0.0, 1.0, 0.0), U0=1.0, b=0.1, exact_iters=None, detail=False, scheme="AB",
+            one_sided=False):
+    """One stochastic Adams-Bashforth step (scheme="AB", Eq. AB) or Euler-Maruyama step
+    (scheme="EM", Eq. EM: q^{n+1} = q^n + dt U^n + sqrt(2 kT dt) g + dt drift).
 
     Readings: the deterministic velocity U^n = M_tt F^n + M_tr T (Sec. III: M_C T is treated like
-    M F); the first step (step == 0, no U^{n-1}) is Euler-Maruyama, i.e. U^{-1} := U^0; the torque is
-    the same constant vector on every particle.  Returns (q^{n+1}, U^n, info)."""
+    M F); the first AB step (step == 0, no U^{n-1}) is Euler-Maruyama, i.e. U^{-1} := U^0; the torque
+    is the same constant vector on every particle.  one_sided selects the one-sided RFD.
+    Returns (q^{n+1}, U^n, info)."""
     pos = _c3(pos)
     N = pos.shape[0]
     F = forces(pos, a, weight, U0, b)
@@ -268,8 +276,8 @@ def ab_step(pos, U_prev, step, seed, dt=0.01, delta=1e-6, tol=1e-3, max_iter=100
     W = noise(N, seed, step, 0)
     Wt = noise(N, seed, step, 1)
     g, m, eps, conv = lanczos_sqrt(pos, W, tol, max_iter, exact_iters, a, eta)
-    d, up, um = rfd_drift(pos, Wt, delta, kT, a, eta, parts=True)
-    Up = Un if (step == 0 or U_prev is None) else _c3(U_prev)
+    d, up, um = rfd_drift(pos, Wt, delta, kT, a, eta, parts=True, one_sided=one_sided)
+    Up = Un if (scheme == "EM" or step == 0 or U_prev is None) else _c3(U_prev)
     new = pos + dt * (1.5 * Un - 0.5 * Up) + math.sqrt(2.0 * kT * dt) * g + dt * d
     info = dict(m=m, eps=eps, converged=conv)
     if detail:

@@ -90,3 +90,44 @@ def test_ab_step_composition():
     g0, _, _, _ = O.lanczos_sqrt(pos, O.noise(3, 9, 0, 0), tol=1e-3)
     d0 = O.rfd_drift(pos, O.noise(3, 9, 0, 1), delta=1e-6)
     assert np.allclose(new0, pos + 0.01 * Un0 + math.sqrt(0.02) * g0 + 0.01 * d0, rtol=0, atol=1e-15)
+
+
+def test_em_deterministic_first_order():
+    """kT = 0: Euler-Maruyama is first order in dt (AB is second order, test above)."""
+    from scipy.integrate import solve_ivp
+
+    q0 = np.array([[0.0, 0.0, 1.5], [4.0, 1.0, 1.2]])
+    t_end = 0.4
+
+    def rhs(t, y):
+        return _det_velocity(y.reshape(-1, 3)).ravel()
+
+    ref = solve_ivp(rhs, (0, t_end), q0.ravel(), method="DOP853", rtol=1e-13, atol=1e-14).y[:, -1]
+    errs = []
+    for nsteps in (20, 40, 80):
+        dt = t_end / nsteps
+        q, Up = q0.copy(), None
+        for n in range(nsteps):
+            q, Up, _ = O.ab_step(q, Up, n, seed=0, dt=dt, kT=0.0, scheme="EM")
+        errs.append(np.linalg.norm(q.ravel() - ref))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.7 < r1 < 2.3 and 1.8 < r2 < 2.2, errs
+
+
+@pytest.mark.parametrize("h", [1.2, 2.0])
+def test_one_sided_rfd_first_order(h):
+    """One-sided difference: derivative with an O(delta) error, halving with delta."""
+    q = np.array([[0.1, 0.0, h]])
+    e = np.array([[0.0, 0.0, 1.0]])
+    errs = [abs(O.rfd_drift(q, e, delta=dl, one_sided=True)[0, 2] - dmuzz_dz(h)) for dl in (2e-3, 1e-3)]
+    assert 1.8 < errs[0] / errs[1] < 2.2
+    assert errs[1] < 1e-2 * abs(dmuzz_dz(h))
+
+
+def test_em_step_composition():
+    pos = np.array([[0.0, 0.0, 1.5], [2.5, 0.0, 1.3], [0.7, 2.4, 2.0]])
+    Uprev = np.full((3, 3), 0.37)
+    new, Un, info = O.ab_step(pos, Uprev, 4, seed=2, dt=0.02, scheme="EM", one_sided=True)
+    g, _, _, _ = O.lanczos_sqrt(pos, O.noise(3, 2, 4, 0), tol=1e-3)
+    d = O.rfd_drift(pos, O.noise(3, 2, 4, 1), delta=1e-6, one_sided=True)
+    assert np.allclose(new, pos + 0.02 * Un + math.sqrt(0.04) * g + 0.02 * d, rtol=0, atol=1e-15)
