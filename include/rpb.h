@@ -55,6 +55,10 @@ typedef struct {
     double eta;      /* viscosity (> 0) */
     double kT;       /* thermal energy (>= 0) */
     int precision;   /* RPB_FP64 or RPB_FP32 */
+    int wall;        /* 1: wall-corrected mobility with the regularisation of Appendix A (the method);
+                        0: unbounded-domain RPY mobility (no image terms, no clamp, H0 = 1), for the
+                        comparison of Sec. II.C without the wall's screening.  Batch contexts and
+                        rpb_mobility_apply_noalloc accept only 1. */
 } rpb_params;
 
 /* Deterministic forcing of Sec. III: gravity -weight z_hat on every sphere, the soft steric
@@ -134,6 +138,24 @@ int rpb_philox_normal(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uin
 int rpb_ab_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed,
                 double dt, double delta, double tol, int max_iter, const rpb_force_params *fp,
                 rpb_step_stats *stats);
+
+/* Integrator and drift variants of rpb_step. */
+#define RPB_SCHEME_AB 0       /* stochastic Adams-Bashforth, Eq. (AB) */
+#define RPB_SCHEME_EM 1       /* Euler-Maruyama, Eq. (EM) */
+#define RPB_RFD_CENTRED 0     /* (kT/delta)[M(q + delta/2 W~) W~ - M(q - delta/2 W~) W~], Sec. II.A */
+#define RPB_RFD_ONE_SIDED 1   /* (kT/delta)[M(q + delta W~) W~ - M(q) W~], the one-sided difference Sec. II.A
+                                 mentions (truncation error O(delta) instead of O(delta^2)) */
+typedef struct {
+    int scheme;   /* RPB_SCHEME_AB or RPB_SCHEME_EM */
+    int rfd;      /* RPB_RFD_CENTRED or RPB_RFD_ONE_SIDED */
+} rpb_step_options;
+
+/* One time step as rpb_ab_step, with the integrator and the drift's difference chosen by opts
+ * (NULL = Adams-Bashforth with the centred difference, i.e. rpb_ab_step).  Euler-Maruyama
+ * (Eq. EM): q <- q + dt U^n + sqrt(2 kT dt) g + dt drift; U_prev is still set to U^n. */
+int rpb_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed, double dt,
+             double delta, double tol, int max_iter, const rpb_force_params *fp, const rpb_step_options *opts,
+             rpb_step_stats *stats);
 
 /* Message for the calling thread's most recent failed call ("" if none). */
 const char *rpb_last_error(void);

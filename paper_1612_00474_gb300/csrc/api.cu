@@ -104,8 +104,10 @@ int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, 
         return RPB_EINVAL;
     }
     *out = nullptr;
-    if (!(p->a > 0.0) || !(p->eta > 0.0) || !(p->kT >= 0.0) || (p->precision != RPB_FP64 && p->precision != RPB_FP32)) {
-        set_error("bad parameters (a=%g eta=%g kT=%g precision=%d)", p->a, p->eta, p->kT, p->precision);
+    if (!(p->a > 0.0) || !(p->eta > 0.0) || !(p->kT >= 0.0) || (p->precision != RPB_FP64 && p->precision != RPB_FP32) ||
+        (p->wall != 0 && p->wall != 1)) {
+        set_error("bad parameters (a=%g eta=%g kT=%g precision=%d wall=%d)", p->a, p->eta, p->kT, p->precision,
+                  p->wall);
         return RPB_EINVAL;
     }
     if (max_N <= 0 || max_N > (int64_t)1 << 28) {
@@ -310,8 +312,21 @@ int rpb_philox_normal(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uin
 int rpb_ab_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed, double dt,
                 double delta, double tol, int max_iter, const rpb_force_params *fp, rpb_step_stats *stats)
 {
+    return rpb_step(ctx, N, pos, U_prev, step, seed, dt, delta, tol, max_iter, fp, nullptr, stats);
+}
+
+int rpb_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed, double dt,
+             double delta, double tol, int max_iter, const rpb_force_params *fp, const rpb_step_options *opts,
+             rpb_step_stats *stats)
+{
     g_err[0] = 0;
     int rc;
+    const int scheme = opts ? opts->scheme : RPB_SCHEME_AB;
+    const int rfd = opts ? opts->rfd : RPB_RFD_CENTRED;
+    if ((scheme != RPB_SCHEME_AB && scheme != RPB_SCHEME_EM) || (rfd != RPB_RFD_CENTRED && rfd != RPB_RFD_ONE_SIDED)) {
+        set_error("bad step options (scheme=%d rfd=%d)", scheme, rfd);
+        return RPB_EINVAL;
+    }
     if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(U_prev, "U_prev", false)))
         return rc;
     if (!fp || !(fp->b > 0.0) || !(dt > 0.0) || !(delta > 0.0) || step < 0 || step > 0xffffffffLL) {
@@ -337,9 +352,11 @@ int rpb_ab_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t st
     double err = -1.0;
     const int lrc = lanczos_impl(ctx, N, pos, W, g, tol, max_iter, &iters, &err, &conv);
     if (lrc != RPB_OK && lrc != RPB_ENOCONV) return lrc;
-    if ((rc = rfd_impl(ctx, N, pos, Wt, delta, drift))) return rc;
+    if ((rc = rfd_impl(ctx, N, pos, Wt, delta, drift, rfd == RPB_RFD_ONE_SIDED))) return rc;
     const double noise = sqrt(2.0 * ctx->p.kT * dt);
-    if ((rc = ab_update_impl(ctx, N, pos, U_prev, Un, g, drift, dt, noise, step == 0 ? 1 : 0))) return rc;
+    // Euler-Maruyama is the update with U^{n-1} := U^n (Eq. EM); AB uses that only on the first step
+    const int em = scheme == RPB_SCHEME_EM || step == 0;
+    if ((rc = ab_update_impl(ctx, N, pos, U_prev, Un, g, drift, dt, noise, em))) return rc;
     if (stats) {
         stats->lanczos_iters = iters;
         stats->lanczos_err = err;

@@ -666,7 +666,7 @@ static int batch_product(rpb_batch *bt, const double *pos, const double *F, cons
     const int gpack = (int)((total + pb - 1) / pb);
     if (bt->p.precision == RPB_FP32) {
         SrcF32 *src = (SrcF32 *)bt->src;
-        pack_f32_kernel<<<gpack, pb, 0, bt->stream>>>(pos, F, T, (int)total, a, src);
+        pack_f32_kernel<<<gpack, pb, 0, bt->stream>>>(pos, F, T, (int)total, a, 1, src);
         const X2Consts c = make_x2_consts(a);
         const PairConsts<double> cd = make_consts<double>(a);
         if (T)
@@ -677,7 +677,7 @@ static int batch_product(rpb_batch *bt, const double *pos, const double *F, cons
                 src, bt->d_inst, bt->d_blocks, active, total, c, cd, a, scale, pos, F, T, U);
     } else {
         SrcF64 *src = (SrcF64 *)bt->src;
-        pack_f64_kernel<<<gpack, pb, 0, bt->stream>>>(pos, F, T, (int)total, a, src);
+        pack_f64_kernel<<<gpack, pb, 0, bt->stream>>>(pos, F, T, (int)total, a, 1, src);
         const PairConsts<double> c = make_consts<double>(a);
         if (T)
             batch_pair_f64_kernel<true><<<bt->nblocks, kPairThreads, 0, bt->stream>>>(
@@ -751,8 +751,9 @@ int rpb_batch_create(rpb_batch **out, const rpb_params *p, int64_t max_total_N, 
         return RPB_EINVAL;
     }
     *out = nullptr;
-    if (!(p->a > 0.0) || !(p->eta > 0.0) || !(p->kT >= 0.0) || (p->precision != RPB_FP64 && p->precision != RPB_FP32)) {
-        set_error("bad parameters");
+    if (!(p->a > 0.0) || !(p->eta > 0.0) || !(p->kT >= 0.0) || (p->precision != RPB_FP64 && p->precision != RPB_FP32) ||
+        p->wall != 1) {
+        set_error("bad parameters (batch contexts need precision RPB_FP64/RPB_FP32 and wall = 1)");
         return RPB_EINVAL;
     }
     if (max_total_N <= 0 || max_total_N > (int64_t)1 << 28 || max_B < 1 || max_B > (1 << 20) || max_iter < 1 ||

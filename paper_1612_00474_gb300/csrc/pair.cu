@@ -33,16 +33,16 @@ namespace rpb {
 
 // ------------------------------------------------------------------ packing
 __global__ void pack_f32_kernel(const double *__restrict__ pos, const double *__restrict__ F,
-                                const double *__restrict__ T, int N, double a, SrcF32 *__restrict__ out)
+                                const double *__restrict__ T, int N, double a, int wall, SrcF32 *__restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double x = pos[i], y = pos[N + i], z = pos[2 * N + i];
-    const double s = H0(z / a);
+    const double s = wall ? H0(z / a) : 1.0;
     const float xh = (float)x, yh = (float)y;
     SrcF32 o;
     o.p = make_float4(xh, yh, (float)(x - (double)xh), (float)(y - (double)yh));
-    o.f = make_float4((float)fmax(z, a), F ? (float)(s * F[i]) : 0.f, F ? (float)(s * F[N + i]) : 0.f,
+    o.f = make_float4((float)(wall ? fmax(z, a) : z), F ? (float)(s * F[i]) : 0.f, F ? (float)(s * F[N + i]) : 0.f,
                       F ? (float)(s * F[2 * N + i]) : 0.f);
     o.t = make_float4(T ? (float)(s * T[i]) : 0.f, T ? (float)(s * T[N + i]) : 0.f, T ? (float)(s * T[2 * N + i]) : 0.f,
                       0.f);
@@ -50,15 +50,15 @@ __global__ void pack_f32_kernel(const double *__restrict__ pos, const double *__
 }
 
 __global__ void pack_f64_kernel(const double *__restrict__ pos, const double *__restrict__ F,
-                                const double *__restrict__ T, int N, double a, SrcF64 *__restrict__ out)
+                                const double *__restrict__ T, int N, double a, int wall, SrcF64 *__restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double z = pos[2 * N + i];
-    const double s = H0(z / a);
+    const double s = wall ? H0(z / a) : 1.0;
     SrcF64 o;
     o.p = make_double2(pos[i], pos[N + i]);
-    o.q = make_double2(fmax(z, a), F ? s * F[i] : 0.0);
+    o.q = make_double2(wall ? fmax(z, a) : z, F ? s * F[i] : 0.0);
     o.r = make_double2(F ? s * F[N + i] : 0.0, F ? s * F[2 * N + i] : 0.0);
     o.s = make_double2(T ? s * T[i] : 0.0, T ? s * T[N + i] : 0.0);
     o.u = make_double2(T ? s * T[2 * N + i] : 0.0, 0.0);
@@ -69,7 +69,7 @@ __global__ void pack_f64_kernel(const double *__restrict__ pos, const double *__
 // grid = (ceil(N/128), splits); block (bx, by) covers targets [128 bx, 128 bx + 128) and sources
 // [by chunk, (by + 1) chunk); chunk is a multiple of 128, so the tile holding the block's own
 // targets (where j == i can occur) is the one starting at 128 bx.
-template <bool TORQUE>
+template <bool TORQUE, bool WALL = true>
 __global__ void __launch_bounds__(kPairThreads) pair_f32_kernel(const SrcF32 *__restrict__ src, int N, int chunk,
                                                                  PairConsts<float> c, double *__restrict__ part)
 {
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32_kernel(const SrcF32 *__
                 const float4 q = TORQUE ? st[k] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float rx = (tp.x - p.x) + (tp.z - p.z);
                 const float ry = (tp.y - p.y) + (tp.w - p.w);
-                pair_velocity_f32<TORQUE>(rx, ry, tz, f.x, f.y, f.z, f.w, q.x, q.y, q.z, c, ux, uy, uz);
+                pair_velocity_f32<TORQUE, WALL>(rx, ry, tz, f.x, f.y, f.z, f.w, q.x, q.y, q.z, c, ux, uy, uz);
             }
         } else {
             for (int k = 0; k < cnt; ++k) {
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32_kernel(const SrcF32 *__
                 const float rx = (tp.x - p.x) + (tp.z - p.z);
                 const float ry = (tp.y - p.y) + (tp.w - p.w);
                 float dx = 0.f, dy = 0.f, dz = 0.f;
-                pair_velocity_f32<TORQUE>(rx, ry, tz, f.x, f.y, f.z, f.w, q.x, q.y, q.z, c, dx, dy, dz);
+                pair_velocity_f32<TORQUE, WALL>(rx, ry, tz, f.x, f.y, f.z, f.w, q.x, q.y, q.z, c, dx, dy, dz);
                 if (k != tid) {
                     ux += dx;
                     uy += dy;
@@ -520,7 +520,7 @@ static int mobility_tt_sym(rpb_ctx *ctx, int N, const double *pos, const double 
     const double a = ctx->p.a;
     SrcF32 *src = (SrcF32 *)w.src;
     const int pb = 256;
-    pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, nullptr, N, a, src);
+    pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, nullptr, N, a, 1, src);
     pair_f32x2_sym_kernel<<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, (const SymCta *)w.sym_index, make_x2_consts(a),
                                                                w.sym_index + w.sym_col_off, w.sym_tgt, w.sym_src);
     pair_sym_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
@@ -531,7 +531,7 @@ static int mobility_tt_sym(rpb_ctx *ctx, int N, const double *pos, const double 
     return cuda_fail(cudaGetLastError(), "symmetric pair kernels");
 }
 
-template <bool TORQUE>
+template <bool TORQUE, bool WALL = true>
 __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__restrict__ src, int N, int chunk,
                                                                  PairConsts<double> c, double *__restrict__ part)
 {
@@ -571,8 +571,8 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
                 const double2 p = sp[k], q = sq[k], r = sr[k];
                 const double2 s = TORQUE ? ss[k] : make_double2(0.0, 0.0);
                 const double2 u = TORQUE ? su[k] : make_double2(0.0, 0.0);
-                pair_velocity<double, TORQUE>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c, ux, uy,
-                                              uz);
+                pair_velocity<double, TORQUE, WALL>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c,
+                                                    ux, uy, uz);
             }
         } else {
             for (int k = 0; k < cnt; ++k) {
@@ -580,8 +580,8 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
                 const double2 s = TORQUE ? ss[k] : make_double2(0.0, 0.0);
                 const double2 u = TORQUE ? su[k] : make_double2(0.0, 0.0);
                 double dx = 0.0, dy = 0.0, dz = 0.0;
-                pair_velocity<double, TORQUE>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c, dx, dy,
-                                              dz);
+                pair_velocity<double, TORQUE, WALL>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c,
+                                                    dx, dy, dz);
                 if (k != tid) {
                     ux += dx;
                     uy += dy;
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
 // Sum the chunk partials in order, add the float64 self term, apply s_i / (8 pi eta).
 __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, int N, const double *__restrict__ pos,
                                    const double *__restrict__ F, const double *__restrict__ T, PairConsts<double> c,
-                                   double a, double scale, double *__restrict__ U)
+                                   double a, double scale, double *__restrict__ U, int wall = 1)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -614,15 +614,14 @@ __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, 
         uz += part[o + 2 * N + i];
     }
     const double z = pos[2 * N + i];
-    const double si = H0(z / a);
-    const double zc = fmax(z, a);
+    const double si = wall ? H0(z / a) : 1.0;
+    const double zc = wall ? fmax(z, a) : z;
     const double Fx = F ? si * F[i] : 0.0, Fy = F ? si * F[N + i] : 0.0, Fz = F ? si * F[2 * N + i] : 0.0;
-    if (T) {
-        pair_velocity<double, true>(0.0, 0.0, zc, zc, Fx, Fy, Fz, si * T[i], si * T[N + i], si * T[2 * N + i], c, ux,
-                                    uy, uz);
-    } else {
-        pair_velocity<double, false>(0.0, 0.0, zc, zc, Fx, Fy, Fz, 0.0, 0.0, 0.0, c, ux, uy, uz);
-    }
+    const double Tx = T ? si * T[i] : 0.0, Ty = T ? si * T[N + i] : 0.0, Tz = T ? si * T[2 * N + i] : 0.0;
+    if (wall)
+        pair_velocity<double, true, true>(0.0, 0.0, zc, zc, Fx, Fy, Fz, Tx, Ty, Tz, c, ux, uy, uz);
+    else
+        pair_velocity<double, true, false>(0.0, 0.0, zc, zc, Fx, Fy, Fz, Tx, Ty, Tz, c, ux, uy, uz);
     const double k = si * scale;
     U[i] = k * ux;
     U[N + i] = k * uy;
@@ -656,7 +655,7 @@ size_t pair_partial_bytes(int64_t max_N, int num_sms)
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, double *U)
 {
     const int N = (int)N64;
-    if (ctx->sym_enabled && F && !T && N >= 2 * kTile) return mobility_tt_sym(ctx, N, pos, F, U);
+    if (ctx->sym_enabled && ctx->p.wall && F && !T && N >= 2 * kTile) return mobility_tt_sym(ctx, N, pos, F, U);
     cudaStream_t st = ctx->stream;
     const double a = ctx->p.a;
     int splits;
@@ -672,8 +671,14 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
     const bool torque = T != nullptr;
     if (ctx->p.precision == RPB_FP32) {
         SrcF32 *src = (SrcF32 *)ctx->ws.src;
-        pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, src);
-        if (ctx->fp32_variant == 1) {
+        pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, ctx->p.wall, src);
+        if (!ctx->p.wall) {
+            const PairConsts<float> c = make_consts<float>(a);
+            if (torque)
+                pair_f32_kernel<true, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+            else
+                pair_f32_kernel<false, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+        } else if (ctx->fp32_variant == 1) {
             const X2Consts c = make_x2_consts(a);
             if (torque)
                 pair_f32x2_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
@@ -688,16 +693,22 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
         }
     } else {
         SrcF64 *src = (SrcF64 *)ctx->ws.src;
-        pack_f64_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, src);
+        pack_f64_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, ctx->p.wall, src);
         const PairConsts<double> c = make_consts<double>(a);
-        if (torque)
+        if (!ctx->p.wall) {
+            if (torque)
+                pair_f64_kernel<true, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+            else
+                pair_f64_kernel<false, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+        } else if (torque) {
             pair_f64_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
-        else
+        } else {
             pair_f64_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
+        }
     }
     const PairConsts<double> cd = make_consts<double>(a);
     pair_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(part, splits, N, pos, F, T, cd, a,
-                                                          1.0 / (8.0 * kPi * ctx->p.eta), U);
+                                                          1.0 / (8.0 * kPi * ctx->p.eta), U, ctx->p.wall);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "pair kernels");
 }
@@ -822,8 +833,9 @@ extern "C" int rpb_mobility_apply_noalloc(int64_t N64, const double *pos, const 
                                           const rpb_params *p, void *stream)
 {
     using namespace rpb;
-    if (!p || !(p->a > 0.0) || !(p->eta > 0.0) || (p->precision != RPB_FP64 && p->precision != RPB_FP32)) {
-        set_error("rpb_mobility_apply_noalloc: missing or bad parameters");
+    if (!p || !(p->a > 0.0) || !(p->eta > 0.0) || (p->precision != RPB_FP64 && p->precision != RPB_FP32) ||
+        p->wall != 1) {
+        set_error("rpb_mobility_apply_noalloc: missing or bad parameters (wall must be 1)");
         return RPB_EINVAL;
     }
     if (N64 <= 0 || N64 > RPB_NOALLOC_MAX_N) {
@@ -866,7 +878,7 @@ extern "C" int rpb_mobility_apply_noalloc(int64_t N64, const double *pos, const 
     const double a = p->a;
     if (p->precision == RPB_FP32) {
         SrcF32 *src = (SrcF32 *)base;
-        pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, src);
+        pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, 1, src);
         const PairConsts<float> c = make_consts<float>(a);
         if (T)
             pair_f32_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
@@ -874,7 +886,7 @@ extern "C" int rpb_mobility_apply_noalloc(int64_t N64, const double *pos, const 
             pair_f32_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
     } else {
         SrcF64 *src = (SrcF64 *)base;
-        pack_f64_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, src);
+        pack_f64_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, 1, src);
         const PairConsts<double> c = make_consts<double>(a);
         if (T)
             pair_f64_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);

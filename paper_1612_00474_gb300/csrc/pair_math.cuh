@@ -33,7 +33,7 @@ __device__ __forceinline__ double rsq<double>(double x)
 // Velocity of the target from one source, in units of 1/(8 pi eta), before the target's s_i.
 // rx, ry: in-plane offset target - source; zi, zj: clamped heights; F, T: source force and torque
 // with s_j folded in.  Accumulates into (ux, uy, uz).  Valid for r = 0 (self pair: mu0 F + wall).
-template <typename R, bool TORQUE>
+template <typename R, bool TORQUE, bool WALL = true>
 __device__ __forceinline__ void pair_velocity(R rx, R ry, R zi, R zj, R Fx, R Fy, R Fz, R Tx, R Ty, R Tz,
                                               const PairConsts<R> &c, R &ux, R &uy, R &uz)
 {
@@ -57,6 +57,7 @@ __device__ __forceinline__ void pair_velocity(R rx, R ry, R zi, R zj, R Fx, R Fy
         uy += ct * (Tz * rx - Tx * rz);
         uz += ct * (Tx * ry - Ty * rx);
     }
+    if (!WALL) return;  // unbounded domain: free-space RPY only
     // ---- wall correction (image of the source below z = 0)
     const R Rz = zi + zj;
     const R invR = rsq<R>(rho2 + Rz * Rz);
@@ -96,7 +97,7 @@ __device__ __forceinline__ void pair_velocity(R rx, R ry, R zi, R zj, R Fx, R Fy
 // share one multiply-add into F, r.F and R.F share their in-plane part, the free-space rotlet
 // c_t T x r and the wall's -|R|^-3 T x R share their z component, and the overlap branch (r < 2a,
 // rare) is evaluated only when some lane of the warp needs it.  Must be called by all 32 lanes.
-template <bool TORQUE>
+template <bool TORQUE, bool WALL = true>
 __device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, float zj, float Fx, float Fy,
                                                   float Fz, float Tx, float Ty, float Tz, const PairConsts<float> &c,
                                                   float &ux, float &uy, float &uz)
@@ -120,6 +121,18 @@ __device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, 
             c2 = c.near_c2 * ir;
             ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
         }
+    }
+    if (!WALL) {  // unbounded domain: free-space RPY only
+        const float k2 = c2 * fmaf(rz, Fz, fmaf(rx, Fx, ry * Fy));
+        ux = fmaf(c1, Fx, fmaf(k2, rx, ux));
+        uy = fmaf(c1, Fy, fmaf(k2, ry, uy));
+        uz = fmaf(c1, Fz, fmaf(k2, rz, uz));
+        if (TORQUE) {
+            ux = fmaf(ct, Ty * rz - Tz * ry, ux);
+            uy = fmaf(ct, Tz * rx - Tx * rz, uy);
+            uz = fmaf(ct, Tx * ry - Ty * rx, uz);
+        }
+        return;
     }
     // ---- wall correction
     const float Rz = zi + zj;

@@ -117,9 +117,9 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double
 
 // Packed source records from float64 SoA inputs (pair.cu); also used by the batched path.
 __global__ void pack_f32_kernel(const double *__restrict__ pos, const double *__restrict__ F,
-                                const double *__restrict__ T, int N, double a, SrcF32 *__restrict__ out);
+                                const double *__restrict__ T, int N, double a, int wall, SrcF32 *__restrict__ out);
 __global__ void pack_f64_kernel(const double *__restrict__ pos, const double *__restrict__ F,
-                                const double *__restrict__ T, int N, double a, SrcF64 *__restrict__ out);
+                                const double *__restrict__ T, int N, double a, int wall, SrcF64 *__restrict__ out);
 
 // Number of column splits and chunk length the pair kernel uses for N targets.
 void pair_grid(int64_t N, int num_sms, int precision, int *splits, int64_t *chunk);
@@ -133,7 +133,8 @@ int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t 
                 double *out);
 int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol, int max_iter,
                  int *iters_out, double *err_out, int *converged_out);
-int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift);
+int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift,
+             int one_sided = 0);
 int ab_update_impl(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, const double *Un, const double *g,
                    const double *drift, double dt, double noise_scale, int first);
 

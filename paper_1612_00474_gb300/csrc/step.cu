@@ -82,16 +82,18 @@ static int elem_grid(int64_t n, int num_sms)
     return g < 1 ? 1 : (int)g;
 }
 
-int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift)
+int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift, int one_sided)
 {
     const int64_t n = 3 * N;
     const int G = elem_grid(n, ctx->num_sms);
-    displace_kernel<<<G, 256, 0, ctx->stream>>>(pos, Wt, n, 0.5 * delta, ctx->ws.pos_a, ctx->ws.pos_b);
+    // centred: q +- delta/2 W~; one-sided: q + delta W~ and q itself
+    displace_kernel<<<G, 256, 0, ctx->stream>>>(pos, Wt, n, one_sided ? delta : 0.5 * delta, ctx->ws.pos_a,
+                                                ctx->ws.pos_b);
     count_launches(1);
     int rc;
     if ((rc = cuda_fail(cudaGetLastError(), "rfd displace"))) return rc;
     if ((rc = mobility_apply_impl(ctx, N, ctx->ws.pos_a, Wt, nullptr, drift))) return rc;
-    if ((rc = mobility_apply_impl(ctx, N, ctx->ws.pos_b, Wt, nullptr, ctx->ws.w))) return rc;
+    if ((rc = mobility_apply_impl(ctx, N, one_sided ? pos : ctx->ws.pos_b, Wt, nullptr, ctx->ws.w))) return rc;
     rfd_combine_kernel<<<G, 256, 0, ctx->stream>>>(drift, ctx->ws.w, n, ctx->p.kT / delta);
     count_launches(1);
     return cuda_fail(cudaGetLastError(), "rfd combine");

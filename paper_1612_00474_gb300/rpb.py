@@ -22,7 +22,9 @@ PRECISIONS = {"fp64": RPB_FP64, "fp32": RPB_FP32}
 EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", "rpb_lanczos_sqrt_apply",
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
            "rpb_launch_count", "rpb_mobility_apply_noalloc", "rpb_batch_create", "rpb_batch_destroy",
-           "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step")
+           "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step")
+SCHEMES = {"AB": 0, "EM": 1}
+RFDS = {"centred": 0, "one-sided": 1}
 NOALLOC_MAX_N = 16384
 
 
@@ -37,7 +39,11 @@ class NoConvergence(RpbError):
 
 
 class Params(ctypes.Structure):
-    _fields_ = [("a", ctypes.c_double), ("eta", ctypes.c_double), ("kT", ctypes.c_double), ("precision", ctypes.c_int)]
+    _fields_ = [("a", ctypes.c_double), ("eta", ctypes.c_double), ("kT", ctypes.c_double), ("precision", ctypes.c_int),
+                ("wall", ctypes.c_int)]
+
+    def __init__(self, a=1.0, eta=1.0, kT=1.0, precision=0, wall=1):
+        super().__init__(a, eta, kT, precision, wall)
 
 
 class ForceParams(ctypes.Structure):
@@ -47,6 +53,10 @@ class ForceParams(ctypes.Structure):
 
 class StepStats(ctypes.Structure):
     _fields_ = [("lanczos_iters", ctypes.c_int), ("lanczos_err", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+class StepOptions(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int), ("rfd", ctypes.c_int)]
 
 
 _lib = None
@@ -79,6 +89,8 @@ def load(build_if_missing=True):
     L.rpb_philox_normal.argtypes = [vp, i64, u64, u32, u32, u32, vp]
     L.rpb_ab_step.argtypes = [vp, i64, vp, vp, i64, u64, d, d, d, i32, ctypes.POINTER(ForceParams),
                               ctypes.POINTER(StepStats)]
+    L.rpb_step.argtypes = [vp, i64, vp, vp, i64, u64, d, d, d, i32, ctypes.POINTER(ForceParams),
+                           ctypes.POINTER(StepOptions), ctypes.POINTER(StepStats)]
     L.rpb_last_error.argtypes = []
     L.rpb_last_error.restype = ctypes.c_char_p
     L.rpb_launch_count.argtypes = []
@@ -160,9 +172,9 @@ def _force_params(weight, U0, b, torque):
 class Context:
     """A library context (rpb_create) bound to the current CUDA device."""
 
-    def __init__(self, max_N, a=1.0, eta=1.0, kT=1.0, precision="fp64", max_iter=64):
+    def __init__(self, max_N, a=1.0, eta=1.0, kT=1.0, precision="fp64", max_iter=64, wall=True):
         L = load()
-        p = Params(float(a), float(eta), float(kT), PRECISIONS[precision])
+        p = Params(float(a), float(eta), float(kT), PRECISIONS[precision], 1 if wall else 0)
         h = ctypes.c_void_p()
         _check(L.rpb_create(ctypes.byref(h), ctypes.byref(p), int(max_N), int(max_iter), _stream()))
         self._h = h
@@ -249,6 +261,22 @@ class Context:
         rc = load().rpb_ab_step(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(U_prev, n, "U_prev"), int(step),
                                 int(seed), float(dt), float(delta), float(tol), int(max_iter or self.max_iter),
                                 ctypes.byref(fp), ctypes.byref(stats))
+        if not (rc == RPB_ENOCONV and not raise_on_noconv):
+            _check(rc)
+        return dict(m=stats.lanczos_iters, eps=stats.lanczos_err, converged=bool(stats.converged))
+
+    def step(self, pos, U_prev, step, seed, scheme="AB", rfd="centred", dt=0.01, delta=1e-6, tol=1e-3,
+             max_iter=None, weight=1.0, U0=1.0, b=0.1, torque=(0.0, 1.0, 0.0), raise_on_noconv=True):
+        """One time step in place with the chosen integrator ("AB" or "EM") and RFD difference
+        ("centred" or "one-sided") (rpb_step); returns the step statistics."""
+        n = pos.numel()
+        fp = _force_params(weight, U0, b, torque)
+        opts = StepOptions(SCHEMES[scheme], RFDS[rfd])
+        stats = StepStats()
+        self._bind_stream()
+        rc = load().rpb_step(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(U_prev, n, "U_prev"), int(step), int(seed),
+                             float(dt), float(delta), float(tol), int(max_iter or self.max_iter), ctypes.byref(fp),
+                             ctypes.byref(opts), ctypes.byref(stats))
         if not (rc == RPB_ENOCONV and not raise_on_noconv):
             _check(rc)
         return dict(m=stats.lanczos_iters, eps=stats.lanczos_err, converged=bool(stats.converged))

@@ -256,3 +256,58 @@ def test_invalid_arguments(ctx64, gpu_lib):
     assert "aligned" in gpu_lib.last_error()
     with pytest.raises(gpu_lib.RpbError):
         ctx64.lanczos_sqrt_apply(pos, F, max_iter=65)
+
+
+# ------------------------------------------------------------------ unbounded mode and step variants
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_unbounded_mode(gpu_lib, prec, tol):
+    N = 300
+    pos = overlapping(N, 501)
+    F, T = inputs.vectors(N, 3), inputs.vectors(N, 4)
+    ctx = gpu_lib.Context(max_N=N, precision=prec, max_iter=16, wall=False)
+    try:
+        got = host(ctx.mobility_apply(dev(pos), dev(F), dev(T)), N)
+        got_tt = host(ctx.mobility_apply(dev(pos), dev(F)), N)
+    finally:
+        ctx.close()
+    assert maxrel(got, O.mobility_apply(pos, F, T, wall=False)) <= tol
+    assert maxrel(got_tt, O.mobility_apply(pos, F, None, wall=False)) <= tol
+
+
+@pytest.mark.parametrize("scheme,rfd", [("EM", "centred"), ("AB", "one-sided"), ("EM", "one-sided")])
+def test_step_variants(ctx64, scheme, rfd):
+    N = 64
+    pos0 = inputs.monolayer(N, seed=8)
+    Uprev = inputs.vectors(N, 9, scale=0.01)
+    q, U = dev(pos0), dev(Uprev)
+    st = ctx64.step(q, U, 3, 21, scheme=scheme, rfd=rfd, dt=0.01, delta=1e-6, tol=1e-3)
+    new_ref, Un_ref, info = O.ab_step(pos0, Uprev, 3, seed=21, dt=0.01, delta=1e-6, tol=1e-3, scheme=scheme,
+                                      one_sided=(rfd == "one-sided"))
+    assert st["m"] == info["m"]
+    assert maxrel(host(q, N) - pos0, new_ref - pos0) <= 1e-8
+    assert maxrel(host(U, N), Un_ref) <= 1e-10
+
+
+def test_checkpoint_resume_bitwise(gpu_lib):
+    """State = (positions, U^{n-1}, step index, seed): six steps straight equal three steps, a round
+    trip of the state through host memory into a new context, and three more (counter-based noise)."""
+    N = 300
+    pos0 = inputs.monolayer(N, seed=12)
+
+    def run(q, U, steps, ctx):
+        for s in steps:
+            ctx.ab_step(q, U, s, 99, dt=0.01, delta=5e-3)
+
+    c1 = gpu_lib.Context(max_N=N, precision="fp32", max_iter=32)
+    qa, Ua = dev(pos0), torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    run(qa, Ua, range(6), c1)
+    qb, Ub = dev(pos0), torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    run(qb, Ub, range(3), c1)
+    saved = (qb.cpu().numpy().copy(), Ub.cpu().numpy().copy())
+    c1.close()
+    c2 = gpu_lib.Context(max_N=N, precision="fp32", max_iter=32)
+    qc = torch.tensor(saved[0], device="cuda")
+    Uc = torch.tensor(saved[1], device="cuda")
+    run(qc, Uc, range(3, 6), c2)
+    c2.close()
+    assert torch.equal(qa, qc) and torch.equal(Ua, Uc)
