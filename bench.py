@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", choices=["monolayer", "batched", "serving"], default="monolayer")
+    ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy"],
+                    default="monolayer")
+    ap.add_argument("--acc-steps", type=int, default=10, help="accuracy: steps compared with the oracle")
     ap.add_argument("--B", type=int, default=512, help="batched: number of suspensions")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     ap.add_argument("--load", type=float, default=0.85, help="serving: offered load relative to measured capacity")
@@ -486,6 +488,106 @@ def run_serving(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_lanczos_sweep(args, rank, world, local_rank):
+    """Lanczos iterations to reach eps <= 1e-3 and <= 1e-5 versus N, with the wall-corrected mobility
+    and with the unbounded-domain mobility (Sec. II.C: screening by the wall keeps the iteration count
+    independent of N; without it the count grows), FP32 pairs, same monolayers and noise."""
+    import torch
+
+    from paper_1612_00474_gb300 import inputs, rpb
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    Ns = [n for n in (1024, 2048, 4096, 8192, 16384, 32768, 65536) if n <= args.N]
+    rows = []
+    t0 = time.perf_counter()
+    for wall in (True, False):
+        ctx = rpb.Context(max_N=max(Ns), precision="fp32", max_iter=64, wall=wall)
+        for N in Ns:
+            q = torch.tensor(inputs.to_soa(inputs.monolayer(N, seed=args.seed)), dtype=torch.float64, device="cuda")
+            W = ctx.philox_normal(N, args.seed, 0, 0)
+            row = {"N": N, "wall": wall}
+            for tol in (1e-3, 1e-5):
+                g, m, eps, conv = ctx.lanczos_sqrt_apply(q, W, tol=tol, max_iter=64, raise_on_noconv=False)
+                row[f"m_{tol:g}"] = m if conv else None
+                row[f"eps_{tol:g}"] = eps
+            rows.append(row)
+        ctx.close()
+    wall_s = time.perf_counter() - t0
+    m_wall = [r["m_1e-05"] for r in rows if r["wall"]]
+    line = _base_line(args, 1, float(max(m_wall)) if all(m_wall) else float("nan"), "iterations", wall_s * 1e3 / len(rows),
+                      "f32", {"workload": f"Lanczos iterations vs N: monolayers phi=0.4, z=a+Exp(0.5a), N in {Ns}, "
+                                          "fp32 pairs, fp64 Lanczos, with and without the wall terms"})
+    line["higher_is_better"] = False
+    line["sweep"] = rows
+    print(json.dumps(line), flush=True)
+
+
+def run_accuracy(args, rank, world, local_rank):
+    """Per-step errors against the FP64 oracle (first `--acc-steps` steps of the N=4096 suspension,
+    both GPU paths restarted from the oracle's state every step, identical Philox noise): the
+    deterministic velocity U^n and the increment q^{n+1} - q^n; then steps/s of each path over
+    `--steps` steps.  The oracle runs with the same delta as each path."""
+    import torch
+
+    import oracle as O
+    from paper_1612_00474_gb300 import inputs, rpb
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    N = args.N
+    dev = lambda x: torch.tensor(inputs.to_soa(x), dtype=torch.float64, device="cuda")  # noqa: E731
+    host = lambda t: inputs.from_soa(t.cpu().numpy(), N)  # noqa: E731
+    paths = {"fp64": dict(delta=1e-6), "fp32": dict(delta=5e-3)}
+    ctxs = {p: rpb.Context(max_N=N, precision=p, max_iter=64) for p in paths}
+    q_ref = inputs.monolayer(N, seed=args.seed)
+    Up_ref = None
+    table = []
+    t_oracle = 0.0
+    for n in range(args.acc_steps):
+        row = {"step": n}
+        refs = {}
+        for p, kw in paths.items():
+            t0 = time.perf_counter()
+            refs[p] = O.ab_step(q_ref, Up_ref, n, seed=args.seed, dt=args.dt, delta=kw["delta"], tol=args.tol,
+                                max_iter=64)
+            t_oracle += time.perf_counter() - t0
+        for p, kw in paths.items():
+            new_ref, Un_ref, info = refs[p]
+            q = dev(q_ref)
+            U = dev(Up_ref) if Up_ref is not None else torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+            st = ctxs[p].ab_step(q, U, n, args.seed, dt=args.dt, delta=kw["delta"], tol=args.tol, max_iter=64)
+            inc, inc_ref = host(q) - q_ref, new_ref - q_ref
+            row[p] = {"U_rel": O.rel_err(host(U), Un_ref), "increment_rel": O.rel_err(inc, inc_ref),
+                      "m": st["m"], "m_oracle": info["m"]}
+        table.append(row)
+        q_ref, Up_ref = refs["fp64"][0], refs["fp64"][1]
+    # throughput of both paths over args.steps steps
+    rates = {}
+    for p, kw in paths.items():
+        q = dev(inputs.monolayer(N, seed=args.seed))
+        U = torch.zeros_like(q)
+        for s in range(args.warmup):
+            ctxs[p].ab_step(q, U, s, args.seed, dt=args.dt, delta=kw["delta"], tol=args.tol, max_iter=64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(args.warmup, args.warmup + args.steps):
+            ctxs[p].ab_step(q, U, s, args.seed, dt=args.dt, delta=kw["delta"], tol=args.tol, max_iter=64)
+        torch.cuda.synchronize()
+        rates[p] = args.steps / (time.perf_counter() - t0)
+        ctxs[p].close()
+    worst32 = max(r["fp32"]["U_rel"] for r in table)
+    line = _base_line(args, 1, rates["fp32"], "steps/s", 1e3 / rates["fp32"], "f32",
+                      {"workload": f"accuracy: N={N} suspension, AB steps dt={args.dt}, tol={args.tol}; FP64 path "
+                                   f"delta=1e-6, FP32 path delta=5e-3; oracle per-step comparison on the first "
+                                   f"{args.acc_steps} steps", "N": N})
+    line.update({"steps_per_s": rates, "per_step_errors": table, "worst_fp32_U_rel": worst32,
+                 "oracle_seconds_per_step": t_oracle / (2 * args.acc_steps)})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.delta is None:
@@ -498,6 +600,10 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, world, local_rank)
+    elif args.workload == "lanczos":
+        run_lanczos_sweep(args, rank, world, local_rank)
+    elif args.workload == "accuracy":
+        run_accuracy(args, rank, world, local_rank)
     elif args.workload == "serving":
         run_serving(args, rank, world, local_rank)
     else:

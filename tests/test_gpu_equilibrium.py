@@ -64,6 +64,8 @@ def test_gibbs_boltzmann_heights(gpu_lib, scheme):
     mean = zs.mean()
     below = (zs < 1.3).mean()
     ks = np.max(np.abs(np.searchsorted(np.sort(zs), h) / zs.size - cdf))
+    print(f"\n{scheme}: mean height {mean:.4f} (Gibbs-Boltzmann {mean_th:.4f}), P(h < 1.3a) {below:.4f} "
+          f"({below_th:.4f}), KS distance {ks:.4f}, {zs.size} samples")
     assert abs(mean - mean_th) < 0.03 * mean_th, (mean, mean_th)
     assert abs(below - below_th) < 0.15 * below_th, (below, below_th)
     assert ks < 0.03, ks
