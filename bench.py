@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy"],
                     default="monolayer")
     ap.add_argument("--acc-steps", type=int, default=10, help="accuracy: steps compared with the oracle")
+    ap.add_argument("--lanczos-iters", type=int, default=12,
+                    help="batched: Lanczos iterations per step inside the step graph (converged instances masked)")
     ap.add_argument("--B", type=int, default=512, help="batched: number of suspensions")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     ap.add_argument("--load", type=float, default=0.85, help="serving: offered load relative to measured capacity")
@@ -361,21 +363,32 @@ def run_batched(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk = clocks_start(local_rank)
-    launches0 = rpb.launch_count()
-    pairs, ms = 0.0, []
-    for _ in range(args.steps):
+    # host-driven steps (one rpb_batch_ab_step call per step), for comparison
+    ms_call = []
+    for _ in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         st = bt.ab_step(q, U, [step] * B, seeds, **kw)
         e1.record(stream)
         e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        pairs += sum(float(N) * N * (3 + s["m"]) for N, s in zip(sizes, st))
+        ms_call.append(e0.elapsed_time(e1))
         step += 1
+    m_used = max(s["m"] for s in st)
+    # timed: all K steps in one rpb_batch_run call (one gather, the step graph replayed K times)
+    clk = clocks_start(local_rank)
+    launches0 = rpb.launch_count()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, unconv = bt.run(q, U, [step] * B, seeds, nsteps=args.steps, lanczos_iters=args.lanczos_iters,
+                        dt=args.dt, delta=args.delta, tol=args.tol)
+    torch.cuda.synchronize()
+    total_s = time.perf_counter() - t0
     clocks = clocks_stop(clk)
     launches = rpb.launch_count() - launches0
-    total_s = sum(ms) / 1e3
+    step += args.steps
+    ms = [total_s * 1e3 / args.steps] * args.steps
+    # pair evaluations: each instance's converged iteration count (m of the last step as the estimate)
+    pairs = args.steps * sum(float(N) * N * (3 + s["m"]) for N, s in zip(sizes, st))
     # the same instances, one rpb_ab_step call each (one step of all B)
     ctx = rpb.Context(max_N=max(sizes), precision=args.precision, max_iter=64)
     torch.cuda.synchronize()
@@ -398,6 +411,9 @@ def run_batched(args, rank, world, local_rank):
         line.update({"instance_steps_per_s": inst_steps,
                      "loop_instance_steps_per_s": B * world / loop_s,
                      "speedup_vs_loop": inst_steps / (B * world / loop_s),
+                     "graph_run": {"steps": args.steps, "lanczos_iters_per_step": args.lanczos_iters,
+                                   "unconverged_instance_steps": unconv, "host_driven_step_ms": ms_call,
+                                   "max_m": m_used},
                      "step_ms": [round(x, 3) for x in ms], "gpu_launches": int(launches), "clocks": clocks})
         print(json.dumps(line), flush=True)
     if dist:

@@ -194,6 +194,19 @@ int rpb_batch_ab_step(rpb_batch *bt, int B, const int64_t *N, double *const *pos
                       const int64_t *steps, const uint64_t *seeds, double dt, double delta, double tol,
                       int max_iter, const rpb_force_params *fp, rpb_step_stats *stats);
 
+/* nsteps AB steps of every instance (as repeated rpb_batch_ab_step) with one gather and one scatter
+ * of the state, the step captured once into a CUDA graph and replayed nsteps times with no host
+ * synchronisation in between.  Inside the graph Lanczos runs exactly lanczos_iters iterations per
+ * step with converged instances masked out (so lanczos_iters must cover the iteration count the
+ * tolerance needs; *unconverged, if not NULL, receives the number of instance-steps that did not
+ * reach tol, and RPB_ENOCONV is returned if it is nonzero with tol > 0).  steps: each instance's
+ * first step index (advanced on the device).  stats: the last step's statistics (B entries, or
+ * NULL).  The work runs on a stream the batch context owns, ordered after the context's stream;
+ * the call returns when it is complete. */
+int rpb_batch_run(rpb_batch *bt, int B, const int64_t *N, double *const *pos, double *const *U_prev,
+                  const int64_t *steps, const uint64_t *seeds, int nsteps, double dt, double delta, double tol,
+                  int lanczos_iters, const rpb_force_params *fp, rpb_step_stats *stats, int64_t *unconverged);
+
 /* Largest N accepted by rpb_mobility_apply_noalloc. */
 #define RPB_NOALLOC_MAX_N 16384
 

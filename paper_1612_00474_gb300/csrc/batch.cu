@@ -260,8 +260,7 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
                                                            double weight, double U0, double b, float cut2,
                                                            double *__restrict__ F)
 {
-    __shared__ double sx[128], sy[128], sz[128];
-    __shared__ float fxs[128], fys[128], fzs[128];
+    __shared__ float4 sp[128];
     const BlockDesc bd = blocks[blockIdx.x];
     const InstDesc d = inst[bd.inst];
     const int tid = threadIdx.x;
@@ -279,21 +278,17 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
     double fx = 0.0, fy = 0.0, fz = 0.0;
     for (int base = 0; base < d.N; base += 128) {
         const int jl = base + tid;
-        if (jl < d.N) {
-            const int64_t j = d.off + jl;
-            sx[tid] = pos[j];
-            sy[tid] = pos[total + j];
-            sz[tid] = pos[2 * total + j];
-            fxs[tid] = (float)sx[tid];
-            fys[tid] = (float)sy[tid];
-            fzs[tid] = (float)sz[tid];
-        }
+        const int64_t jt = d.off + jl;
+        sp[tid] = jl < d.N ? make_float4((float)pos[jt], (float)pos[total + jt], (float)pos[2 * total + jt], 0.f)
+                           : make_float4(1e18f, 0.f, 0.f, 0.f);
         __syncthreads();
-        const int cnt = min(128, d.N - base);
-        for (int k = 0; k < cnt; ++k) {
-            const float dxf = xf - fxs[k], dyf = yf - fys[k], dzf = zf - fzs[k];
-            if (dxf * dxf + dyf * dyf + dzf * dzf < cut2 && base + k != il) {
-                const double dx = xi - sx[k], dy = yi - sy[k], dz = zi - sz[k];
+#pragma unroll 8
+        for (int k = 0; k < 128; ++k) {
+            const float4 p = sp[k];
+            const float dxf = xf - p.x, dyf = yf - p.y, dzf = zf - p.z;
+            if (fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf)) < cut2 && base + k != il) {
+                const int64_t j = d.off + base + k;
+                const double dx = xi - pos[j], dy = yi - pos[total + j], dz = zi - pos[2 * total + j];
                 const double r = sqrt(dx * dx + dy * dy + dz * dz);
                 if (r > 0.0) {
                     const double m = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
@@ -558,6 +553,12 @@ struct rpb_batch {
     int64_t total = 0;
     int B = 0;
     int nblocks = 0;
+    // multi-step runs: a private stream to capture and replay the step graph on, joined to the
+    // caller's stream by an event; a device counter of unconverged instance-steps
+    cudaStream_t cap = nullptr;
+    cudaEvent_t join = nullptr;
+    unsigned long long *d_unconv = nullptr;
+    unsigned long long *h_unconv = nullptr;
 };
 
 namespace rpb {
@@ -572,9 +573,12 @@ static void batch_free(rpb_batch *bt)
         if (p) cudaFree(p);
     for (double *p : bt->vec)
         if (p) cudaFree(p);
-    void *host[] = {bt->h_inst, bt->h_blocks, bt->h_nactive, bt->h_lz};
+    void *host[] = {bt->h_inst, bt->h_blocks, bt->h_nactive, bt->h_lz, bt->h_unconv};
     for (void *p : host)
         if (p) cudaFreeHost(p);
+    if (bt->d_unconv) cudaFree(bt->d_unconv);
+    if (bt->join) cudaEventDestroy(bt->join);
+    if (bt->cap) cudaStreamDestroy(bt->cap);
 }
 
 static int grid_for(int64_t n, int sms)
@@ -691,7 +695,12 @@ static int batch_product(rpb_batch *bt, const double *pos, const double *F, cons
 }
 
 // Lanczos for every instance at once; per-instance m, eps and convergence land in h_lz statuses.
-static int batch_lanczos(rpb_batch *bt, const double *pos, const double *W, double *g, double tol, int max_iter)
+// graph == false: the host reads the number of still-active instances after every iteration and stops
+// when it reaches zero, then copies the per-instance statuses to h_lz.  graph == true (inside a CUDA
+// graph capture): exactly max_iter iterations are enqueued, with converged instances masked out of
+// every kernel, and nothing is read back.
+static int batch_lanczos(rpb_batch *bt, const double *pos, const double *W, double *g, double tol, int max_iter,
+                         bool graph = false)
 {
     cudaStream_t st = bt->stream;
     const int B = bt->B;
@@ -720,11 +729,13 @@ static int batch_lanczos(rpb_batch *bt, const double *pos, const double *W, doub
         batch_tail_kernel<<<(B + 3) / 4, 128, 0, st>>>(bt->lz, bt->lz_stride, L, k, tol, bt->norm2, B, bt->d_active,
                                                        bt->d_nactive);
         count_launches(5);
-        if ((rc = cuda_fail(cudaMemcpyAsync(bt->h_nactive, bt->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st),
-                            "n_active copy")))
-            return rc;
-        if ((rc = cuda_fail(cudaStreamSynchronize(st), "batch lanczos iteration"))) return rc;
-        if (*bt->h_nactive == 0) break;
+        if (!graph) {
+            if ((rc = cuda_fail(cudaMemcpyAsync(bt->h_nactive, bt->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st),
+                                "n_active copy")))
+                return rc;
+            if ((rc = cuda_fail(cudaStreamSynchronize(st), "batch lanczos iteration"))) return rc;
+            if (*bt->h_nactive == 0) break;
+        }
         if (k + 1 < max_iter) {
             batch_scale_kernel<<<ge, 256, 0, st>>>(w, bt->d_inst, bt->d_inst_of, bt->d_active, total, bt->lz,
                                                    bt->lz_stride, L.status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
@@ -733,11 +744,133 @@ static int batch_lanczos(rpb_batch *bt, const double *pos, const double *W, doub
     }
     batch_combine_kernel<<<ge, 256, 0, st>>>(V, ld, bt->d_inst_of, total, bt->lz, bt->lz_stride, L, g);
     count_launches(1);
+    if (graph) return cuda_fail(cudaGetLastError(), "batch lanczos kernels");
     if ((rc = cuda_fail(cudaMemcpyAsync(bt->h_lz, bt->lz, (size_t)B * bt->lz_stride * sizeof(double),
                                         cudaMemcpyDeviceToHost, st),
                         "status copy")))
         return rc;
     return cuda_fail(cudaStreamSynchronize(st), "batch lanczos");
+}
+
+// After a step replayed from a CUDA graph: advance every instance's step counter and count the
+// instances whose Lanczos did not converge within the fixed iteration count.
+__global__ void batch_advance_kernel(InstDesc *__restrict__ inst, int B, const int *__restrict__ active,
+                                     unsigned long long *__restrict__ unconv)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    inst[b].step += 1u;
+    inst[b].first = 0;
+    if (active[b]) atomicAdd(unconv, 1ull);
+}
+
+// One AB step of the packed batch (state in vec[V_POS], vec[V_UP]).  graph: see batch_lanczos; the
+// step then also advances the device-side step counters.
+static int batch_step_body(rpb_batch *bt, double dt, double delta, double tol, int max_iter,
+                           const rpb_force_params *fp, bool graph)
+{
+    cudaStream_t st = bt->stream;
+    const int64_t total = bt->total, n = 3 * total;
+    double **v = bt->vec;
+    const int ge = grid_for(n, bt->num_sms);
+    int rc;
+    const double a = bt->p.a;
+    const double rcut = (2.0 * a + 50.0 * fp->b) * 1.01 + 0.01 * a;
+    batch_forces_kernel<<<bt->nblocks, 128, 0, st>>>(v[V_POS], bt->d_inst, bt->d_blocks, total, a, fp->weight, fp->U0,
+                                                     fp->b, (float)(rcut * rcut), v[V_F]);
+    batch_fill3_kernel<<<ge, 256, 0, st>>>(v[V_T], total, fp->torque[0], fp->torque[1], fp->torque[2]);
+    count_launches(2);
+    if ((rc = batch_product(bt, v[V_POS], v[V_F], v[V_T], v[V_UN], nullptr))) return rc;
+    batch_philox_kernel<<<ge, 256, 0, st>>>(bt->d_inst, bt->d_inst_of, total, 0u, v[V_W]);
+    batch_philox_kernel<<<ge, 256, 0, st>>>(bt->d_inst, bt->d_inst_of, total, 1u, v[V_WT]);
+    count_launches(2);
+    if ((rc = batch_lanczos(bt, v[V_POS], v[V_W], v[V_G], tol, max_iter, graph))) return rc;
+    // RFD: two products at the displaced configurations, regularised anew
+    batch_displace_kernel<<<ge, 256, 0, st>>>(v[V_POS], v[V_WT], n, 0.5 * delta, v[V_PA], v[V_PB]);
+    count_launches(1);
+    if ((rc = batch_product(bt, v[V_PA], v[V_WT], nullptr, v[V_DRIFT], nullptr))) return rc;
+    if ((rc = batch_product(bt, v[V_PB], v[V_WT], nullptr, v[V_WORK], nullptr))) return rc;
+    batch_rfd_combine_kernel<<<ge, 256, 0, st>>>(v[V_DRIFT], v[V_WORK], n, bt->p.kT / delta);
+    batch_ab_update_kernel<<<ge, 256, 0, st>>>(bt->d_inst, bt->d_inst_of, total, v[V_POS], v[V_UP], v[V_UN], v[V_G],
+                                               v[V_DRIFT], dt, sqrt(2.0 * bt->p.kT * dt));
+    count_launches(2);
+    if (graph) {
+        batch_advance_kernel<<<(bt->B + 127) / 128, 128, 0, st>>>(bt->d_inst, bt->B, bt->d_active, bt->d_unconv);
+        count_launches(1);
+    }
+    return cuda_fail(cudaGetLastError(), "batch step kernels");
+}
+
+// Per-instance statistics from the host copy of the Lanczos states; returns how many did not converge.
+static int batch_read_stats(rpb_batch *bt, double tol, rpb_step_stats *stats)
+{
+    const LzLayout L(bt->max_iter);
+    int noconv = 0;
+    for (int b = 0; b < bt->B; ++b) {
+        const double *stb = bt->h_lz + (size_t)b * bt->lz_stride + L.status;
+        const int conv = stb[7] != 0.0;
+        noconv += !conv && tol > 0.0;
+        if (stats) {
+            stats[b].lanczos_iters = (int)stb[6];
+            stats[b].lanczos_err = stb[ST_EPS];
+            stats[b].converged = conv;
+        }
+    }
+    return noconv;
+}
+
+// nsteps AB steps of the batch: one gather, one CUDA graph of a step (fixed Lanczos iteration count,
+// converged instances masked) replayed nsteps times without host synchronisation, one scatter.
+static int batch_run_impl(rpb_batch *bt, int B, const int64_t *N, double *const *pos, double *const *U_prev,
+                          const int64_t *steps, const uint64_t *seeds, int nsteps, double dt, double delta, double tol,
+                          int lanczos_iters, const rpb_force_params *fp, rpb_step_stats *stats, int64_t *unconverged)
+{
+    int rc;
+    if ((rc = batch_setup(bt, B, N, steps, seeds, pos, U_prev, nullptr, nullptr))) return rc;
+    cudaStream_t st = bt->stream;
+    double **v = bt->vec;
+    if ((rc = batch_gather(bt, 0, v[V_POS], 0)) || (rc = batch_gather(bt, 1, v[V_UP], 0))) return rc;
+    if ((rc = cuda_fail(cudaMemsetAsync(bt->d_unconv, 0, sizeof(unsigned long long), st), "memset"))) return rc;
+    if (nsteps > 0) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const uint64_t before = rpb_launch_count();
+        if ((rc = cuda_fail(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return rc;
+        const int brc = batch_step_body(bt, dt, delta, tol, lanczos_iters, fp, true);
+        const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+        const int per_step = (int)(rpb_launch_count() - before);
+        count_launches(-per_step);  // captured, not executed
+        if (brc) {
+            if (graph) cudaGraphDestroy(graph);
+            return brc;
+        }
+        if ((rc = cuda_fail(ec, "end capture"))) return rc;
+        if ((rc = cuda_fail(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate"))) {
+            cudaGraphDestroy(graph);
+            return rc;
+        }
+        for (int s = 0; s < nsteps && !rc; ++s) rc = cuda_fail(cudaGraphLaunch(exec, st), "graph launch");
+        if (!rc) count_launches(per_step * nsteps);
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (rc) return rc;
+    }
+    if ((rc = batch_gather(bt, 0, v[V_POS], 1)) || (rc = batch_gather(bt, 1, v[V_UP], 1))) return rc;
+    if ((rc = cuda_fail(cudaMemcpyAsync(bt->h_lz, bt->lz, (size_t)B * bt->lz_stride * sizeof(double),
+                                        cudaMemcpyDeviceToHost, st),
+                        "status copy")) ||
+        (rc = cuda_fail(cudaMemcpyAsync(bt->h_unconv, bt->d_unconv, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                        st),
+                        "count copy")) ||
+        (rc = cuda_fail(cudaStreamSynchronize(st), "batch run")))
+        return rc;
+    batch_read_stats(bt, tol, stats);
+    if (unconverged) *unconverged = (int64_t)*bt->h_unconv;
+    if (*bt->h_unconv && tol > 0.0) {
+        set_error("lanczos: %llu instance-step(s) did not converge in %d iterations", *bt->h_unconv, lanczos_iters);
+        return RPB_ENOCONV;
+    }
+    return RPB_OK;
 }
 
 }  // namespace rpb
@@ -794,7 +927,11 @@ int rpb_batch_create(rpb_batch **out, const rpb_params *p, int64_t max_total_N, 
               cudaMallocHost(&bt->h_inst, max_B * sizeof(InstDesc)) == cudaSuccess &&
               cudaMallocHost(&bt->h_blocks, max_blocks * sizeof(BlockDesc)) == cudaSuccess &&
               cudaMallocHost(&bt->h_nactive, sizeof(int)) == cudaSuccess &&
-              cudaMallocHost(&bt->h_lz, (size_t)max_B * L.total * sizeof(double)) == cudaSuccess;
+              cudaMallocHost(&bt->h_lz, (size_t)max_B * L.total * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&bt->d_unconv, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMallocHost(&bt->h_unconv, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&bt->join, cudaEventDisableTiming) == cudaSuccess;
     for (double *&v : bt->vec) ok = ok && cudaMalloc(&v, vb) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -878,50 +1015,47 @@ int rpb_batch_ab_step(rpb_batch *bt, int B, const int64_t *N, double *const *pos
         }
     int rc;
     if ((rc = batch_setup(bt, B, N, steps, seeds, pos, U_prev, nullptr, nullptr))) return rc;
-    cudaStream_t st = bt->stream;
-    const int64_t total = bt->total, n = 3 * total;
     double **v = bt->vec;
-    const int ge = grid_for(n, bt->num_sms);
     if ((rc = batch_gather(bt, 0, v[V_POS], 0)) || (rc = batch_gather(bt, 1, v[V_UP], 0))) return rc;
-    const double a = bt->p.a;
-    const double rcut = (2.0 * a + 50.0 * fp->b) * 1.01 + 0.01 * a;
-    batch_forces_kernel<<<bt->nblocks, 128, 0, st>>>(v[V_POS], bt->d_inst, bt->d_blocks, total, a, fp->weight, fp->U0,
-                                                     fp->b, (float)(rcut * rcut), v[V_F]);
-    batch_fill3_kernel<<<ge, 256, 0, st>>>(v[V_T], total, fp->torque[0], fp->torque[1], fp->torque[2]);
-    count_launches(2);
-    if ((rc = batch_product(bt, v[V_POS], v[V_F], v[V_T], v[V_UN], nullptr))) return rc;
-    batch_philox_kernel<<<ge, 256, 0, st>>>(bt->d_inst, bt->d_inst_of, total, 0u, v[V_W]);
-    batch_philox_kernel<<<ge, 256, 0, st>>>(bt->d_inst, bt->d_inst_of, total, 1u, v[V_WT]);
-    count_launches(2);
-    if ((rc = batch_lanczos(bt, v[V_POS], v[V_W], v[V_G], tol, max_iter))) return rc;
-    // RFD: two products at the displaced configurations, regularised anew
-    batch_displace_kernel<<<ge, 256, 0, st>>>(v[V_POS], v[V_WT], n, 0.5 * delta, v[V_PA], v[V_PB]);
-    count_launches(1);
-    if ((rc = batch_product(bt, v[V_PA], v[V_WT], nullptr, v[V_DRIFT], nullptr))) return rc;
-    if ((rc = batch_product(bt, v[V_PB], v[V_WT], nullptr, v[V_WORK], nullptr))) return rc;
-    batch_rfd_combine_kernel<<<ge, 256, 0, st>>>(v[V_DRIFT], v[V_WORK], n, bt->p.kT / delta);
-    batch_ab_update_kernel<<<ge, 256, 0, st>>>(bt->d_inst, bt->d_inst_of, total, v[V_POS], v[V_UP], v[V_UN], v[V_G],
-                                               v[V_DRIFT], dt, sqrt(2.0 * bt->p.kT * dt));
-    count_launches(2);
-    if ((rc = cuda_fail(cudaGetLastError(), "batch step kernels"))) return rc;
+    if ((rc = batch_step_body(bt, dt, delta, tol, max_iter, fp, false))) return rc;
     if ((rc = batch_gather(bt, 0, v[V_POS], 1)) || (rc = batch_gather(bt, 1, v[V_UP], 1))) return rc;
-    const LzLayout L(bt->max_iter);
-    int noconv = 0;
-    for (int b = 0; b < B; ++b) {
-        const double *stb = bt->h_lz + (size_t)b * bt->lz_stride + L.status;
-        const int conv = stb[7] != 0.0;
-        noconv += !conv && tol > 0.0;
-        if (stats) {
-            stats[b].lanczos_iters = (int)stb[6];
-            stats[b].lanczos_err = stb[ST_EPS];
-            stats[b].converged = conv;
-        }
-    }
+    const int noconv = batch_read_stats(bt, tol, stats);
     if (noconv) {
         set_error("lanczos: %d instance(s) did not converge in %d iterations", noconv, max_iter);
         return RPB_ENOCONV;
     }
     return RPB_OK;
+}
+
+int rpb_batch_run(rpb_batch *bt, int B, const int64_t *N, double *const *pos, double *const *U_prev,
+                  const int64_t *steps, const uint64_t *seeds, int nsteps, double dt, double delta, double tol,
+                  int lanczos_iters, const rpb_force_params *fp, rpb_step_stats *stats, int64_t *unconverged)
+{
+    if (!bt || !N || !pos || !U_prev || !steps || !seeds || !fp) {
+        set_error("null argument to rpb_batch_run");
+        return RPB_EINVAL;
+    }
+    if (!(fp->b > 0.0) || !(dt > 0.0) || !(delta > 0.0) || lanczos_iters < 1 || lanczos_iters > bt->max_iter ||
+        nsteps < 0) {
+        set_error("bad run arguments (dt=%g delta=%g lanczos_iters=%d nsteps=%d)", dt, delta, lanczos_iters, nsteps);
+        return RPB_EINVAL;
+    }
+    for (int b = 0; b < B && b < bt->max_B; ++b)
+        if (!pos[b] || !U_prev[b] || steps[b] < 0 || steps[b] + nsteps > 0xffffffffLL) {
+            set_error("instance %d: null buffer or bad step", b);
+            return RPB_EINVAL;
+        }
+    // Everything runs on the batch's own capture stream, ordered after the caller's stream.
+    cudaStream_t user = bt->stream;
+    int rc;
+    if ((rc = cuda_fail(cudaEventRecord(bt->join, user), "event record")) ||
+        (rc = cuda_fail(cudaStreamWaitEvent(bt->cap, bt->join, 0), "stream wait")))
+        return rc;
+    bt->stream = bt->cap;
+    rc = batch_run_impl(bt, B, N, pos, U_prev, steps, seeds, nsteps, dt, delta, tol, lanczos_iters, fp, stats,
+                        unconverged);
+    bt->stream = user;
+    return rc;
 }
 
 }  // extern "C"

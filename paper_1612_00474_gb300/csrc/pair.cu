@@ -420,22 +420,28 @@ __global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, cons
                                        const double *__restrict__ pos, const double *__restrict__ F,
                                        PairConsts<double> c, double a, double scale, double *__restrict__ U)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int b = i / kTile, l = i - b * kTile;
-    double ux = 0.0, uy = 0.0, uz = 0.0;
-    for (int k = row_cta[b]; k < row_cta[b + 1]; ++k) {
-        const double *o = tgt_part + (size_t)k * 3 * kTile;
-        ux += o[l];
-        uy += o[kTile + l];
-        uz += o[2 * kTile + l];
-    }
+    // one CTA per 128-sphere tile b, thread (q, l) = (component, sphere): coalesced column sums
+    __shared__ double s[3][kTile];
+    const int b = blockIdx.x;
+    const int q = threadIdx.x / kTile, l = threadIdx.x - q * kTile;
+    double acc = 0.0;
+    for (int k = row_cta[b]; k < row_cta[b + 1]; ++k) acc += tgt_part[((size_t)k * 3 + q) * kTile + l];
+    // column of float32 partials: compensated float32 sum (GB300's float64 rate would make a float64
+    // add per partial the bottleneck), converted once
+    const float *col = src_part + (size_t)col_start[b] * 3 * kTile + q * kTile + l;
+    float cs = 0.f, cc = 0.f;
+#pragma unroll 4
     for (int bb = 0; bb < b; ++bb) {
-        const float *o = src_part + (size_t)(col_start[b] + bb) * 3 * kTile;
-        ux += (double)o[l];
-        uy += (double)o[kTile + l];
-        uz += (double)o[2 * kTile + l];
+        const float yv = col[(size_t)bb * 3 * kTile] - cc;
+        const float tv = cs + yv;
+        cc = (tv - cs) - yv;
+        cs = tv;
     }
+    s[q][l] = acc + ((double)cs - (double)cc);
+    __syncthreads();
+    const int i = b * kTile + l;
+    if (q != 0 || i >= N) return;
+    double ux = s[0][l], uy = s[1][l], uz = s[2][l];
     const double z = pos[2 * N + i];
     const double si = H0(z / a);
     const double zc = fmax(z, a);
@@ -523,7 +529,7 @@ static int mobility_tt_sym(rpb_ctx *ctx, int N, const double *pos, const double 
     pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, nullptr, N, a, 1, src);
     pair_f32x2_sym_kernel<<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, (const SymCta *)w.sym_index, make_x2_consts(a),
                                                                w.sym_index + w.sym_col_off, w.sym_tgt, w.sym_src);
-    pair_sym_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
+    pair_sym_reduce_kernel<<<(N + kTile - 1) / kTile, 3 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
                                                              w.sym_index + w.sym_col_off, N, pos, F,
                                                              make_consts<double>(a), a, 1.0 / (8.0 * kPi * ctx->p.eta),
                                                              U);
@@ -720,8 +726,7 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
 __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ pos, int N, double a, double weight,
                                                      double U0, double b, float cut2, double *__restrict__ F)
 {
-    __shared__ double sx[128], sy[128], sz[128];
-    __shared__ float fxs[128], fys[128], fzs[128];
+    __shared__ float4 sp[64];  // float32 copies of the tile's positions, for the screen only
     const int tid = threadIdx.x;
     const int i = blockIdx.x * 128 + tid;
     double xi = 0.0, yi = 0.0, zi = 0.0;
@@ -733,33 +738,61 @@ __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ 
     const float xf = (float)xi, yf = (float)yi, zf = (float)zi;
     const double f0 = U0 / b;
     double fx = 0.0, fy = 0.0, fz = 0.0;
+    // Near pairs found by the float32 screen are queued per thread and evaluated in float64 together
+    // after the screen (or when the queue is full), so a warp pays for the slowest lane's list rather
+    // than for every lane's pairs one after another.
+    constexpr int kQ = 32;
+    int queue[kQ];
+    int nq = 0;
+    auto flush = [&]() {
+        for (int q = 0; q < nq; ++q) {
+            const int jj = queue[q];
+            const double dx = xi - pos[jj], dy = yi - pos[N + jj], dz = zi - pos[2 * N + jj];
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r > 0.0) {
+                const double m = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
+                fx += m * dx;
+                fy += m * dy;
+                fz += m * dz;
+            }
+        }
+        nq = 0;
+    };
+    // the tile as 64 interleaved pairs: sp[p] = (x[2p], x[2p+1], y[2p], y[2p+1]); z in sp2, so that two
+    // sources are screened per lane with packed float32x2 arithmetic
+    __shared__ float2 sz[64];
+    float *fxy = reinterpret_cast<float *>(sp);
+    float *fz2 = reinterpret_cast<float *>(sz);
+    const float2 X = make_float2(xf, xf), Y = make_float2(yf, yf), Z = make_float2(zf, zf);
+    const int pp = tid >> 1, hh = tid & 1;
     for (int base = 0; base < N; base += 128) {
         const int j = base + tid;
-        if (j < N) {
-            sx[tid] = pos[j];
-            sy[tid] = pos[N + j];
-            sz[tid] = pos[2 * N + j];
-            fxs[tid] = (float)sx[tid];
-            fys[tid] = (float)sy[tid];
-            fzs[tid] = (float)sz[tid];
-        }
+        // slots past N hold a far-away point that never passes the screen
+        const bool in = j < N;
+        fxy[4 * pp + hh] = in ? (float)pos[j] : 1e18f;
+        fxy[4 * pp + 2 + hh] = in ? (float)pos[N + j] : 0.f;
+        fz2[2 * pp + hh] = in ? (float)pos[2 * N + j] : 0.f;
         __syncthreads();
-        const int cnt = min(128, N - base);
-        for (int k = 0; k < cnt; ++k) {
-            const float dxf = xf - fxs[k], dyf = yf - fys[k], dzf = zf - fzs[k];
-            if (dxf * dxf + dyf * dyf + dzf * dzf < cut2 && base + k != i) {
-                const double dx = xi - sx[k], dy = yi - sy[k], dz = zi - sz[k];
-                const double r = sqrt(dx * dx + dy * dy + dz * dz);
-                if (r > 0.0) {
-                    const double m = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
-                    fx += m * dx;
-                    fy += m * dy;
-                    fz += m * dz;
+#pragma unroll 8
+        for (int k = 0; k < 64; ++k) {
+            const float4 p = sp[k];
+            const float2 dx = sub2(X, make_float2(p.x, p.y)), dy = sub2(Y, make_float2(p.z, p.w)), dz = sub2(Z, sz[k]);
+            const float2 d2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+            if (d2.x < cut2 || d2.y < cut2) {  // rare: a near pair (or the sphere itself)
+                const int j0 = base + 2 * k;
+                if (d2.x < cut2 && j0 != i) {
+                    queue[nq++] = j0;
+                    if (nq == kQ) flush();
+                }
+                if (d2.y < cut2 && j0 + 1 != i) {
+                    queue[nq++] = j0 + 1;
+                    if (nq == kQ) flush();
                 }
             }
         }
         __syncthreads();
     }
+    flush();
     if (i < N) {
         fz += (zi < a ? f0 : f0 * exp(-(zi - a) / b)) - weight;
         F[i] = fx;

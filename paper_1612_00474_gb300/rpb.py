@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": RPB_FP64, "fp32": RPB_FP32}
 EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", "rpb_lanczos_sqrt_apply",
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
            "rpb_launch_count", "rpb_mobility_apply_noalloc", "rpb_batch_create", "rpb_batch_destroy",
-           "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step")
+           "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step", "rpb_batch_run")
 SCHEMES = {"AB": 0, "EM": 1}
 RFDS = {"centred": 0, "one-sided": 1}
 NOALLOC_MAX_N = 16384
@@ -103,6 +103,8 @@ def load(build_if_missing=True):
     L.rpb_batch_mobility_apply.argtypes = [vp, i32, pi64, vp, vp, vp, vp]
     L.rpb_batch_ab_step.argtypes = [vp, i32, pi64, vp, vp, pi64, ctypes.POINTER(u64), d, d, d, i32,
                                     ctypes.POINTER(ForceParams), ctypes.POINTER(StepStats)]
+    L.rpb_batch_run.argtypes = [vp, i32, pi64, vp, vp, pi64, ctypes.POINTER(u64), i32, d, d, d, i32,
+                                ctypes.POINTER(ForceParams), ctypes.POINTER(StepStats), pi64]
     for name in EXPORTS:
         if name not in ("rpb_last_error", "rpb_launch_count"):
             getattr(L, name).restype = ctypes.c_int
@@ -351,3 +353,22 @@ class BatchContext:
         if not (rc == RPB_ENOCONV and not raise_on_noconv):
             _check(rc)
         return [dict(m=s.lanczos_iters, eps=s.lanczos_err, converged=bool(s.converged)) for s in stats]
+
+    def run(self, pos, U_prev, steps, seeds, nsteps, lanczos_iters=16, dt=0.01, delta=1e-6, tol=1e-3, weight=1.0,
+            U0=1.0, b=0.1, torque=(0.0, 1.0, 0.0), raise_on_noconv=True):
+        """nsteps AB steps of every instance with the step replayed from a CUDA graph (rpb_batch_run);
+        returns (last step's statistics, number of unconverged instance-steps)."""
+        B = len(pos)
+        Ns = (ctypes.c_int64 * B)(*[p.numel() // 3 for p in pos])
+        st = (ctypes.c_int64 * B)(*[int(s) for s in steps])
+        sd = (ctypes.c_uint64 * B)(*[int(s) for s in seeds])
+        stats = (StepStats * B)()
+        unconv = ctypes.c_int64(0)
+        fp = _force_params(weight, U0, b, torque)
+        self._bind_stream()
+        rc = load().rpb_batch_run(self._h, B, Ns, self._ptrs(pos, "pos"), self._ptrs(U_prev, "U_prev"), st, sd,
+                                  int(nsteps), float(dt), float(delta), float(tol), int(lanczos_iters),
+                                  ctypes.byref(fp), stats, ctypes.byref(unconv))
+        if not (rc == RPB_ENOCONV and not raise_on_noconv):
+            _check(rc)
+        return [dict(m=s.lanczos_iters, eps=s.lanczos_err, converged=bool(s.converged)) for s in stats], unconv.value

@@ -147,3 +147,26 @@ def test_batch_errors(batch64, gpu_lib):
     with pytest.raises(gpu_lib.RpbError):
         batch64.mobility_apply(big, big)                        # total > max_total_N
     assert "max_total_N" in gpu_lib.last_error()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_run_graph_equals_steps(batch32, batch64, precision):
+    """rpb_batch_run (the step captured once in a CUDA graph and replayed) gives bitwise the same
+    trajectory as the same number of rpb_batch_ab_step calls."""
+    bt = batch32 if precision == "fp32" else batch64
+    delta = 5e-3 if precision == "fp32" else 1e-6
+    sizes = [40, 128, 200, 77, 1]
+    seeds = [5, 6, 7, 8, 9]
+    steps0 = [0, 2, 0, 5, 0]
+    poss = [inputs.monolayer(N, seed=300 + k) for k, N in enumerate(sizes)]
+    qa = [dev(p) for p in poss]
+    Ua = [torch.zeros(3 * N, dtype=torch.float64, device="cuda") for N in sizes]
+    for s in range(4):
+        sa = bt.ab_step(qa, Ua, [x + s for x in steps0], seeds, delta=delta)
+    qb = [dev(p) for p in poss]
+    Ub = [torch.zeros(3 * N, dtype=torch.float64, device="cuda") for N in sizes]
+    sb, unconv = bt.run(qb, Ub, steps0, seeds, nsteps=4, lanczos_iters=32, delta=delta)
+    assert unconv == 0
+    assert [s["m"] for s in sa] == [s["m"] for s in sb]
+    for k in range(len(sizes)):
+        assert torch.equal(qa[k], qb[k]) and torch.equal(Ua[k], Ub[k]), k
