@@ -43,6 +43,10 @@ def lib():
         L.oracle_matvec_rows_w.restype = None
         L.oracle_dense_w.argtypes = [i64, dp, d, d, ctypes.c_int, dp, dp]
         L.oracle_dense_w.restype = None
+        L.oracle_matvec_rows_p.argtypes = [i64, i64, i64, dp, dp, dp, d, d, ctypes.c_int, d, d, dp]
+        L.oracle_matvec_rows_p.restype = None
+        L.oracle_forces_p.argtypes = [i64, dp, d, d, d, d, d, d, dp]
+        L.oracle_forces_p.restype = None
         L.oracle_matvec.argtypes = [i64, dp, dp, dp, d, d, dp]
         L.oracle_dense.argtypes = [i64, dp, d, d, dp, dp]
         L.oracle_forces.argtypes = [i64, dp, d, d, d, d, dp]
@@ -120,18 +124,24 @@ def wall_image_tr(x, y, a=1.0):
 
 
 # ---------------------------------------------------------------- matvec and dense
-def mobility_apply(pos, F=None, T=None, a=1.0, eta=1.0, rows=None, wall=True):
+def mobility_apply(pos, F=None, T=None, a=1.0, eta=1.0, rows=None, wall=True, periodic=None):
     """U = M_tt F + M_tr T (Sec. II.B direct summation, Sec. III torque coupling); shape (N, 3).
 
     rows=(i0, i1) restricts the output to targets i0..i1-1 (all N sources are summed).
-    wall=False: the unbounded-domain RPY mobility (no wall terms, no regularisation)."""
+    wall=False: the unbounded-domain RPY mobility (no wall terms, no regularisation).
+    periodic=(Lx, Ly): pseudo-periodic boundaries of Appendix B (minimum image plus the eight
+    neighbour cells, see rpb_oracle.c)."""
     pos = _c3(pos)
     N = pos.shape[0]
     Fc = None if F is None else _c3(F)
     Tc = None if T is None else _c3(T)
     i0, i1 = (0, N) if rows is None else rows
     U = np.zeros((i1 - i0, 3))
-    lib().oracle_matvec_rows_w(N, i0, i1, _p(pos), _p(Fc), _p(Tc), a, eta, int(bool(wall)), _p(U))
+    if periodic is not None:
+        lib().oracle_matvec_rows_p(N, i0, i1, _p(pos), _p(Fc), _p(Tc), a, eta, int(bool(wall)), float(periodic[0]),
+                                   float(periodic[1]), _p(U))
+    else:
+        lib().oracle_matvec_rows_w(N, i0, i1, _p(pos), _p(Fc), _p(Tc), a, eta, int(bool(wall)), _p(U))
     return U
 
 
@@ -145,11 +155,15 @@ def dense(pos, a=1.0, eta=1.0, wall=True):
     return tt, tr
 
 
-def forces(pos, a=1.0, weight=1.0, U0=1.0, b=0.1):
-    """Gravity -weight z plus the soft steric forces of Eq. (soft_potential); shape (N, 3)."""
+def forces(pos, a=1.0, weight=1.0, U0=1.0, b=0.1, periodic=None):
+    """Gravity -weight z plus the soft steric forces of Eq. (soft_potential); shape (N, 3).
+    periodic=(Lx, Ly): minimum image convention (Appendix B)."""
     pos = _c3(pos)
     F = np.zeros_like(pos)
-    lib().oracle_forces(pos.shape[0], _p(pos), a, weight, U0, b, _p(F))
+    if periodic is not None:
+        lib().oracle_forces_p(pos.shape[0], _p(pos), a, weight, U0, b, float(periodic[0]), float(periodic[1]), _p(F))
+    else:
+        lib().oracle_forces(pos.shape[0], _p(pos), a, weight, U0, b, _p(F))
     return F
 
 

@@ -228,6 +228,63 @@ void oracle_forces(int64_t N, const double *pos, double a, double weight, double
     }
 }
 
+/* ------------------------------------------------------------------ pseudo-periodic boundaries
+ * Appendix B: periodic in x and y with periods Lx, Ly; forces by the minimum image convention;
+ * hydrodynamic interactions with the particles of the unit cell and of its eight neighbour cells.
+ * Reading: for each pair the in-plane minimum-image displacement d is taken and the mobility is summed
+ * over the nine shifts d + (nx Lx, ny Ly), nx, ny in {-1, 0, 1}; the pair (i, i) with no shift is the
+ * self block, its eight shifts are ordinary pairs. */
+static double min_image(double d, double L)
+{
+    return d - L * nearbyint(d / L);
+}
+
+void oracle_matvec_rows_p(int64_t N, int64_t i0, int64_t i1, const double *pos, const double *F, const double *T,
+                          double a, double eta, int wall, double Lx, double Ly, double *U)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = i0; i < i1; ++i) {
+        double u[3] = {0.0, 0.0, 0.0};
+        const double *qi = &pos[3 * i];
+        for (int64_t j = 0; j < N; ++j) {
+            const double dx = min_image(qi[0] - pos[3 * j], Lx), dy = min_image(qi[1] - pos[3 * j + 1], Ly);
+            for (int nx = -1; nx <= 1; ++nx)
+                for (int ny = -1; ny <= 1; ++ny) {
+                    const double qj[3] = {qi[0] - (dx + nx * Lx), qi[1] - (dy + ny * Ly), pos[3 * j + 2]};
+                    const int self = (i == j) && nx == 0 && ny == 0;
+                    double Mtt[9], Mtr[9];
+                    oracle_pair_blocks_w(qi, qj, self, a, eta, wall, Mtt, Mtr);
+                    for (int p = 0; p < 3; ++p)
+                        for (int q = 0; q < 3; ++q) {
+                            if (F) u[p] += Mtt[3 * p + q] * F[3 * j + q];
+                            if (T) u[p] += Mtr[3 * p + q] * T[3 * j + q];
+                        }
+                }
+        }
+        for (int p = 0; p < 3; ++p) U[3 * (i - i0) + p] = u[p];
+    }
+}
+
+void oracle_forces_p(int64_t N, const double *pos, double a, double weight, double U0, double b, double Lx, double Ly,
+                     double *F)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < N; ++i) {
+        double f[3] = {0.0, 0.0, -weight};
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double r[3] = {min_image(pos[3 * i] - pos[3 * j], Lx), min_image(pos[3 * i + 1] - pos[3 * j + 1], Ly),
+                           pos[3 * i + 2] - pos[3 * j + 2]};
+            double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            if (rn == 0.0) continue;
+            double m = soft_force(rn, 2.0 * a, U0, b);
+            for (int p = 0; p < 3; ++p) f[p] += m * r[p] / rn;
+        }
+        f[2] += soft_force(pos[3 * i + 2], a, U0, b);
+        for (int p = 0; p < 3; ++p) F[3 * i + p] = f[p];
+    }
+}
+
 /* Raw image tensor at many points (for the surface-quadrature pins): out[9*k ..]. */
 void oracle_blake_image_raw_batch(int64_t n, const double *rx, const double *ry, const double *zi,
                                   const double *zj, double *out)
