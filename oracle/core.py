@@ -182,7 +182,8 @@ def _tridiag_sqrt_e1(alpha, beta):
     return Q @ (np.sqrt(lam) * Q[0, :])
 
 
-def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.0, matvec=None, wall=True):
+def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.0, matvec=None, wall=True,
+                 periodic=None):
     """g_m ~ M_tt^{1/2} W by m steps of Lanczos with full reorthogonalisation.
 
     Readings where the paper is silent (it cites the Krylov method of Ando et al.):
@@ -202,7 +203,7 @@ def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.
     n = w0.size
     if matvec is None:
         def matvec(v):
-            return mobility_apply(pos, v.reshape(-1, 3), None, a, eta, wall=wall).ravel()
+            return mobility_apply(pos, v.reshape(-1, 3), None, a, eta, wall=wall, periodic=periodic).ravel()
     nW = float(np.sqrt(w0 @ w0))
     if nW == 0.0:
         return np.zeros_like(w0).reshape(-1, 3), 0, float("nan"), True
@@ -245,7 +246,7 @@ def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.
 
 
 # ---------------------------------------------------------------- RFD (Sec. II.A)
-def rfd_drift(pos, Wt, delta=1e-6, kT=1.0, a=1.0, eta=1.0, parts=False, one_sided=False):
+def rfd_drift(pos, Wt, delta=1e-6, kT=1.0, a=1.0, eta=1.0, parts=False, one_sided=False, periodic=None):
     """(kT/delta)[M_tt(q + delta/2 W~) W~ - M_tt(q - delta/2 W~) W~]; the displaced configurations
     are regularised anew (clamp and H0 at the displaced heights).  parts=True also returns the two
     matvecs.  one_sided=True: (kT/delta)[M_tt(q + delta W~) W~ - M_tt(q) W~], the one-sided
@@ -253,11 +254,11 @@ def rfd_drift(pos, Wt, delta=1e-6, kT=1.0, a=1.0, eta=1.0, parts=False, one_side
     pos = _c3(pos)
     Wt = _c3(Wt)
     if one_sided:
-        up = mobility_apply(pos + delta * Wt, Wt, None, a, eta)
-        um = mobility_apply(pos, Wt, None, a, eta)
+        up = mobility_apply(pos + delta * Wt, Wt, None, a, eta, periodic=periodic)
+        um = mobility_apply(pos, Wt, None, a, eta, periodic=periodic)
     else:
-        up = mobility_apply(pos + 0.5 * delta * Wt, Wt, None, a, eta)
-        um = mobility_apply(pos - 0.5 * delta * Wt, Wt, None, a, eta)
+        up = mobility_apply(pos + 0.5 * delta * Wt, Wt, None, a, eta, periodic=periodic)
+        um = mobility_apply(pos - 0.5 * delta * Wt, Wt, None, a, eta, periodic=periodic)
     d = (kT / delta) * (up - um)
     if parts:
         return d, up, um
@@ -274,7 +275,7 @@ def noise(N, seed, step, stream, instance=0):
 # ---------------------------------------------------------------- AB step (Eq. AB)
 def ab_step(pos, U_prev, step, seed, dt=0.01, delta=1e-6, tol=1e-3, max_iter=100, kT=1.0, a=1.0, eta=1.0,
             weight=1.0, torque=(0.0, 1.0, 0.0), U0=1.0, b=0.1, exact_iters=None, detail=False, scheme="AB",
-            one_sided=False):
+            one_sided=False, periodic=None):
     """One stochastic Adams-Bashforth step (scheme="AB", Eq. AB) or Euler-Maruyama step
     (scheme="EM", Eq. EM: q^{n+1} = q^n + dt U^n + sqrt(2 kT dt) g + dt drift).
 
@@ -284,13 +285,13 @@ def ab_step(pos, U_prev, step, seed, dt=0.01, delta=1e-6, tol=1e-3, max_iter=100
     Returns (q^{n+1}, U^n, info)."""
     pos = _c3(pos)
     N = pos.shape[0]
-    F = forces(pos, a, weight, U0, b)
+    F = forces(pos, a, weight, U0, b, periodic=periodic)
     T = np.tile(np.asarray(torque, dtype=np.float64), (N, 1))
-    Un = mobility_apply(pos, F, T, a, eta)
+    Un = mobility_apply(pos, F, T, a, eta, periodic=periodic)
     W = noise(N, seed, step, 0)
     Wt = noise(N, seed, step, 1)
-    g, m, eps, conv = lanczos_sqrt(pos, W, tol, max_iter, exact_iters, a, eta)
-    d, up, um = rfd_drift(pos, Wt, delta, kT, a, eta, parts=True, one_sided=one_sided)
+    g, m, eps, conv = lanczos_sqrt(pos, W, tol, max_iter, exact_iters, a, eta, periodic=periodic)
+    d, up, um = rfd_drift(pos, Wt, delta, kT, a, eta, parts=True, one_sided=one_sided, periodic=periodic)
     Up = Un if (scheme == "EM" or step == 0 or U_prev is None) else _c3(U_prev)
     new = pos + dt * (1.5 * Un - 0.5 * Up) + math.sqrt(2.0 * kT * dt) * g + dt * d
     info = dict(m=m, eps=eps, converged=conv)
