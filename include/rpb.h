@@ -90,6 +90,13 @@ int rpb_destroy(rpb_ctx *ctx);
 /* Change the stream later calls enqueue on. */
 int rpb_set_stream(rpb_ctx *ctx, void *stream);
 
+/* Pseudo-periodic boundaries parallel to the wall (Appendix B): periods Lx, Ly (> 4a), or both 0 to
+ * switch them off (the default).  When on, forces use the minimum image convention and the products
+ * sum every source's minimum image and its eight shifts by one period (the unit cell and its eight
+ * neighbour cells), i.e. nine times the pair work, with one-way kernels; positions may lie outside
+ * the cell (they are folded in for the computation, and returned unfolded). */
+int rpb_set_periodic(rpb_ctx *ctx, double Lx, double Ly);
+
 /* U = M_tt F + M_tr T  (Sec. II.B Eq. mobilityDifferential and mobilityOverlap; Sec. III Eq.
  * mobilityDifferentialTR; regularisation M = B Mtilde B of Appendix A Eq. effMob, applied to
  * both blocks).  pos: 3N positions.  F, T: 3N forces and torques; either may be NULL (treated

@@ -71,7 +71,7 @@ static int check_vec(const void *p, const char *name, bool nullable)
 
 static void free_ws(Workspace &w)
 {
-    void *dev[] = {w.src, w.partial, w.V, w.w, w.red, w.lz, w.pos_a, w.pos_b,
+    void *dev[] = {w.src, w.partial, w.V, w.w, w.red, w.lz, w.pos_a, w.pos_b, w.pos_w,
                    w.vec_a, w.vec_b, w.vec_c, w.vec_d, w.vec_e, w.vec_f, w.vec_g,
                    w.sym_index, w.sym_tgt, w.sym_src};
     for (void *p : dev)
@@ -155,6 +155,7 @@ int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, 
         {(void **)&w.lz, lanczos_state_elems(max_iter) * sizeof(double)},
         {(void **)&w.pos_a, vb},
         {(void **)&w.pos_b, vb},
+        {(void **)&w.pos_w, vb},
         {(void **)&w.vec_a, vb},
         {(void **)&w.vec_b, vb},
         {(void **)&w.vec_c, vb},
@@ -228,6 +229,23 @@ int rpb_set_stream(rpb_ctx *ctx, void *stream)
         return RPB_EINVAL;
     }
     ctx->stream = (cudaStream_t)stream;
+    return RPB_OK;
+}
+
+int rpb_set_periodic(rpb_ctx *ctx, double Lx, double Ly)
+{
+    g_err[0] = 0;
+    if (!ctx) {
+        set_error("null context");
+        return RPB_EINVAL;
+    }
+    const bool off = Lx == 0.0 && Ly == 0.0;
+    if (!off && !(Lx > 4.0 * ctx->p.a && Ly > 4.0 * ctx->p.a && std::isfinite(Lx) && std::isfinite(Ly))) {
+        set_error("periods must both be 0 or both exceed 4a (Lx=%g Ly=%g)", Lx, Ly);
+        return RPB_EINVAL;
+    }
+    ctx->Lx = off ? 0.0 : Lx;
+    ctx->Ly = off ? 0.0 : Ly;
     return RPB_OK;
 }
 

@@ -605,6 +605,125 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
     }
 }
 
+// ------------------------------------------------------------------ pseudo-periodic boundaries
+// Positions folded into the unit cell [0, Lx) x [0, Ly) (heights unchanged).
+__global__ void wrap_kernel(const double *__restrict__ pos, int N, double Lx, double Ly, double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double x = pos[i], y = pos[N + i];
+    out[i] = x - Lx * floor(x / Lx);
+    out[N + i] = y - Ly * floor(y / Ly);
+    out[2 * N + i] = pos[2 * N + i];
+}
+
+// Appendix B: periodic in x and y; each source is taken at its minimum image and at the eight shifts of
+// it by one period (the unit cell and its eight neighbour cells).  One-way kernels (the symmetric
+// pass is not used in this mode).  The pack kernel has wrapped every position into the unit cell, so
+// in-plane offsets lie in (-L, L) and the minimum-image correction is 0 or +-L.  The sphere's own
+// unshifted image is the self term (added by the reduce kernel); its eight shifted images are pairs.
+template <bool TORQUE, bool WALL>
+__global__ void __launch_bounds__(kPairThreads) pair_periodic_f64_kernel(const SrcF64 *__restrict__ src, int N,
+                                                                          int chunk, PairConsts<double> c, double Lx,
+                                                                          double Ly, double *__restrict__ part)
+{
+    __shared__ SrcF64 ss[kTile];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kPairThreads + tid;
+    const int j0 = blockIdx.y * chunk;
+    const int j1 = min(N, j0 + chunk);
+    double2 tp = make_double2(0.0, 0.0);
+    double tz = 1.0;
+    if (i < N) {
+        tp = src[i].p;
+        tz = src[i].q.x;
+    }
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int base = j0; base < j1; base += kTile) {
+        if (base + tid < j1) ss[tid] = src[base + tid];
+        __syncthreads();
+        const int cnt = min(kTile, j1 - base);
+        for (int k = 0; k < cnt; ++k) {
+            const SrcF64 s = ss[k];
+            double dx = tp.x - s.p.x, dy = tp.y - s.p.y;
+            dx -= Lx * rint(dx / Lx);
+            dy -= Ly * rint(dy / Ly);
+            const bool self = base + k == i;
+            for (int nx = -1; nx <= 1; ++nx)
+                for (int ny = -1; ny <= 1; ++ny) {
+                    if (self && nx == 0 && ny == 0) continue;
+                    pair_velocity<double, TORQUE, WALL>(dx + nx * Lx, dy + ny * Ly, tz, s.q.x, s.q.y, s.r.x, s.r.y,
+                                                        s.s.x, s.s.y, s.u.x, c, ux, uy, uz);
+                }
+        }
+        __syncthreads();
+    }
+    if (i < N) {
+        const size_t o = (size_t)blockIdx.y * 3 * N;
+        part[o + i] = ux;
+        part[o + N + i] = uy;
+        part[o + 2 * N + i] = uz;
+    }
+}
+
+// Float32 version; the period is split L = L_hi + L_lo like the positions.
+template <bool TORQUE, bool WALL>
+__global__ void __launch_bounds__(kPairThreads) pair_periodic_f32_kernel(const SrcF32 *__restrict__ src, int N,
+                                                                          int chunk, PairConsts<float> c, float Lxh,
+                                                                          float Lxl, float Lyh, float Lyl,
+                                                                          double *__restrict__ part)
+{
+    __shared__ SrcF32 ss[kTile];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kPairThreads + tid;
+    const int j0 = blockIdx.y * chunk;
+    const int j1 = min(N, j0 + chunk);
+    float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float tz = 1.f;
+    if (i < N) {
+        tp = src[i].p;
+        tz = src[i].f.x;
+    }
+    const float ix = 1.f / Lxh, iy = 1.f / Lyh;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int base = j0; base < j1; base += kTile) {
+        if (base + tid < j1) ss[tid] = src[base + tid];
+        __syncthreads();
+        const int cnt = min(kTile, j1 - base);
+        float ux = 0.f, uy = 0.f, uz = 0.f;
+        for (int k = 0; k < cnt; ++k) {
+            const SrcF32 s = ss[k];
+            float dx = (tp.x - s.p.x) + (tp.z - s.p.z);
+            float dy = (tp.y - s.p.y) + (tp.w - s.p.w);
+            const float mx = rintf(dx * ix), my = rintf(dy * iy);
+            dx = (dx - mx * Lxh) - mx * Lxl;
+            dy = (dy - my * Lyh) - my * Lyl;
+            const bool self = base + k == i;
+            for (int nx = -1; nx <= 1; ++nx)
+                for (int ny = -1; ny <= 1; ++ny) {
+                    float ax = 0.f, ay = 0.f, az = 0.f;
+                    pair_velocity_f32<TORQUE, WALL>((dx + nx * Lxh) + nx * Lxl, (dy + ny * Lyh) + ny * Lyl, tz, s.f.x,
+                                                    s.f.y, s.f.z, s.f.w, s.t.x, s.t.y, s.t.z, c, ax, ay, az);
+                    if (!(self && nx == 0 && ny == 0)) {
+                        ux += ax;
+                        uy += ay;
+                        uz += az;
+                    }
+                }
+        }
+        sx += ux;
+        sy += uy;
+        sz += uz;
+        __syncthreads();
+    }
+    if (i < N) {
+        const size_t o = (size_t)blockIdx.y * 3 * N;
+        part[o + i] = sx;
+        part[o + N + i] = sy;
+        part[o + 2 * N + i] = sz;
+    }
+}
+
 // Sum the chunk partials in order, add the float64 self term, apply s_i / (8 pi eta).
 __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, int N, const double *__restrict__ pos,
                                    const double *__restrict__ F, const double *__restrict__ T, PairConsts<double> c,
@@ -661,7 +780,8 @@ size_t pair_partial_bytes(int64_t max_N, int num_sms)
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, double *U)
 {
     const int N = (int)N64;
-    if (ctx->sym_enabled && ctx->p.wall && F && !T && N >= 2 * kTile) return mobility_tt_sym(ctx, N, pos, F, U);
+    if (ctx->sym_enabled && ctx->p.wall && !(ctx->Lx > 0.0) && F && !T && N >= 2 * kTile)
+        return mobility_tt_sym(ctx, N, pos, F, U);
     cudaStream_t st = ctx->stream;
     const double a = ctx->p.a;
     int splits;
@@ -675,6 +795,42 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
     const int pb = 256;
     const dim3 grid((unsigned)((N + kPairThreads - 1) / kPairThreads), (unsigned)splits);
     const bool torque = T != nullptr;
+    if (ctx->Lx > 0.0) {  // pseudo-periodic: wrap into the unit cell, pack, nine shifts per source
+        const double Lx = ctx->Lx, Ly = ctx->Ly;
+        wrap_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, N, Lx, Ly, ctx->ws.pos_w);
+        const double *pw = ctx->ws.pos_w;
+        if (ctx->p.precision == RPB_FP32) {
+            SrcF32 *src = (SrcF32 *)ctx->ws.src;
+            pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pw, F, T, N, a, ctx->p.wall, src);
+            const PairConsts<float> c = make_consts<float>(a);
+            const float Lxh = (float)Lx, Lyh = (float)Ly;
+            const float Lxl = (float)(Lx - (double)Lxh), Lyl = (float)(Ly - (double)Lyh);
+            if (torque && ctx->p.wall)
+                pair_periodic_f32_kernel<true, true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lxh, Lxl, Lyh, Lyl, part);
+            else if (torque)
+                pair_periodic_f32_kernel<true, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lxh, Lxl, Lyh, Lyl, part);
+            else if (ctx->p.wall)
+                pair_periodic_f32_kernel<false, true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lxh, Lxl, Lyh, Lyl, part);
+            else
+                pair_periodic_f32_kernel<false, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lxh, Lxl, Lyh, Lyl, part);
+        } else {
+            SrcF64 *src = (SrcF64 *)ctx->ws.src;
+            pack_f64_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pw, F, T, N, a, ctx->p.wall, src);
+            const PairConsts<double> c = make_consts<double>(a);
+            if (torque && ctx->p.wall)
+                pair_periodic_f64_kernel<true, true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lx, Ly, part);
+            else if (torque)
+                pair_periodic_f64_kernel<true, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lx, Ly, part);
+            else if (ctx->p.wall)
+                pair_periodic_f64_kernel<false, true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lx, Ly, part);
+            else
+                pair_periodic_f64_kernel<false, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lx, Ly, part);
+        }
+        pair_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(part, splits, N, pos, F, T, make_consts<double>(a), a,
+                                                              1.0 / (8.0 * kPi * ctx->p.eta), U, ctx->p.wall);
+        count_launches(4);
+        return cuda_fail(cudaGetLastError(), "periodic pair kernels");
+    }
     if (ctx->p.precision == RPB_FP32) {
         SrcF32 *src = (SrcF32 *)ctx->ws.src;
         pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, ctx->p.wall, src);
@@ -723,8 +879,12 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
 // F_i = -weight z + sum_j f(|r_ij|) r_ij/|r_ij| + f_wall(z_i) z with f = -dU/dr of Eq. (soft_potential).
 // Pairs are screened in float32 against a cutoff with a generous margin; the ones inside are
 // evaluated in float64.
+// PER: pseudo-periodic boundaries (Appendix B), minimum image in x (period Lx) and y (period Ly); the
+// positions are then the ones folded into the unit cell.
+template <bool PER>
 __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ pos, int N, double a, double weight,
-                                                     double U0, double b, float cut2, double *__restrict__ F)
+                                                     double U0, double b, float cut2, double *__restrict__ F,
+                                                     double Lx = 0.0, double Ly = 0.0)
 {
     __shared__ float4 sp[64];  // float32 copies of the tile's positions, for the screen only
     const int tid = threadIdx.x;
@@ -747,7 +907,12 @@ __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ 
     auto flush = [&]() {
         for (int q = 0; q < nq; ++q) {
             const int jj = queue[q];
-            const double dx = xi - pos[jj], dy = yi - pos[N + jj], dz = zi - pos[2 * N + jj];
+            double dx = xi - pos[jj], dy = yi - pos[N + jj];
+            const double dz = zi - pos[2 * N + jj];
+            if (PER) {
+                dx -= Lx * rint(dx / Lx);
+                dy -= Ly * rint(dy / Ly);
+            }
             const double r = sqrt(dx * dx + dy * dy + dz * dz);
             if (r > 0.0) {
                 const double m = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
@@ -764,27 +929,37 @@ __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ 
     float *fxy = reinterpret_cast<float *>(sp);
     float *fz2 = reinterpret_cast<float *>(sz);
     const float2 X = make_float2(xf, xf), Y = make_float2(yf, yf), Z = make_float2(zf, zf);
+    const float fLx = (float)Lx, fLy = (float)Ly;
+    const float fiLx = PER ? 1.f / fLx : 0.f, fiLy = PER ? 1.f / fLy : 0.f;
     const int pp = tid >> 1, hh = tid & 1;
     for (int base = 0; base < N; base += 128) {
         const int j = base + tid;
-        // slots past N hold a far-away point that never passes the screen
+        // slots past N hold a point far above the wall (never inside the screen, also after the
+        // minimum-image fold of x and y); the queue test re-checks the index
         const bool in = j < N;
-        fxy[4 * pp + hh] = in ? (float)pos[j] : 1e18f;
+        fxy[4 * pp + hh] = in ? (float)pos[j] : 0.f;
         fxy[4 * pp + 2 + hh] = in ? (float)pos[N + j] : 0.f;
-        fz2[2 * pp + hh] = in ? (float)pos[2 * N + j] : 0.f;
+        fz2[2 * pp + hh] = in ? (float)pos[2 * N + j] : 1e18f;
         __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < 64; ++k) {
             const float4 p = sp[k];
-            const float2 dx = sub2(X, make_float2(p.x, p.y)), dy = sub2(Y, make_float2(p.z, p.w)), dz = sub2(Z, sz[k]);
+            float2 dx = sub2(X, make_float2(p.x, p.y)), dy = sub2(Y, make_float2(p.z, p.w));
+            const float2 dz = sub2(Z, sz[k]);
+            if (PER) {
+                dx.x -= fLx * rintf(dx.x * fiLx);
+                dx.y -= fLx * rintf(dx.y * fiLx);
+                dy.x -= fLy * rintf(dy.x * fiLy);
+                dy.y -= fLy * rintf(dy.y * fiLy);
+            }
             const float2 d2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
             if (d2.x < cut2 || d2.y < cut2) {  // rare: a near pair (or the sphere itself)
                 const int j0 = base + 2 * k;
-                if (d2.x < cut2 && j0 != i) {
+                if (d2.x < cut2 && j0 != i && j0 < N) {
                     queue[nq++] = j0;
                     if (nq == kQ) flush();
                 }
-                if (d2.y < cut2 && j0 + 1 != i) {
+                if (d2.y < cut2 && j0 + 1 != i && j0 + 1 < N) {
                     queue[nq++] = j0 + 1;
                     if (nq == kQ) flush();
                 }
@@ -807,9 +982,17 @@ int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_para
     const double rc = 2.0 * a + 50.0 * fp->b;
     const double rcm = rc * 1.01 + 0.01 * a;
     const float cut2 = (float)(rcm * rcm);
-    forces_kernel<<<(unsigned)((N + 127) / 128), 128, 0, ctx->stream>>>(pos, (int)N, a, fp->weight, fp->U0, fp->b,
-                                                                          cut2, F);
-    count_launches(1);
+    if (ctx->Lx > 0.0) {
+        const int pb = 256;
+        wrap_kernel<<<(unsigned)((N + pb - 1) / pb), pb, 0, ctx->stream>>>(pos, (int)N, ctx->Lx, ctx->Ly, ctx->ws.pos_w);
+        forces_kernel<true><<<(unsigned)((N + 127) / 128), 128, 0, ctx->stream>>>(
+            ctx->ws.pos_w, (int)N, a, fp->weight, fp->U0, fp->b, cut2, F, ctx->Lx, ctx->Ly);
+        count_launches(2);
+    } else {
+        forces_kernel<false><<<(unsigned)((N + 127) / 128), 128, 0, ctx->stream>>>(pos, (int)N, a, fp->weight, fp->U0,
+                                                                                    fp->b, cut2, F);
+        count_launches(1);
+    }
     return cuda_fail(cudaGetLastError(), "forces kernel");
 }
 

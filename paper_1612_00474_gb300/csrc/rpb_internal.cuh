@@ -71,6 +71,7 @@ struct Workspace {
     double *lz = nullptr;         // Lanczos small state (alpha, beta, y, y_prev, coefficients, status)
     double *pos_a = nullptr;      // displaced positions (RFD), 3 max_N
     double *pos_b = nullptr;
+    double *pos_w = nullptr;      // positions folded into the unit cell (pseudo-periodic mode), 3 max_N
     double *vec_a = nullptr;      // 3 max_N scratch vectors for the AB step
     double *vec_b = nullptr;
     double *vec_c = nullptr;
@@ -99,6 +100,7 @@ struct rpb_ctx {
     int num_sms;
     int fp32_variant;  // float32 pair kernel: 1 = packed float32x2 (default), 0 = scalar; env RPB_FP32_PAIR
     int sym_enabled;   // float32 translation-translation products use the symmetric pass; env RPB_FP32_SYM=0 off
+    double Lx = 0.0, Ly = 0.0;  // pseudo-periodic periods (0: unbounded in-plane), rpb_set_periodic
     rpb::Workspace ws;
 };
 

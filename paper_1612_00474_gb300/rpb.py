@@ -22,7 +22,8 @@ PRECISIONS = {"fp64": RPB_FP64, "fp32": RPB_FP32}
 EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", "rpb_lanczos_sqrt_apply",
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
            "rpb_launch_count", "rpb_mobility_apply_noalloc", "rpb_batch_create", "rpb_batch_destroy",
-           "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step", "rpb_batch_run")
+           "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step", "rpb_batch_run",
+           "rpb_set_periodic")
 SCHEMES = {"AB": 0, "EM": 1}
 RFDS = {"centred": 0, "one-sided": 1}
 NOALLOC_MAX_N = 16384
@@ -82,6 +83,7 @@ def load(build_if_missing=True):
     L.rpb_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), i64, i32, vp]
     L.rpb_destroy.argtypes = [vp]
     L.rpb_set_stream.argtypes = [vp, vp]
+    L.rpb_set_periodic.argtypes = [vp, d, d]
     L.rpb_mobility_apply.argtypes = [vp, i64, vp, vp, vp, vp]
     L.rpb_lanczos_sqrt_apply.argtypes = [vp, i64, vp, vp, vp, d, i32, ctypes.POINTER(i32), ctypes.POINTER(d)]
     L.rpb_rfd_drift.argtypes = [vp, i64, vp, vp, d, vp]
@@ -197,6 +199,10 @@ class Context:
 
     def _bind_stream(self):
         _check(load().rpb_set_stream(self._h, _stream()))
+
+    def set_periodic(self, Lx, Ly):
+        """Pseudo-periodic boundaries with periods (Lx, Ly); (0, 0) switches them off (rpb_set_periodic)."""
+        _check(load().rpb_set_periodic(self._h, float(Lx), float(Ly)))
 
     @staticmethod
     def _empty(n, like):

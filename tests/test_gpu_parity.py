@@ -311,3 +311,98 @@ def test_checkpoint_resume_bitwise(gpu_lib):
     run(qc, Uc, range(3, 6), c2)
     c2.close()
     assert torch.equal(qa, qc) and torch.equal(Ua, Uc)
+
+
+# ------------------------------------------------------------------ pseudo-periodic boundaries (Appendix B)
+LXY = (20.0, 17.5)
+
+
+def periodic_config(N, seed, L=LXY):
+    """Spheres scattered over the cell and its neighbours (so the library must fold them), with pairs
+    that straddle an edge and a corner of the cell."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros((N, 3))
+    p[:, 0] = rng.uniform(-0.5 * L[0], 1.5 * L[0], N)
+    p[:, 1] = rng.uniform(-0.5 * L[1], 1.5 * L[1], N)
+    p[:, 2] = rng.uniform(0.8, 3.0, N)
+    fixed = [[0.3, 0.5 * L[1], 1.2], [L[0] - 0.6, 0.5 * L[1], 1.3], [0.2, 0.2, 1.1], [L[0] - 0.4, L[1] - 0.3, 1.0]]
+    k = min(N, 4)
+    p[:k] = np.array(fixed[:k])
+    return p
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("N", [1, 4, 129, 300])
+def test_periodic_mobility(gpu_lib, prec, tol, N):
+    pos = periodic_config(N, 600 + N)
+    F, T = inputs.vectors(N, 5), inputs.vectors(N, 6)
+    ctx = gpu_lib.Context(max_N=N, precision=prec, max_iter=16)
+    try:
+        ctx.set_periodic(*LXY)
+        got = host(ctx.mobility_apply(dev(pos), dev(F), dev(T)), N)
+        got_tt = host(ctx.mobility_apply(dev(pos), dev(F)), N)
+        ctx.set_periodic(0.0, 0.0)
+        got_open = host(ctx.mobility_apply(dev(pos), dev(F)), N)
+    finally:
+        ctx.close()
+    assert maxrel(got, O.mobility_apply(pos, F, T, periodic=LXY)) <= tol
+    assert maxrel(got_tt, O.mobility_apply(pos, F, None, periodic=LXY)) <= tol
+    assert maxrel(got_open, O.mobility_apply(pos, F, None)) <= tol
+
+
+def test_periodic_mobility_fp32_symmetric_size(gpu_lib):
+    """N large enough that a float32 context would take the symmetric pass without periodicity."""
+    N = 640
+    pos = periodic_config(N, 77, L=(40.0, 36.0))
+    F = inputs.vectors(N, 7)
+    ctx = gpu_lib.Context(max_N=N, precision="fp32", max_iter=16)
+    try:
+        ctx.set_periodic(40.0, 36.0)
+        got = host(ctx.mobility_apply(dev(pos), dev(F)), N)
+    finally:
+        ctx.close()
+    assert maxrel(got, O.mobility_apply(pos, F, None, periodic=(40.0, 36.0))) <= 1e-5
+
+
+@pytest.mark.parametrize("N", [2, 300])
+def test_periodic_forces(gpu_lib, N):
+    pos = periodic_config(N, 700 + N)
+    ctx = gpu_lib.Context(max_N=N, precision="fp64", max_iter=16)
+    try:
+        ctx.set_periodic(*LXY)
+        got = host(ctx.forces(dev(pos), weight=1.0, U0=1.0, b=0.1), N)
+    finally:
+        ctx.close()
+    ref = O.forces(pos, 1.0, 1.0, 1.0, 0.1, periodic=LXY)
+    assert maxrel(got, ref) <= 1e-12
+
+
+def test_periodic_step(gpu_lib):
+    N = 64
+    L = (12.0, 11.0)
+    pos0 = periodic_config(N, 31, L=L)
+    Uprev = inputs.vectors(N, 32, scale=0.01)
+    ctx = gpu_lib.Context(max_N=N, precision="fp64", max_iter=64)
+    try:
+        ctx.set_periodic(*L)
+        q, U = dev(pos0), dev(Uprev)
+        st = ctx.step(q, U, 2, 5, scheme="AB", dt=0.01, delta=1e-6, tol=1e-3)
+    finally:
+        ctx.close()
+    new_ref, Un_ref, info = O.ab_step(pos0, Uprev, 2, seed=5, dt=0.01, delta=1e-6, tol=1e-3, periodic=L)
+    assert st["m"] == info["m"]
+    assert maxrel(host(U, N), Un_ref) <= 1e-10
+    assert maxrel(host(q, N) - pos0, new_ref - pos0) <= 1e-8
+
+
+def test_periodic_invalid(gpu_lib):
+    ctx = gpu_lib.Context(max_N=8, precision="fp64", max_iter=8)
+    try:
+        with pytest.raises(gpu_lib.RpbError):
+            ctx.set_periodic(3.0, 3.0)      # not above 4a
+        with pytest.raises(gpu_lib.RpbError):
+            ctx.set_periodic(10.0, 0.0)     # one direction only
+        with pytest.raises(gpu_lib.RpbError):
+            ctx.set_periodic(float("nan"), 10.0)
+    finally:
+        ctx.close()
