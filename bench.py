@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--periodic", action="store_true",
+                    help="monolayer: pseudo-periodic boundaries with the monolayer's square as the unit cell")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy"],
                     default="monolayer")
@@ -65,30 +67,39 @@ def parse():
     return ap.parse_args()
 
 
+def cell_side(N, phi=0.4):
+    """Side of the square the monolayer generator fills (a = 1)."""
+    return math.sqrt(N * math.pi / phi)
+
+
 def workload_name(args):
+    per = (f", pseudo-periodic {cell_side(args.N):.2f}a x {cell_side(args.N):.2f}a cell (unit cell + 8 neighbours)"
+           if args.periodic else "")
     return (f"roller monolayer N={args.N} (phi=0.4, z=a+Exp(0.5a), gravity -1 z, torque +1 y, U0=1, b=0.1a), "
-            f"AB step dt={args.dt}, RFD delta={args.delta}, Lanczos tol={args.tol}, {args.precision} pairs")
+            f"AB step dt={args.dt}, RFD delta={args.delta}, Lanczos tol={args.tol}, {args.precision} pairs{per}")
 
 
-def oracle_sample(N, seed, seconds):
-    """Time the FP64 oracle's fused product on a row sample of the workload; returns Gpairs/s and info."""
+def oracle_sample(N, seed, seconds, periodic=None):
+    """Time the FP64 oracle's fused product on a row sample of the workload; returns Gpairs/s and info
+    (pair evaluations: nine per pair with pseudo-periodic boundaries)."""
     import oracle as O
     from paper_1612_00474_gb300 import inputs
 
     pos = inputs.monolayer(N, seed=seed)
     F = np.tile([0.0, 0.0, -1.0], (N, 1))
     T = np.tile([0.0, 1.0, 0.0], (N, 1))
-    O.mobility_apply(pos, F, T, rows=(0, 4))  # start the OpenMP pool
-    rows = 64
+    images = 9 if periodic else 1
+    O.mobility_apply(pos, F, T, rows=(0, 4), periodic=periodic)  # start the OpenMP pool
+    rows = 64  # 16 chunks of 4 rows: every OpenMP thread of the host busy while calibrating
     t0 = time.perf_counter()
-    O.mobility_apply(pos, F, T, rows=(0, rows))
+    O.mobility_apply(pos, F, T, rows=(0, rows), periodic=periodic)
     dt = time.perf_counter() - t0
     rows = int(max(8, min(N, rows * seconds / max(dt, 1e-6))))
     t0 = time.perf_counter()
-    O.mobility_apply(pos, F, T, rows=(0, rows))
+    O.mobility_apply(pos, F, T, rows=(0, rows), periodic=periodic)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return rows * N / dt / 1e9, dict(rows=rows, seconds=dt, cores=cores)
+    return images * rows * N / dt / 1e9, dict(rows=rows, seconds=dt, cores=cores)
 
 
 def clocks_start(device_index):
@@ -138,7 +149,8 @@ def run_reference(args, rank, world):
     vals = []
     info = None
     for k in range(args.warmup + args.steps):
-        v, info = oracle_sample(N, args.seed, per_step)
+        v, info = oracle_sample(N, args.seed, per_step,
+                                periodic=(cell_side(N), cell_side(N)) if args.periodic else None)
         if k >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
@@ -192,6 +204,10 @@ def run_ours(args, rank, world, local_rank):
     N = args.N
     seed = args.seed + rank  # independent replicas, one suspension per rank
     ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=64)
+    images = 1
+    if args.periodic:
+        ctx.set_periodic(cell_side(N), cell_side(N))
+        images = 9  # each source at its minimum image and the eight neighbour-cell shifts
     pos0 = inputs.monolayer(N, seed=seed)
     q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
     Up = torch.zeros_like(q)
@@ -226,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
     launches = rpb.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ms]
     total_s = sum(step_ms) / 1e3
-    pairs = float(N) * N * sum(3 + m for m in ms_list)
+    pairs = images * float(N) * N * sum(3 + m for m in ms_list)
 
     # end to end through the C ABI with host buffers: copy state in, step, copy state out
     h_q = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
@@ -250,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_m.append(st["m"])
         step += 1
     clocks = clocks_stop(clk)
-    e2e_pairs = float(N) * N * sum(3 + m for m in e2e_m)
+    e2e_pairs = images * float(N) * N * sum(3 + m for m in e2e_m)
     e2e_s = sum(e2e_ms) / 1e3
 
     # dominant kernel: the translation-translation pair pass (m + 2 of the 3 + m passes per step),
@@ -282,7 +298,8 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, info = oracle_sample(N, args.seed, args.cpu_seconds)
+        per = (cell_side(N), cell_side(N)) if args.periodic else None
+        v, info = oracle_sample(N, args.seed, args.cpu_seconds, periodic=per)
         cpu = {"value": v, "unit": "Gpairs/s", "cores": info["cores"], "kind": "oracle",
                "sample": (f"fused M_tt F + M_tr T of the N={N} monolayer on {info['rows']} target rows x {N} "
                           f"sources ({info['seconds']:.1f} s, FP64 oracle, OpenMP over target rows)")}
@@ -290,8 +307,12 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
         peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        sym = args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256
-        if sym:  # each unordered pair once (171 flop) except inside the 128-wide diagonal tiles (126 flop each way)
+        sym = (args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256
+               and not args.periodic)
+        if args.periodic:
+            flops_tt = 9.0 * N * N * FLOPS_TT
+            kernel = f"pair_periodic_f{args.precision[2:]}_kernel<false,true> (translation-translation, 9 images)"
+        elif sym:  # each unordered pair once (171 flop) except inside the 128-wide diagonal tiles (126 flop each way)
             diag = float(N) * 128
             flops_tt = FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag
             kernel = "pair_f32x2_sym_kernel (translation-translation, reciprocity)"
@@ -307,12 +328,14 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": workload_name(args), "N": N, "precision": args.precision,
                        "pair_arith": args.precision, "lanczos_arith": "f64", "parallelism": f"replicas x{world}",
-                       "l2": "256 MB buffer written between timed steps"},
+                       "l2": "256 MB buffer written between timed steps",
+                       "periodic": [cell_side(N)] * 2 if args.periodic else None,
+                       "pair_evaluations_per_product": images * N * N},
             "steps_per_s": args.steps * world / total_s,
             "lanczos_m": ms_list,
             "step_ms": [round(x, 3) for x in step_ms],
             "matvec": {"tt_ms": t_tt * 1e3, "fused_ms": t_fused * 1e3,
-                       "tt_gpairs_s": N * N / t_tt / 1e9, "fused_gpairs_s": N * N / t_fused / 1e9},
+                       "tt_gpairs_s": images * N * N / t_tt / 1e9, "fused_gpairs_s": images * N * N / t_fused / 1e9},
             "roofline": {"bound": "alu", "kernel": kernel,
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
