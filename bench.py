@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--periodic", action="store_true",
                     help="monolayer: pseudo-periodic boundaries with the monolayer's square as the unit cell")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy"],
+    ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy", "small"],
                     default="monolayer")
     ap.add_argument("--acc-steps", type=int, default=10, help="accuracy: steps compared with the oracle")
     ap.add_argument("--lanczos-iters", type=int, default=12,
@@ -627,6 +627,130 @@ def run_accuracy(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+_ORACLE_TIMING = r"""
+import json, os, sys, time
+import oracle as O
+from paper_1612_00474_gb300 import inputs
+res = {}
+threads = int(os.environ.get("OMP_NUM_THREADS", "1"))
+for N in ((256, 4096) if sys.argv[2] == "1" else (256,)):
+    q = inputs.monolayer(N, seed=0)
+    if N == 256:
+        O.ab_step(q, None, 0, seed=0, dt=0.01, delta=1e-6, tol=1e-3)
+    t0 = time.perf_counter()
+    O.ab_step(q, None, 0, seed=0, dt=0.01, delta=1e-6, tol=1e-3)
+    res[f"ab_step_N{N}_s"] = time.perf_counter() - t0
+N = 4096
+q = inputs.monolayer(N, seed=0)
+F = [[0.0, 0.0, -1.0]] * N
+T = [[0.0, 1.0, 0.0]] * N
+t0 = time.perf_counter()
+O.mobility_apply(q, F, T)
+res["fused_product_N4096_s"] = time.perf_counter() - t0
+N = 65536
+q = inputs.monolayer(N, seed=0)
+F = [[0.0, 0.0, -1.0]] * N
+T = [[0.0, 1.0, 0.0]] * N
+rows = max(8, 4 * threads)
+t0 = time.perf_counter()
+O.mobility_apply(q, F, T, rows=(0, rows))
+dt = time.perf_counter() - t0
+rows = int(max(8, min(N, rows * float(sys.argv[1]) / max(dt, 1e-6))))
+t0 = time.perf_counter()
+O.mobility_apply(q, F, T, rows=(0, rows))
+dt = time.perf_counter() - t0
+res["fused_product_N65536_gpairs_s"] = rows * N / dt / 1e9
+res["fused_product_N65536_rows"] = rows
+print(json.dumps(res))
+"""
+
+
+def oracle_timing(threads, seconds, step_4096=True):
+    """FP64 oracle timings on `threads` host threads, in a fresh interpreter (the OpenMP pool size is
+    fixed at first use): one full AB step at N = 256 (and at N = 4096 if step_4096), one fused product
+    at N = 4096, and the fused product of the N = 65536 monolayer on a row sample of about `seconds`
+    seconds."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    here = os.path.dirname(os.path.abspath(__file__))
+    out = subprocess.run([sys.executable, "-c", _ORACLE_TIMING, str(seconds), "1" if step_4096 else "0"], env=env,
+                         cwd=here,
+                         capture_output=True, text=True, check=True)
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res["threads"] = threads
+    return res
+
+
+def run_small(args, rank, world, local_rank):
+    """The 256-sphere configuration (seed 0, FP64 pairs, dt = 0.01, delta = 1e-6, tol = 1e-3):
+    microseconds per AB step on the GPU through rpb_ab_step (the host reads the Lanczos status back
+    after every iteration) and through a graph-replayed rpb_batch_run of the one suspension, beside the
+    FP64 oracle's full step on all host cores and on one core (plus, on both, one 4096-sphere step and
+    a row sample of the 65536-sphere fused product)."""
+    import torch
+
+    from paper_1612_00474_gb300 import inputs, rpb
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    N, seed = 256, 0
+    kw = dict(dt=0.01, delta=1e-6, tol=1e-3)
+    pos0 = inputs.monolayer(N, seed=seed)
+    ctx = rpb.Context(max_N=N, precision="fp64", max_iter=64)
+    q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
+    U = torch.zeros_like(q)
+    step = 0
+    for _ in range(args.warmup):
+        ctx.ab_step(q, U, step, seed, max_iter=64, **kw)
+        step += 1
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    clk = clocks_start(local_rank)
+    launches0 = rpb.launch_count()
+    us, ms_m = [], []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.ab_step(q, U, step, seed, max_iter=64, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        us.append(e0.elapsed_time(e1) * 1e3)
+        ms_m.append(st["m"])
+        step += 1
+    launches = rpb.launch_count() - launches0
+    ctx.close()
+    # the same suspension as a one-instance graph-replayed run
+    bt = rpb.BatchContext(max_total_N=N, max_B=1, precision="fp64", max_iter=64)
+    qb = [torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")]
+    Ub = [torch.zeros_like(qb[0])]
+    bt.run(qb, Ub, [0], [seed], nsteps=max(1, args.warmup), lanczos_iters=args.lanczos_iters, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, unconv = bt.run(qb, Ub, [max(1, args.warmup)], [seed], nsteps=args.steps, lanczos_iters=args.lanczos_iters,
+                       **kw)
+    torch.cuda.synchronize()
+    graph_us = (time.perf_counter() - t0) * 1e6 / args.steps
+    bt.close()
+    clocks = clocks_stop(clk)
+    gpu_us = statistics.median(us)
+    line = _base_line(args, 1, gpu_us, "us/step", gpu_us / 1e3, "f64",
+                      {"workload": f"small: N={N} monolayer (seed {seed}), AB step dt=0.01, delta=1e-6, tol=1e-3, "
+                                   f"fp64 pairs", "N": N})
+    line["higher_is_better"] = False
+    line.update({"us_per_step": {"rpb_ab_step_median": gpu_us, "rpb_ab_step_mean": statistics.mean(us),
+                                 "graph_run": graph_us},
+                 "graph_run": {"lanczos_iters_per_step": args.lanczos_iters, "unconverged_instance_steps": unconv},
+                 "lanczos_m": ms_m, "gpu_launches": int(launches), "clocks": clocks})
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        allc = oracle_timing(cores, 5.0)
+        one = oracle_timing(1, 5.0, step_4096=False)  # a one-core 4096-sphere step takes minutes
+        line["cpu_baseline"] = {"value": allc["ab_step_N256_s"] * 1e6, "unit": "us/step", "cores": cores,
+                                "kind": "oracle", "sample": "one full AB step of the same N=256 suspension"}
+        line["oracle_timing"] = {"all_cores": allc, "one_core": one}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.delta is None:
@@ -645,6 +769,8 @@ def main():
         run_accuracy(args, rank, world, local_rank)
     elif args.workload == "serving":
         run_serving(args, rank, world, local_rank)
+    elif args.workload == "small":
+        run_small(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

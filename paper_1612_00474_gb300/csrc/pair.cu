@@ -273,29 +273,47 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32x2_kernel(const SrcF32 *
 
 // ------------------------------------------------------------------ symmetric tt pass
 // Translation-translation product evaluating each unordered pair once (reciprocity M_ji = M_ij^T).
-// CTA c covers target block b = ctas[c].b (128 targets) and source tiles [t0, t1) with t0 >= b of the
-// upper triangle.  The diagonal tile (t = b) is done one-directionally with the self pair excluded;
-// every other tile gives both u_i (target side, registers) and v_j (source side): each lane's v_j for
-// four sources are combined across the warp by a reduce-scatter (two exchange levels, then three
-// butterfly levels), the four warps' sums are added at the end of the tile, and the tile's source
-// sums go to src_part[col_start[t] + b].  The reduce kernel adds, for each sphere, its row's target
-// partials and its column's source partials in a fixed order.
+// The work is the upper triangle of (target block b, source tile t >= b) units of 128 x 128 spheres,
+// taken in row-major order and cut into runs of equal length, one per CTA, so that every CTA has the
+// same amount of work; a run is split at row ends into segments (b, t0, t1).  Per segment the CTA
+// keeps the 128 targets of block b in registers; the diagonal tile (t = b) is done one-directionally
+// with the self pair excluded; every other tile gives both u_i (target side, registers) and v_j
+// (source side): each lane's v_j for four sources are combined across the warp by a reduce-scatter
+// (two exchange levels, then three butterfly levels), the four warps' sums are added at the end of
+// the tile, and the tile's source sums go to src_part[col_start[t] + b].  Each segment's target sums
+// go to tgt_part[segment].  The reduce kernel adds, for each sphere, its row's segment partials and
+// its column's source partials in a fixed order.
 struct SymCta {
+    int s0, s1, pad0, pad1;  // segments [s0, s1)
+};
+struct SymSeg {
     int b, t0, t1, pad;
 };
 
-__global__ void __launch_bounds__(kPairThreads) pair_f32x2_sym_kernel(const SrcF32 *__restrict__ src, int N,
-                                                                       const SymCta *__restrict__ ctas, X2Consts c,
-                                                                       const int *__restrict__ col_start,
-                                                                       double *__restrict__ tgt_part,
-                                                                       float *__restrict__ src_part)
+template <int MINB>
+__global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(const SrcF32 *__restrict__ src, int N,
+                                                                             const SymCta *__restrict__ ctas,
+                                                                             const SymSeg *__restrict__ segs,
+                                                                             X2Consts c,
+                                                                             const int *__restrict__ col_start,
+                                                                             double *__restrict__ tgt_part,
+                                                                             float *__restrict__ src_part)
 {
     constexpr int P = kTile / 2;
     __shared__ float4 sA[P], sB[P], sC[P], sD[P];
     __shared__ float sv[4][3][kTile];
     const SymCta cd = ctas[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int i = cd.b * kTile + tid;
+    const float2 zero2 = make_float2(0.f, 0.f);
+    const int pp = tid >> 1, hh = tid & 1;
+    const bool bit4 = (lane >> 4) & 1, bit3 = (lane >> 3) & 1;
+    float *fA = reinterpret_cast<float *>(sA);
+    float *fB = reinterpret_cast<float *>(sB);
+    float *fC = reinterpret_cast<float *>(sC);
+    float *fD = reinterpret_cast<float *>(sD);
+    for (int sg = cd.s0; sg < cd.s1; ++sg) {
+    const SymSeg seg = segs[sg];
+    const int i = seg.b * kTile + tid;
     float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 tf = make_float4(1.f, 0.f, 0.f, 0.f);
     if (i < N) {
@@ -306,15 +324,8 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32x2_sym_kernel(const SrcF
     const float2 txl = make_float2(tp.z, tp.z), tyl = make_float2(tp.w, tp.w);
     const float2 tz2 = make_float2(tf.x, tf.x);
     const float2 Gx = make_float2(tf.y, tf.y), Gy = make_float2(tf.z, tf.z), Gz = make_float2(tf.w, tf.w);
-    const float2 zero2 = make_float2(0.f, 0.f);
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-    const int pp = tid >> 1, hh = tid & 1;
-    const bool bit4 = (lane >> 4) & 1, bit3 = (lane >> 3) & 1;
-    float *fA = reinterpret_cast<float *>(sA);
-    float *fB = reinterpret_cast<float *>(sB);
-    float *fC = reinterpret_cast<float *>(sC);
-    float *fD = reinterpret_cast<float *>(sD);
-    for (int t = cd.t0; t < cd.t1; ++t) {
+    for (int t = seg.t0; t < seg.t1; ++t) {
         const int j = t * kTile + tid;
         float4 sp_ = make_float4(1e18f, 0.f, 0.f, 0.f), sf_ = make_float4(1.f, 0.f, 0.f, 0.f);
         if (j < N) {
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32x2_sym_kernel(const SrcF
         fD[4 * pp + 2 + hh] = sf_.w;
         __syncthreads();
         float2 ux = zero2, uy = zero2, uz = zero2;
-        if (t == cd.b) {
+        if (t == seg.b) {
             for (int k = 0; k < P; ++k) {
                 const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
                 const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
@@ -400,23 +411,24 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32x2_sym_kernel(const SrcF
             sz = tv;
         }
         __syncthreads();
-        if (t != cd.b) {
-            float *o = src_part + (size_t)(col_start[t] + cd.b) * 3 * kTile;
+        if (t != seg.b) {
+            float *o = src_part + (size_t)(col_start[t] + seg.b) * 3 * kTile;
 #pragma unroll
             for (int q = 0; q < 3; ++q) o[q * kTile + tid] = (sv[0][q][tid] + sv[1][q][tid]) + (sv[2][q][tid] + sv[3][q][tid]);
         }
         __syncthreads();
     }
-    double *o = tgt_part + (size_t)blockIdx.x * 3 * kTile;
+    double *o = tgt_part + (size_t)sg * 3 * kTile;
     o[tid] = (double)sx - (double)cx;
     o[kTile + tid] = (double)sy - (double)cy;
     o[2 * kTile + tid] = (double)sz - (double)cz;
+    }
 }
 
 // Row partials of the targets plus column partials of the sources, fixed order; float64 self term;
 // s_i / (8 pi eta).  Translation-translation only (no torque).
 __global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
-                                       const int *__restrict__ row_cta, const int *__restrict__ col_start, int N,
+                                       const int *__restrict__ row_seg, const int *__restrict__ col_start, int N,
                                        const double *__restrict__ pos, const double *__restrict__ F,
                                        PairConsts<double> c, double a, double scale, double *__restrict__ U)
 {
@@ -425,7 +437,7 @@ __global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, cons
     const int b = blockIdx.x;
     const int q = threadIdx.x / kTile, l = threadIdx.x - q * kTile;
     double acc = 0.0;
-    for (int k = row_cta[b]; k < row_cta[b + 1]; ++k) acc += tgt_part[((size_t)k * 3 + q) * kTile + l];
+    for (int k = row_seg[b]; k < row_seg[b + 1]; ++k) acc += tgt_part[((size_t)k * 3 + q) * kTile + l];
     // column of float32 partials: compensated float32 sum (GB300's float64 rate would make a float64
     // add per partial the bottleneck), converted once
     const float *col = src_part + (size_t)col_start[b] * 3 * kTile + q * kTile + l;
@@ -453,30 +465,53 @@ __global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, cons
     U[2 * N + i] = k * uz;
 }
 
-// Upper-triangle schedule for N targets: rows split into runs of about (tiles / (8 SMs)) tiles.
-void sym_schedule(int64_t N, int num_sms, std::vector<int> &cta4, std::vector<int> &row_cta, std::vector<int> &col_start)
+// Upper-triangle schedule for N targets: the nb (nb + 1) / 2 units (b, t >= b) in row-major order
+// cut into ncta runs of equal length (about two waves of resident CTAs), each run split into
+// segments at row ends.  cta4: (s0, s1, 0, 0) per CTA; seg4: (b, t0, t1, 0) per segment, in unit
+// order, so row b's segments are [row_seg[b], row_seg[b + 1]); col_start[t]: first source-partial
+// slot of column t.
+void sym_schedule(int64_t N, int slots, std::vector<int> &cta4, std::vector<int> &seg4, std::vector<int> &row_seg,
+                  std::vector<int> &col_start)
 {
     const int nb = (int)((N + kTile - 1) / kTile);
-    const int64_t tiles = (int64_t)nb * (nb + 1) / 2;
-    int L = (int)((tiles + 8 * (int64_t)num_sms - 1) / (8 * (int64_t)num_sms));
-    if (L < 1) L = 1;
+    const int64_t units = (int64_t)nb * (nb + 1) / 2;
+    int64_t ncta = std::min<int64_t>(units, 2 * (int64_t)std::max(slots, 1));
+    const int64_t L = (units + ncta - 1) / ncta;
     cta4.clear();
-    row_cta.assign(nb + 1, 0);
+    seg4.clear();
+    row_seg.assign(nb + 1, 0);
     col_start.assign(nb, 0);
     for (int t = 0; t < nb; ++t) col_start[t] = (int)((int64_t)t * (t - 1) / 2);
-    int n = 0;
-    for (int b = 0; b < nb; ++b) {
-        row_cta[b] = n;
-        for (int t0 = b; t0 < nb; t0 += L) {
-            cta4.push_back(b);
-            cta4.push_back(t0);
-            cta4.push_back(std::min(nb, t0 + L));
-            cta4.push_back(0);
-            ++n;
+    int b = 0, t = 0, nseg = 0;
+    int64_t left = units;
+    while (left > 0) {
+        int64_t k = std::min(L, left);
+        left -= k;
+        cta4.push_back(nseg);
+        while (k > 0) {
+            const int m = (int)std::min<int64_t>(k, nb - t);
+            if (t == b) row_seg[b] = nseg;
+            seg4.push_back(b);
+            seg4.push_back(t);
+            seg4.push_back(t + m);
+            seg4.push_back(0);
+            ++nseg;
+            t += m;
+            k -= m;
+            if (t == nb) {
+                ++b;
+                t = b;
+            }
         }
+        cta4.push_back(nseg);
+        cta4.push_back(0);
+        cta4.push_back(0);
     }
-    row_cta[nb] = n;
+    row_seg[nb] = nseg;
 }
+
+// Capacity of the schedule: at most kSymMaxCtaPerSm x SMs CTAs and that many plus nb segments.
+constexpr int kSymMaxCtaPerSm = 32;
 
 size_t sym_src_part_bytes(int64_t max_N)
 {
@@ -487,13 +522,14 @@ size_t sym_src_part_bytes(int64_t max_N)
 size_t sym_tgt_part_bytes(int64_t max_N, int num_sms)
 {
     const int64_t nb = (max_N + kTile - 1) / kTile;
-    return (size_t)(2 * nb + 8 * (int64_t)num_sms + 8) * 3 * kTile * sizeof(double);
+    return (size_t)(nb + (int64_t)kSymMaxCtaPerSm * num_sms + 1) * 3 * kTile * sizeof(double);
 }
 
 size_t sym_index_ints(int64_t max_N, int num_sms)
 {
     const int64_t nb = (max_N + kTile - 1) / kTile;
-    return (size_t)4 * (2 * nb + 8 * (int64_t)num_sms + 8) + 2 * (nb + 1);
+    const int64_t maxcta = (int64_t)kSymMaxCtaPerSm * num_sms;
+    return (size_t)(4 * maxcta + 4 * (maxcta + nb + 1) + 2 * (nb + 1));
 }
 
 // Symmetric translation-translation product (float32 pairs); requires ctx->ws.sym_* scratch.
@@ -501,34 +537,54 @@ static int mobility_tt_sym(rpb_ctx *ctx, int N, const double *pos, const double 
 {
     cudaStream_t st = ctx->stream;
     Workspace &w = ctx->ws;
+    const bool six = ctx->sym_minb == 6;
     if (w.sym_N != N) {
-        std::vector<int> cta4, row_cta, col_start;
-        sym_schedule(N, ctx->num_sms, cta4, row_cta, col_start);
-        const size_t need = cta4.size() + row_cta.size() + col_start.size();
-        if (need > w.sym_index_ints || cta4.size() / 4 * 3 * kTile * sizeof(double) > w.sym_tgt_bytes) {
+        int per_sm = 0;
+        int rc;
+        if ((rc = cuda_fail(six ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_f32x2_sym_kernel<6>,
+                                                                                 kPairThreads, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_f32x2_sym_kernel<5>,
+                                                                                 kPairThreads, 0),
+                            "symmetric kernel occupancy")))
+            return rc;
+        per_sm = std::max(1, std::min(per_sm, kSymMaxCtaPerSm / 2));
+        std::vector<int> cta4, seg4, row_seg, col_start;
+        sym_schedule(N, per_sm * ctx->num_sms, cta4, seg4, row_seg, col_start);
+        const size_t need = cta4.size() + seg4.size() + row_seg.size() + col_start.size();
+        if (need > w.sym_index_ints || seg4.size() / 4 * 3 * kTile * sizeof(double) > w.sym_tgt_bytes) {
             set_error("internal: symmetric schedule larger than its scratch (N=%d)", N);
             return RPB_EINVAL;
         }
         std::vector<int> host(need);
-        std::copy(cta4.begin(), cta4.end(), host.begin());
-        std::copy(row_cta.begin(), row_cta.end(), host.begin() + cta4.size());
-        std::copy(col_start.begin(), col_start.end(), host.begin() + cta4.size() + row_cta.size());
-        int rc;
+        size_t o = 0;
+        for (const std::vector<int> *v : {&cta4, &seg4, &row_seg, &col_start}) {
+            std::copy(v->begin(), v->end(), host.begin() + o);
+            o += v->size();
+        }
         if ((rc = cuda_fail(cudaMemcpyAsync(w.sym_index, host.data(), need * sizeof(int), cudaMemcpyHostToDevice, st),
                             "symmetric schedule copy")))
             return rc;
         if ((rc = cuda_fail(cudaStreamSynchronize(st), "symmetric schedule copy"))) return rc;
         w.sym_N = N;
         w.sym_ncta = (int)(cta4.size() / 4);
-        w.sym_row_off = (int)cta4.size();
-        w.sym_col_off = (int)(cta4.size() + row_cta.size());
+        w.sym_seg_off = (int)cta4.size();
+        w.sym_row_off = (int)(cta4.size() + seg4.size());
+        w.sym_col_off = (int)(cta4.size() + seg4.size() + row_seg.size());
     }
     const double a = ctx->p.a;
     SrcF32 *src = (SrcF32 *)w.src;
     const int pb = 256;
     pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, nullptr, N, a, 1, src);
-    pair_f32x2_sym_kernel<<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, (const SymCta *)w.sym_index, make_x2_consts(a),
-                                                               w.sym_index + w.sym_col_off, w.sym_tgt, w.sym_src);
+    const SymCta *ctas = (const SymCta *)w.sym_index;
+    const SymSeg *segs = (const SymSeg *)(w.sym_index + w.sym_seg_off);
+    if (six)
+        pair_f32x2_sym_kernel<6><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, make_x2_consts(a),
+                                                                      w.sym_index + w.sym_col_off, w.sym_tgt,
+                                                                      w.sym_src);
+    else
+        pair_f32x2_sym_kernel<5><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, make_x2_consts(a),
+                                                                      w.sym_index + w.sym_col_off, w.sym_tgt,
+                                                                      w.sym_src);
     pair_sym_reduce_kernel<<<(N + kTile - 1) / kTile, 3 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
                                                              w.sym_index + w.sym_col_off, N, pos, F,
                                                              make_consts<double>(a), a, 1.0 / (8.0 * kPi * ctx->p.eta),
@@ -557,7 +613,6 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
         tz = src[i].q.x;
     }
     double ux = 0.0, uy = 0.0, uz = 0.0;
-    const int diag = blockIdx.x * kTile;
     for (int base = j0; base < j1; base += kTile) {
         const int j = base + tid;
         if (j < j1) {
@@ -571,7 +626,8 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
         }
         __syncthreads();
         const int cnt = min(kTile, j1 - base);
-        if (base != diag) {
+        const int self_k = i - base;  // this thread's own sphere is source self_k of the tile, if in [0, cnt)
+        if (self_k < 0 || self_k >= cnt) {
 #pragma unroll 2
             for (int k = 0; k < cnt; ++k) {
                 const double2 p = sp[k], q = sq[k], r = sr[k];
@@ -588,7 +644,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
                 double dx = 0.0, dy = 0.0, dz = 0.0;
                 pair_velocity<double, TORQUE, WALL>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c,
                                                     dx, dy, dz);
-                if (k != tid) {
+                if (k != self_k) {
                     ux += dx;
                     uy += dy;
                     uz += dz;
@@ -760,9 +816,20 @@ static int target_blocks(int num_sms)
 
 void pair_grid(int64_t N, int num_sms, int precision, int *splits, int64_t *chunk)
 {
-    (void)precision;
     const int64_t tiles = (N + kTile - 1) / kTile;
     int64_t S = (target_blocks(num_sms) + tiles - 1) / tiles;
+    if (precision == RPB_FP64) {
+        // Float64 runs at a small fraction of the float32 rate on this part, so even a small product
+        // is spread over every SM: source chunks may be shorter than a tile (multiples of 4 sources;
+        // the float64 kernel finds its own sphere by index, not by tile alignment).
+        if (S > (N + 3) / 4) S = (N + 3) / 4;
+        if (S < 1) S = 1;
+        int64_t ch = ((N + S - 1) / S + 3) / 4 * 4;
+        *chunk = ch;
+        *splits = (int)((N + ch - 1) / ch);
+        return;
+    }
+    // float32 kernels evaluate whole 128-source tiles and rely on tile-aligned chunks
     if (S > tiles) S = tiles;
     if (S < 1) S = 1;
     int64_t ch = ((N + S - 1) / S + kTile - 1) / kTile * kTile;

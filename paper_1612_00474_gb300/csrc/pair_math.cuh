@@ -17,12 +17,23 @@
 
 namespace rpb {
 
+// Reciprocal square root of a float32 squared distance: the hardware approximation with subnormal
+// inputs flushed to zero, one MUFU operation.  Squared distances below the smallest normal float are
+// treated as coincident spheres by the callers (kMinNormal).
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kMinNormal = 1.17549435e-38f;
+
 template <typename R>
 __device__ __forceinline__ R rsq(R x);
 template <>
 __device__ __forceinline__ float rsq<float>(float x)
 {
-    return rsqrtf(x);
+    return rsqrt_ftz(x);
 }
 template <>
 __device__ __forceinline__ double rsq<double>(double x)
@@ -106,7 +117,7 @@ __device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, 
     const float rz = zi - zj;
     const float rho2 = fmaf(rx, rx, ry * ry);
     const float r2 = fmaf(rz, rz, rho2);
-    const float inv_r = rsqrtf(r2);
+    const float inv_r = rsqrt_ftz(r2);
     const float inv_r2 = inv_r * inv_r;
     const float ir3 = inv_r * inv_r2;
     float c1 = inv_r * fmaf(c.two_3_a2, inv_r2, 1.f);
@@ -115,8 +126,8 @@ __device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, 
     const bool near = r2 < c.four_a2;
     if (__any_sync(0xffffffffu, near)) {
         if (near) {  // overlap branch; r = 0 (coincident spheres) gives the self form
-            const float r = r2 > 0.f ? r2 * inv_r : 0.f;
-            const float ir = r2 > 0.f ? inv_r : 0.f;
+            const float r = r2 >= kMinNormal ? r2 * inv_r : 0.f;
+            const float ir = r2 >= kMinNormal ? inv_r : 0.f;
             c1 = c.near_c1 * fmaf(-c.near_r, r, 1.f);
             c2 = c.near_c2 * ir;
             ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
@@ -136,7 +147,7 @@ __device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, 
     }
     // ---- wall correction
     const float Rz = zi + zj;
-    const float invR = rsqrtf(fmaf(Rz, Rz, rho2));
+    const float invR = rsqrt_ftz(fmaf(Rz, Rz, rho2));
     const float invR2 = invR * invR;
     const float ez = Rz * invR;
     const float t = zj * invR;
@@ -243,8 +254,8 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 
 __device__ __forceinline__ void near_fix(float r2, float inv_r, const X2Consts &c, float &c1, float &c2, float &ct)
 {
-    const float r = r2 > 0.f ? r2 * inv_r : 0.f;
-    const float ir = r2 > 0.f ? inv_r : 0.f;
+    const float r = r2 >= kMinNormal ? r2 * inv_r : 0.f;
+    const float ir = r2 >= kMinNormal ? inv_r : 0.f;
     c1 = c.near_c1 * fmaf(-c.near_r, r, 1.f);
     c2 = c.near_c2 * ir;
     ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
@@ -258,7 +269,7 @@ __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi
     const float2 rz = sub2(zi, zj);
     const float2 rho2 = fma2(rx, rx, mul2(ry, ry));
     const float2 r2 = fma2(rz, rz, rho2);
-    const float2 inv_r = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 inv_r2 = mul2(inv_r, inv_r);
     const float2 ir3 = mul2(inv_r, inv_r2);
     float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
@@ -271,7 +282,7 @@ __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi
     }
     const float2 Rz = add2(zi, zj);
     const float2 R2 = fma2(Rz, Rz, rho2);
-    const float2 invR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+    const float2 invR = make_float2(rsqrt_ftz(R2.x), rsqrt_ftz(R2.y));
     const float2 invR2 = mul2(invR, invR);
     const float2 ez = mul2(Rz, invR);
     const float2 t = mul2(zj, invR);
@@ -322,7 +333,7 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 zi, flo
     const float2 rz = sub2(zi, zj);
     const float2 rho2 = fma2(rx, rx, mul2(ry, ry));
     const float2 r2 = fma2(rz, rz, rho2);
-    const float2 inv_r = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 inv_r2 = mul2(inv_r, inv_r);
     const float2 ir3 = mul2(inv_r, inv_r2);
     float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
@@ -335,7 +346,7 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 zi, flo
     }
     const float2 Rz = add2(zi, zj);
     const float2 R2 = fma2(Rz, Rz, rho2);
-    const float2 invR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+    const float2 invR = make_float2(rsqrt_ftz(R2.x), rsqrt_ftz(R2.y));
     const float2 invR2 = mul2(invR, invR);
     const float2 ez = mul2(Rz, invR);
     const float2 t = mul2(zj, invR);

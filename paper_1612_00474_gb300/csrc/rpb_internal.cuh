@@ -81,12 +81,12 @@ struct Workspace {
     double *vec_g = nullptr;
     double *host_status = nullptr; // pinned host copy of the Lanczos status word
     // symmetric translation-translation pass (float32 contexts): schedule, row and column partials
-    int *sym_index = nullptr;      // CTA table (4 ints each), row_cta, col_start
+    int *sym_index = nullptr;      // CTA table and segment table (4 ints each), row_seg, col_start
     size_t sym_index_ints = 0;
     double *sym_tgt = nullptr;
     size_t sym_tgt_bytes = 0;
     float *sym_src = nullptr;
-    int sym_N = -1, sym_ncta = 0, sym_row_off = 0, sym_col_off = 0;
+    int sym_N = -1, sym_ncta = 0, sym_seg_off = 0, sym_row_off = 0, sym_col_off = 0;
 };
 
 }  // namespace rpb
@@ -100,6 +100,7 @@ struct rpb_ctx {
     int num_sms;
     int fp32_variant;  // float32 pair kernel: 1 = packed float32x2 (default), 0 = scalar; env RPB_FP32_PAIR
     int sym_enabled;   // float32 translation-translation products use the symmetric pass; env RPB_FP32_SYM=0 off
+    int sym_minb;      // symmetric kernel compiled for 6 (default) or 5 resident CTAs per SM; env RPB_SYM_MINB=5
     double Lx = 0.0, Ly = 0.0;  // pseudo-periodic periods (0: unbounded in-plane), rpb_set_periodic
     rpb::Workspace ws;
 };
