@@ -71,16 +71,20 @@ __device__ __forceinline__ void lanczos_tail_warp(double *__restrict__ lz, const
             for (int i = m - 1; i >= l; --i) {
                 const double f = s * e[i];
                 const double bb = c * e[i];
-                r = hypot(f, g);
-                e[i + 1] = r;
-                if (r == 0.0) {
+                // Givens rotation from one reciprocal square root (the entries of T are of the order
+                // of the mobility, far from the float64 overflow and underflow limits)
+                const double r2 = fma(f, f, g * g);
+                if (r2 == 0.0) {
+                    e[i + 1] = 0.0;
                     d[i + 1] -= p;
                     e[m] = 0.0;
                     restart = true;
                     break;
                 }
-                s = f / r;
-                c = g / r;
+                const double ir = rsqrt(r2);
+                e[i + 1] = r2 * ir;
+                s = f * ir;
+                c = g * ir;
                 g = d[i + 1] - p;
                 r = (d[i] - g) * s + 2.0 * c * bb;
                 p = s * r;

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32_kernel(const SrcF32 *__
 // and (Tz[2p], Tz[2p+1]).  Slots past the chunk's end hold a distant source with zero load, whose
 // contribution is exactly zero, so every tile is a full 64 iterations.
 template <bool TORQUE>
-__global__ void __launch_bounds__(kPairThreads) pair_f32x2_kernel(const SrcF32 *__restrict__ src, int N, int chunk,
+__global__ void __launch_bounds__(kPairThreads, 6) pair_f32x2_kernel(const SrcF32 *__restrict__ src, int N, int chunk,
                                                                    X2Consts c, double *__restrict__ part)
 {
     constexpr int P = kTile / 2;
@@ -290,7 +290,7 @@ struct SymSeg {
     int b, t0, t1, pad;
 };
 
-template <int MINB>
+template <int MINB, bool TORQUE>
 __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(const SrcF32 *__restrict__ src, int N,
                                                                              const SymCta *__restrict__ ctas,
                                                                              const SymSeg *__restrict__ segs,
@@ -301,6 +301,8 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
 {
     constexpr int P = kTile / 2;
     __shared__ float4 sA[P], sB[P], sC[P], sD[P];
+    __shared__ float4 sE[TORQUE ? P : 1];
+    __shared__ float2 sG[TORQUE ? P : 1];
     __shared__ float sv[4][3][kTile];
     const SymCta cd = ctas[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -311,26 +313,33 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     float *fB = reinterpret_cast<float *>(sB);
     float *fC = reinterpret_cast<float *>(sC);
     float *fD = reinterpret_cast<float *>(sD);
+    float *fE = reinterpret_cast<float *>(sE);
+    float *fG = reinterpret_cast<float *>(sG);
     for (int sg = cd.s0; sg < cd.s1; ++sg) {
     const SymSeg seg = segs[sg];
     const int i = seg.b * kTile + tid;
     float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 tf = make_float4(1.f, 0.f, 0.f, 0.f);
+    float4 th = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < N) {
         tp = src[i].p;
         tf = src[i].f;
+        if (TORQUE) th = src[i].t;
     }
     const float2 txh = make_float2(tp.x, tp.x), tyh = make_float2(tp.y, tp.y);
     const float2 txl = make_float2(tp.z, tp.z), tyl = make_float2(tp.w, tp.w);
     const float2 tz2 = make_float2(tf.x, tf.x);
     const float2 Gx = make_float2(tf.y, tf.y), Gy = make_float2(tf.z, tf.z), Gz = make_float2(tf.w, tf.w);
+    const float2 Hx = make_float2(th.x, th.x), Hy = make_float2(th.y, th.y), Hz = make_float2(th.z, th.z);
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     for (int t = seg.t0; t < seg.t1; ++t) {
         const int j = t * kTile + tid;
         float4 sp_ = make_float4(1e18f, 0.f, 0.f, 0.f), sf_ = make_float4(1.f, 0.f, 0.f, 0.f);
+        float4 st_ = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j < N) {
             sp_ = src[j].p;
             sf_ = src[j].f;
+            if (TORQUE) st_ = src[j].t;
         }
         fA[4 * pp + hh] = sp_.x;
         fA[4 * pp + 2 + hh] = sp_.y;
@@ -340,17 +349,24 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
         fC[4 * pp + 2 + hh] = sf_.y;
         fD[4 * pp + hh] = sf_.z;
         fD[4 * pp + 2 + hh] = sf_.w;
+        if (TORQUE) {
+            fE[4 * pp + hh] = st_.x;
+            fE[4 * pp + 2 + hh] = st_.y;
+            fG[2 * pp + hh] = st_.z;
+        }
         __syncthreads();
         float2 ux = zero2, uy = zero2, uz = zero2;
         if (t == seg.b) {
             for (int k = 0; k < P; ++k) {
                 const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
+                const float4 e = TORQUE ? sE[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float2 g = TORQUE ? sG[k] : zero2;
                 const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
                 const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
                 float2 dx = zero2, dy = zero2, dz = zero2;
-                pair_velocity_x2<false>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
-                                        make_float2(d.x, d.y), make_float2(d.z, d.w), zero2, zero2, zero2, c, dx, dy,
-                                        dz);
+                pair_velocity_x2<TORQUE>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
+                                         make_float2(d.x, d.y), make_float2(d.z, d.w), make_float2(e.x, e.y),
+                                         make_float2(e.z, e.w), g, c, dx, dy, dz);
                 if (k == pp) {
                     if (hh == 0) {
                         dx.x = 0.f;
@@ -372,10 +388,14 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float4 a = sA[k + h], b = sB[k + h], cc = sC[k + h], d = sD[k + h];
+                    const float4 e = TORQUE ? sE[k + h] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float2 g = TORQUE ? sG[k + h] : zero2;
                     const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
                     const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
-                    pair_sym_x2(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), make_float2(d.x, d.y),
-                                make_float2(d.z, d.w), Gx, Gy, Gz, c, ux, uy, uz, v[h][0], v[h][1], v[h][2]);
+                    pair_sym_x2<TORQUE>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
+                                        make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
+                                        make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c, ux, uy, uz,
+                                        v[h][0], v[h][1], v[h][2]);
                 }
                 // reduce-scatter of the four sources 2k .. 2k+3 over the warp: lane L ends with the
                 // sum for source 2k + 2 bit4(L) + bit3(L); lanes 0, 8, 16, 24 store it
@@ -425,12 +445,13 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     }
 }
 
-// Row partials of the targets plus column partials of the sources, fixed order; float64 self term;
-// s_i / (8 pi eta).  Translation-translation only (no torque).
+// Row partials of the targets plus column partials of the sources, fixed order; float64 self term
+// (with the torque's wall self coupling when T is given); s_i / (8 pi eta).
 __global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
                                        const int *__restrict__ row_seg, const int *__restrict__ col_start, int N,
                                        const double *__restrict__ pos, const double *__restrict__ F,
-                                       PairConsts<double> c, double a, double scale, double *__restrict__ U)
+                                       const double *__restrict__ T, PairConsts<double> c, double a, double scale,
+                                       double *__restrict__ U)
 {
     // one CTA per 128-sphere tile b, thread (q, l) = (component, sphere): coalesced column sums
     __shared__ double s[3][kTile];
@@ -457,8 +478,12 @@ __global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, cons
     const double z = pos[2 * N + i];
     const double si = H0(z / a);
     const double zc = fmax(z, a);
-    pair_velocity<double, false>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], 0.0, 0.0, 0.0, c, ux, uy,
-                                 uz);
+    if (T)
+        pair_velocity<double, true>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], si * T[i],
+                                    si * T[N + i], si * T[2 * N + i], c, ux, uy, uz);
+    else
+        pair_velocity<double, false>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], 0.0, 0.0, 0.0, c,
+                                     ux, uy, uz);
     const double k = si * scale;
     U[i] = k * ux;
     U[N + i] = k * uy;
@@ -466,16 +491,17 @@ __global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, cons
 }
 
 // Upper-triangle schedule for N targets: the nb (nb + 1) / 2 units (b, t >= b) in row-major order
-// cut into ncta runs of equal length (about two waves of resident CTAs), each run split into
-// segments at row ends.  cta4: (s0, s1, 0, 0) per CTA; seg4: (b, t0, t1, 0) per segment, in unit
+// cut into ncta runs of equal length, each run split into segments at row ends.  ncta = 30 x SMs
+// (when there are that many units) fills whole waves both at 5 and at 6 resident CTAs per SM, the
+// occupancies of the kernel's two forms (with and without torques).  cta4: (s0, s1, 0, 0) per CTA; seg4: (b, t0, t1, 0) per segment, in unit
 // order, so row b's segments are [row_seg[b], row_seg[b + 1]); col_start[t]: first source-partial
 // slot of column t.
-void sym_schedule(int64_t N, int slots, std::vector<int> &cta4, std::vector<int> &seg4, std::vector<int> &row_seg,
+void sym_schedule(int64_t N, int num_sms, std::vector<int> &cta4, std::vector<int> &seg4, std::vector<int> &row_seg,
                   std::vector<int> &col_start)
 {
     const int nb = (int)((N + kTile - 1) / kTile);
     const int64_t units = (int64_t)nb * (nb + 1) / 2;
-    int64_t ncta = std::min<int64_t>(units, 2 * (int64_t)std::max(slots, 1));
+    int64_t ncta = std::min<int64_t>(units, 30 * (int64_t)num_sms);
     const int64_t L = (units + ncta - 1) / ncta;
     cta4.clear();
     seg4.clear();
@@ -533,23 +559,15 @@ size_t sym_index_ints(int64_t max_N, int num_sms)
 }
 
 // Symmetric translation-translation product (float32 pairs); requires ctx->ws.sym_* scratch.
-static int mobility_tt_sym(rpb_ctx *ctx, int N, const double *pos, const double *F, double *U)
+// Symmetric product (float32 pairs), translation-translation or, with T, the fused product;
+// requires ctx->ws.sym_* scratch.
+static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F, const double *T, double *U)
 {
     cudaStream_t st = ctx->stream;
     Workspace &w = ctx->ws;
-    const bool six = ctx->sym_minb == 6;
     if (w.sym_N != N) {
-        int per_sm = 0;
-        int rc;
-        if ((rc = cuda_fail(six ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_f32x2_sym_kernel<6>,
-                                                                                 kPairThreads, 0)
-                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_f32x2_sym_kernel<5>,
-                                                                                 kPairThreads, 0),
-                            "symmetric kernel occupancy")))
-            return rc;
-        per_sm = std::max(1, std::min(per_sm, kSymMaxCtaPerSm / 2));
         std::vector<int> cta4, seg4, row_seg, col_start;
-        sym_schedule(N, per_sm * ctx->num_sms, cta4, seg4, row_seg, col_start);
+        sym_schedule(N, ctx->num_sms, cta4, seg4, row_seg, col_start);
         const size_t need = cta4.size() + seg4.size() + row_seg.size() + col_start.size();
         if (need > w.sym_index_ints || seg4.size() / 4 * 3 * kTile * sizeof(double) > w.sym_tgt_bytes) {
             set_error("internal: symmetric schedule larger than its scratch (N=%d)", N);
@@ -561,6 +579,7 @@ static int mobility_tt_sym(rpb_ctx *ctx, int N, const double *pos, const double 
             std::copy(v->begin(), v->end(), host.begin() + o);
             o += v->size();
         }
+        int rc;
         if ((rc = cuda_fail(cudaMemcpyAsync(w.sym_index, host.data(), need * sizeof(int), cudaMemcpyHostToDevice, st),
                             "symmetric schedule copy")))
             return rc;
@@ -574,21 +593,29 @@ static int mobility_tt_sym(rpb_ctx *ctx, int N, const double *pos, const double 
     const double a = ctx->p.a;
     SrcF32 *src = (SrcF32 *)w.src;
     const int pb = 256;
-    pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, nullptr, N, a, 1, src);
+    pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, 1, src);
     const SymCta *ctas = (const SymCta *)w.sym_index;
     const SymSeg *segs = (const SymSeg *)(w.sym_index + w.sym_seg_off);
-    if (six)
-        pair_f32x2_sym_kernel<6><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, make_x2_consts(a),
-                                                                      w.sym_index + w.sym_col_off, w.sym_tgt,
-                                                                      w.sym_src);
-    else
-        pair_f32x2_sym_kernel<5><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, make_x2_consts(a),
-                                                                      w.sym_index + w.sym_col_off, w.sym_tgt,
-                                                                      w.sym_src);
+    const X2Consts c = make_x2_consts(a);
+    const int *cs = w.sym_index + w.sym_col_off;
+    if (T) {
+        if (ctx->sym_minb == 6)
+            pair_f32x2_sym_kernel<6, true><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
+                                                                                w.sym_src);
+        else
+            pair_f32x2_sym_kernel<5, true><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
+                                                                                w.sym_src);
+    } else {
+        if (ctx->sym_minb == 5)
+            pair_f32x2_sym_kernel<5, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
+                                                                                 w.sym_src);
+        else
+            pair_f32x2_sym_kernel<6, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
+                                                                                 w.sym_src);
+    }
     pair_sym_reduce_kernel<<<(N + kTile - 1) / kTile, 3 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
-                                                             w.sym_index + w.sym_col_off, N, pos, F,
-                                                             make_consts<double>(a), a, 1.0 / (8.0 * kPi * ctx->p.eta),
-                                                             U);
+                                                             cs, N, pos, F, T, make_consts<double>(a), a,
+                                                             1.0 / (8.0 * kPi * ctx->p.eta), U);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "symmetric pair kernels");
 }
@@ -814,7 +841,9 @@ static int target_blocks(int num_sms)
     return num_sms * 8;
 }
 
-void pair_grid(int64_t N, int num_sms, int precision, int *splits, int64_t *chunk)
+constexpr int64_t kMaxSplitsF32 = 16;  // source chunks of a float32 one-way product
+
+void pair_grid(int64_t N, int num_sms, int precision, int slots, int *splits, int64_t *chunk)
 {
     const int64_t tiles = (N + kTile - 1) / kTile;
     int64_t S = (target_blocks(num_sms) + tiles - 1) / tiles;
@@ -830,30 +859,67 @@ void pair_grid(int64_t N, int num_sms, int precision, int *splits, int64_t *chun
         return;
     }
     // float32 kernels evaluate whole 128-source tiles and rely on tile-aligned chunks
-    if (S > tiles) S = tiles;
-    if (S < 1) S = 1;
-    int64_t ch = ((N + S - 1) / S + kTile - 1) / kTile * kTile;
-    if (ch < kTile) ch = kTile;
-    *chunk = ch;
-    *splits = (int)((N + ch - 1) / ch);
+    auto chunk_of = [&](int64_t s) { return std::max<int64_t>(kTile, ((N + s - 1) / s + kTile - 1) / kTile * kTile); };
+    if (slots > 0) {
+        // The grid's CTAs do nearly equal work, so they run in waves of `slots` (the resident CTAs of
+        // the whole GPU) and the kernel takes about (number of waves) x (one CTA's time, which is
+        // proportional to its chunk).  Take the split count minimising that product; a larger one
+        // only if it saves over 1%.
+        auto cost = [&](int64_t s) {
+            const int64_t ch = chunk_of(s), sp = (N + ch - 1) / ch;
+            return (double)((tiles * sp + slots - 1) / slots) * (double)ch;
+        };
+        const int64_t smax = std::min<int64_t>(kMaxSplitsF32, tiles);
+        S = 1;
+        double best = cost(1);
+        for (int64_t s2 = 2; s2 <= smax; ++s2) {
+            const double l = cost(s2);
+            if (l < 0.99 * best) {
+                best = l;
+                S = s2;
+            }
+        }
+    } else {
+        if (S > tiles) S = tiles;
+        if (S < 1) S = 1;
+    }
+    *chunk = chunk_of(S);
+    *splits = (int)((N + *chunk - 1) / *chunk);
+}
+
+// Resident CTAs over the whole GPU of the float32 one-way kernels (translation only, with torques).
+int pair_occupancy(rpb_ctx *ctx)
+{
+    int a = 0, b = 0;
+    int rc;
+    if ((rc = cuda_fail(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, pair_f32x2_kernel<false>, kPairThreads, 0),
+                        "pair kernel occupancy")) ||
+        (rc = cuda_fail(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_f32x2_kernel<true>, kPairThreads, 0),
+                        "pair kernel occupancy")))
+        return rc;
+    ctx->f32_slots[0] = std::max(1, a) * ctx->num_sms;
+    ctx->f32_slots[1] = std::max(1, b) * ctx->num_sms;
+    return RPB_OK;
 }
 
 size_t pair_partial_bytes(int64_t max_N, int num_sms)
 {
     const int64_t tiles = (max_N + kTile - 1) / kTile;
-    return (size_t)3 * sizeof(double) * (size_t)(target_blocks(num_sms) + tiles + 1) * kTile;
+    const int64_t f64 = (target_blocks(num_sms) + tiles + 1) * kTile;  // float64 splits x N bound
+    const int64_t f32 = (int64_t)kMaxSplitsF32 * max_N;                 // float32 splits x N bound
+    return (size_t)3 * sizeof(double) * (size_t)std::max(f64, f32);
 }
 
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, double *U)
 {
     const int N = (int)N64;
-    if (ctx->sym_enabled && ctx->p.wall && !(ctx->Lx > 0.0) && F && !T && N >= 2 * kTile)
-        return mobility_tt_sym(ctx, N, pos, F, U);
+    if (ctx->sym_enabled && ctx->p.wall && !(ctx->Lx > 0.0) && F && N >= 2 * kTile && (!T || ctx->sym_fused))
+        return mobility_sym(ctx, N, pos, F, T, U);
     cudaStream_t st = ctx->stream;
     const double a = ctx->p.a;
     int splits;
     int64_t chunk;
-    pair_grid(N64, ctx->num_sms, ctx->p.precision, &splits, &chunk);
+    pair_grid(N64, ctx->num_sms, ctx->p.precision, ctx->f32_slots[T != nullptr ? 1 : 0], &splits, &chunk);
     if ((size_t)splits * 3 * N * sizeof(double) > ctx->ws.partial_bytes) {
         set_error("internal: pair partial buffer too small (N=%d splits=%d)", N, splits);
         return RPB_EINVAL;
@@ -936,7 +1002,9 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
         }
     }
     const PairConsts<double> cd = make_consts<double>(a);
-    pair_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(part, splits, N, pos, F, T, cd, a,
+    // 64-sphere CTAs: the float64 self terms of a small product then spread over several SMs
+    const int rb = 64;
+    pair_reduce_kernel<<<(N + rb - 1) / rb, rb, 0, st>>>(part, splits, N, pos, F, T, cd, a,
                                                           1.0 / (8.0 * kPi * ctx->p.eta), U, ctx->p.wall);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "pair kernels");
@@ -1149,7 +1217,7 @@ extern "C" int rpb_mobility_apply_noalloc(int64_t N64, const double *pos, const 
     if ((rc = noalloc_setup(&base, &sms))) return rc;
     int splits;
     int64_t chunk;
-    pair_grid(N64, sms, p->precision, &splits, &chunk);
+    pair_grid(N64, sms, p->precision, 0, &splits, &chunk);
     const int64_t max_splits = kNoAllocPartialElems / (3 * N64);
     if (splits > max_splits) {
         chunk = ((N64 + max_splits - 1) / max_splits + kTile - 1) / kTile * kTile;

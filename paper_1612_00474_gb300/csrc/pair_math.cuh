@@ -322,12 +322,19 @@ __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi
     }
 }
 
-// Both directions of a translation-translation pair block, two pairs per lane (packed float32x2).
-// Reciprocity of the mobility (M_ji = M_ij^T) lets one evaluation of the pair geometry serve the
-// target (u_i += M_ij F_j, accumulated) and the source (v_j = M_ij^T F_i, returned): the free-space
-// block is symmetric, and the transposed wall block swaps the roles of C and D.
+// Both directions of a pair block, two pairs per lane (packed float32x2).  Reciprocity of the
+// mobility (M_ji = M_ij^T) lets one evaluation of the pair geometry serve the target
+// (u_i += M_ij F_j, accumulated) and the source (v_j = M_ji F_i, returned): the free-space
+// translation block is symmetric, and the transposed wall block swaps the roles of C and D.
+// TORQUE adds the translation-rotation coupling both ways: u_i += M_tr(i,j) T_j and
+// v_j += M_tr(j,i) H_i.  For the reversed pair the in-plane offset and the height difference change
+// sign, the image height z_i + z_j, |R|, s, e_z and the rotlet coefficient are unchanged, and
+// t' = z~_i / |R| replaces t = z~_j / |R|.
+// F: source loads, G: target loads; T: source torques, H: target torques.
+template <bool TORQUE>
 __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 zi, float2 zj, float2 Fx, float2 Fy,
-                                            float2 Fz, float2 Gx, float2 Gy, float2 Gz, const X2Consts &c,
+                                            float2 Fz, float2 Gx, float2 Gy, float2 Gz, float2 Tx, float2 Ty,
+                                            float2 Tz, float2 Hx, float2 Hy, float2 Hz, const X2Consts &c,
                                             float2 &ux, float2 &uy, float2 &uz, float2 &vx, float2 &vy, float2 &vz)
 {
     const float2 rz = sub2(zi, zj);
@@ -383,6 +390,42 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 zi, flo
         vx = fma2(cF, Gx, mul2(kk, rx));
         vy = fma2(cF, Gy, mul2(kk, ry));
         vz = fma2(cF, Gz, fma2(k2, rz, fma2(ke, Rz, kz)));
+    }
+    if (TORQUE) {
+        // the rotation coupling of pair_velocity_x2 (c_t T x r - p T x R + |R|^-2 [...]), with the
+        // factors that do not depend on the direction computed once
+        const float2 p = mul2(invR2, invR);
+        const float2 dcp = sub2(ct, p);
+        const float2 ctrz = mul2(ct, rz), pRz = mul2(p, Rz);
+        const float2 se = mul2(s, ez);
+        const float2 i2 = add2(invR2, invR2);
+        const float2 s2i = mul2(add2(s, s), invR2);
+        const float2 ce0 = fma2(c.m10, se, mul2(c.c6, ez));  // c_e = ce0 - 6 t
+        {  // target side, source torque T_j
+            const float2 m1 = sub2(ctrz, pRz);
+            const float2 tz3 = fma2(Tx, ry, neg2(mul2(Ty, rx)));
+            const float2 m2 = fma2(add2(t, se), i2, m1);
+            const float2 ce = fma2(c.m6, t, ce0);
+            const float2 w = mul2(neg2(tz3), invR);
+            const float2 cw = mul2(mul2(ce, w), p);
+            const float2 dTz = mul2(dcp, Tz);
+            ux = fma2(Ty, m2, fma2(neg2(dTz), ry, fma2(cw, rx, ux)));
+            uy = fma2(neg2(Tx), m2, fma2(dTz, rx, fma2(cw, ry, uy)));
+            uz = fma2(dcp, tz3, fma2(cw, Rz, fma2(s2i, w, uz)));
+        }
+        {  // source side, target torque H_i, reversed pair
+            const float2 tr = mul2(zi, invR);
+            const float2 m1 = neg2(add2(ctrz, pRz));
+            const float2 tz3 = fma2(Hy, rx, neg2(mul2(Hx, ry)));
+            const float2 m2 = fma2(add2(tr, se), i2, m1);
+            const float2 ce = fma2(c.m6, tr, ce0);
+            const float2 w = mul2(neg2(tz3), invR);
+            const float2 cw = mul2(mul2(ce, w), p);
+            const float2 dTz = mul2(dcp, Hz);
+            vx = fma2(Hy, m2, fma2(dTz, ry, fma2(neg2(cw), rx, vx)));
+            vy = fma2(neg2(Hx), m2, fma2(neg2(dTz), rx, fma2(neg2(cw), ry, vy)));
+            vz = fma2(dcp, tz3, fma2(cw, Rz, fma2(s2i, w, vz)));
+        }
     }
 }
 

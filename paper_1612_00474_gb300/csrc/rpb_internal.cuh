@@ -100,8 +100,10 @@ struct rpb_ctx {
     int num_sms;
     int fp32_variant;  // float32 pair kernel: 1 = packed float32x2 (default), 0 = scalar; env RPB_FP32_PAIR
     int sym_enabled;   // float32 translation-translation products use the symmetric pass; env RPB_FP32_SYM=0 off
-    int sym_minb;      // symmetric kernel compiled for 6 (default) or 5 resident CTAs per SM; env RPB_SYM_MINB=5
+    int sym_minb;      // symmetric kernels compiled for 6 or 5 resident CTAs per SM; env RPB_SYM_MINB
+    int sym_fused;     // products with torques also use the symmetric pass; env RPB_FP32_SYM_FUSED=0 off
     double Lx = 0.0, Ly = 0.0;  // pseudo-periodic periods (0: unbounded in-plane), rpb_set_periodic
+    int f32_slots[2] = {0, 0};  // resident CTAs of the float32 one-way pair kernels (tt, with torques)
     rpb::Workspace ws;
 };
 
@@ -125,7 +127,9 @@ __global__ void pack_f64_kernel(const double *__restrict__ pos, const double *__
                                 const double *__restrict__ T, int N, double a, int wall, SrcF64 *__restrict__ out);
 
 // Number of column splits and chunk length the pair kernel uses for N targets.
-void pair_grid(int64_t N, int num_sms, int precision, int *splits, int64_t *chunk);
+// slots: resident CTAs of the float32 kernel over the GPU (0: unknown, fixed rule).
+void pair_grid(int64_t N, int num_sms, int precision, int slots, int *splits, int64_t *chunk);
+int pair_occupancy(rpb_ctx *ctx);
 size_t pair_partial_bytes(int64_t max_N, int num_sms);
 size_t sym_src_part_bytes(int64_t max_N);
 size_t sym_tgt_part_bytes(int64_t max_N, int num_sms);
