@@ -53,12 +53,16 @@ def parse():
     ap.add_argument("--periodic", action="store_true",
                     help="monolayer: pseudo-periodic boundaries with the monolayer's square as the unit cell")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy", "small"],
+    ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy", "small",
+                                           "fingering"],
                     default="monolayer")
     ap.add_argument("--acc-steps", type=int, default=10, help="accuracy: steps compared with the oracle")
     ap.add_argument("--lanczos-iters", type=int, default=12,
                     help="batched: Lanczos iterations per step inside the step graph (converged instances masked)")
     ap.add_argument("--B", type=int, default=512, help="batched: number of suspensions")
+    ap.add_argument("--hg", type=float, default=1.5, help="fingering: gravitational height h_g / a")
+    ap.add_argument("--fing-steps", type=int, default=2500, help="fingering: steps of each run (0.016 s each)")
+    ap.add_argument("--sample-every", type=int, default=10, help="fingering: steps between front spectra")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     ap.add_argument("--load", type=float, default=0.85, help="serving: offered load relative to measured capacity")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: device-memory budget for resident state")
@@ -751,6 +755,140 @@ def run_small(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- roller fingering (Sec. IV)
+# Physical setting of the roller runs: a = 0.656 um, water (eta = 1 mPa s), torque 8 pi eta a^3 omega y
+# with omega = 62.8 rad/s, U0 = 4 kT, b = 0.1 a, dt = 0.016 s = tau_U / 2, Lanczos tolerance 1e-3,
+# N = 32768 in a 60a x 4915a strip; front spectra over k in [2e-3, 0.26] per um.
+FING_A_M = 0.656e-6
+FING_ETA = 1e-3
+FING_KT = 1.380649e-23 * 298.0   # the temperature is not stated; 298 K gives tau_U / 2 = 0.016 s
+FING_OMEGA = 62.8
+FING_DT_S = 0.016
+FING_LX, FING_LY = 60.0, 4915.0
+FING_KMIN_UM, FING_KMAX_UM = 2.0e-3, 0.26
+FING_T_STAR_PAPER = {1.5: (9.4, 11.8), 3.5: (17.3, 26.9), 6.1: (32.6, 42.9)}  # (deterministic, stochastic) s
+
+
+def fingering_units():
+    """Reduced units a = eta = kT = 1: time unit eta a^3 / kT."""
+    tau0 = FING_ETA * FING_A_M ** 3 / FING_KT
+    return dict(tau0=tau0, dt=FING_DT_S / tau0, torque=8.0 * math.pi * FING_OMEGA * tau0)
+
+
+def fingering_initial(N, hg, U0, b, seed):
+    """Rollers in the 60a x 4915a strip (x across the front, y along it): heights from the one-sphere
+    Gibbs-Boltzmann density exp(-(w h + U_wall(h)) / kT) with w = kT / (h_g - a) and the wall branch
+    of the soft potential, in-plane positions uniform, 3D overlaps (r < 2a) rejected in sequence."""
+    rng = np.random.default_rng(seed)
+    w = 1.0 / (hg - 1.0)
+    h = np.linspace(1e-3, 1.0 + 60.0 / w, 200001)
+    uw = np.where(h < 1.0, U0 * (1.0 + (1.0 - h) / b), U0 * np.exp(-(h - 1.0) / b))
+    pdf = np.exp(-(w * h + uw - (w * 1.0 + U0)))
+    cdf = np.cumsum(pdf)
+    cdf /= cdf[-1]
+    cells = {}
+    out = np.zeros((N, 3))
+    n = 0
+    while n < N:
+        x, y = rng.uniform(0.0, FING_LX), rng.uniform(0.0, FING_LY)
+        z = float(np.interp(rng.uniform(), cdf, h))
+        cx, cy = int(x // 2.0), int(y // 2.0)
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for j in cells.get((cx + dx, cy + dy), ()):
+                    if (out[j, 0] - x) ** 2 + (out[j, 1] - y) ** 2 + (out[j, 2] - z) ** 2 < 4.0:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            out[n] = (x, y, z)
+            cells.setdefault((cx, cy), []).append(n)
+            n += 1
+    return out
+
+
+def front_band_power(p, frac=0.7):
+    """Power of the number density along the front, sum of |n(k_y)|^2 over the wavenumbers of the band,
+    from the fraction `frac` of the spheres with the largest x (the front)."""
+    k_a = 2.0 * math.pi * np.arange(1, 4096) / FING_LY       # per a
+    k_um = k_a / (FING_A_M * 1e6)
+    ks = k_a[(k_um >= FING_KMIN_UM) & (k_um <= FING_KMAX_UM)]
+    y = p[np.argsort(p[:, 0])[int((1.0 - frac) * len(p)):], 1]
+    nk = np.exp(-1j * np.outer(ks, y)).sum(axis=1)
+    return float(np.sum(np.abs(nk) ** 2))
+
+
+def run_fingering(args, rank, world, local_rank):
+    """Roller fingering run: the same N = 32768 strip advanced deterministically (kT = 0) and with
+    Brownian motion, the front's band power sampled along the way; t* is the time of its maximum."""
+    import torch
+
+    from paper_1612_00474_gb300 import inputs, rpb
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    units = fingering_units()
+    N, hg, U0, b = 32768 if args.N == 65536 else args.N, args.hg, 4.0, 0.1
+    weight = 1.0 / (hg - 1.0)
+    torque = (0.0, units["torque"], 0.0)
+    pos0 = fingering_initial(N, hg, U0, b, args.seed)
+    runs = {}
+    clk = clocks_start(local_rank)
+    for name, kT in (("deterministic", 0.0), ("stochastic", 1.0)):
+        ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=64, kT=kT)
+        q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
+        U = torch.zeros_like(q)
+        h_edges = np.linspace(0.0, 12.0, 49)
+        x_edges = np.arange(-100.0, 1501.0, 20.0)
+
+        def sample(p):
+            return (front_band_power(p), np.histogram(p[:, 2], h_edges)[0], np.histogram(p[:, 0], x_edges)[0],
+                    float(p[:, 2].mean()), float(np.mean(np.sort(p[:, 0])[int(0.3 * N):])))
+
+        times, samples, ms = [0.0], [sample(pos0)], []
+        t0 = time.perf_counter()
+        for step in range(args.fing_steps):
+            st = ctx.ab_step(q, U, step, args.seed, dt=units["dt"], delta=args.delta, tol=args.tol, max_iter=64,
+                             weight=weight, U0=U0, b=b, torque=torque)
+            ms.append(st["m"])
+            if (step + 1) % args.sample_every == 0:
+                times.append((step + 1) * FING_DT_S)
+                samples.append(sample(inputs.from_soa(q.cpu().numpy(), N)))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ctx.close()
+        power = [s_[0] for s_ in samples]
+        k = int(np.argmax(power))
+        every = max(1, len(times) // 80)
+        runs[name] = {"t_star_s": times[k], "t_star_at_end_of_run": k == len(power) - 1,
+                      "steps_per_s": args.fing_steps / wall, "lanczos_m_mean": float(np.mean(ms)),
+                      "P_h_at_t_star": {"edges_a": h_edges.tolist(), "counts": samples[k][1].tolist()},
+                      "rho_x_at_t_star": {"edges_a": x_edges.tolist(), "counts": samples[k][2].tolist()},
+                      "P_h_initial": samples[0][1].tolist(),
+                      "series": [{"t_s": round(t, 3), "band_power": round(s_[0], 1), "mean_h": round(s_[3], 3),
+                                  "front_x": round(s_[4], 2)} for t, s_ in zip(times, samples)][::every]}
+    clocks = clocks_stop(clk)
+    paper = FING_T_STAR_PAPER.get(round(hg, 1))
+    det, sto = runs["deterministic"]["t_star_s"], runs["stochastic"]["t_star_s"]
+    line = _base_line(args, 1, runs["stochastic"]["steps_per_s"], "steps/s", 1e3 / runs["stochastic"]["steps_per_s"],
+                      "f32" if args.precision == "fp32" else "f64",
+                      {"workload": f"roller fingering: N={N} strip 60a x 4915a, h_g={hg}a, U0=4kT, b=0.1a, "
+                                   f"torque 8 pi eta a^3 omega (omega=62.8 rad/s), dt=0.016 s, "
+                                   f"{args.fing_steps} steps per run, {args.precision} pairs", "N": N})
+    line.update({"fingering": {"t_star_s": {"deterministic": det, "stochastic": sto},
+                               "ratio_stochastic_over_deterministic": sto / det if det > 0 else None,
+                               "paper_t_star_s": ({"deterministic": paper[0], "stochastic": paper[1],
+                                                   "ratio": paper[1] / paper[0]} if paper else None),
+                               "reduced_units": units, "runs": runs},
+                 "clocks": clocks})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.delta is None:
@@ -771,6 +909,8 @@ def main():
         run_serving(args, rank, world, local_rank)
     elif args.workload == "small":
         run_small(args, rank, world, local_rank)
+    elif args.workload == "fingering":
+        run_fingering(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

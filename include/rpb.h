@@ -141,7 +141,9 @@ int rpb_philox_normal(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uin
  * rpb_philox_normal(seed, step, 0 / 1).  step == 0 is the first step: U^{n-1} is ignored and
  * taken equal to U^n (Euler-Maruyama).  pos, U_prev: 3N, in/out.  stats: host pointer (may be
  * NULL).  Synchronises the stream (Lanczos).  RPB_ENOCONV as for rpb_lanczos_sqrt_apply (the
- * step is still taken). */
+ * step is still taken).  A context with kT = 0 takes the deterministic step: no noise is drawn and
+ * neither the Lanczos square root nor the drift is computed (both carry a factor kT); stats then
+ * report 0 iterations, converged. */
 int rpb_ab_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed,
                 double dt, double delta, double tol, int max_iter, const rpb_force_params *fp,
                 rpb_step_stats *stats);

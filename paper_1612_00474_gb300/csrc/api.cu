@@ -369,13 +369,24 @@ int rpb_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step,
     if ((rc = forces_impl(ctx, N, pos, fp, F))) return rc;
     if ((rc = fill_torque(ctx, N, fp->torque, T))) return rc;
     if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
-    if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 0u, 0u, W))) return rc;
-    if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 1u, 0u, Wt))) return rc;
     int iters = 0, conv = 0;
     double err = -1.0;
-    const int lrc = lanczos_impl(ctx, N, pos, W, g, tol, max_iter, &iters, &err, &conv);
-    if (lrc != RPB_OK && lrc != RPB_ENOCONV) return lrc;
-    if ((rc = rfd_impl(ctx, N, pos, Wt, delta, drift, rfd == RPB_RFD_ONE_SIDED))) return rc;
+    int lrc = RPB_OK;
+    if (ctx->p.kT > 0.0) {
+        if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 0u, 0u, W))) return rc;
+        if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 1u, 0u, Wt))) return rc;
+        lrc = lanczos_impl(ctx, N, pos, W, g, tol, max_iter, &iters, &err, &conv);
+        if (lrc != RPB_OK && lrc != RPB_ENOCONV) return lrc;
+        if ((rc = rfd_impl(ctx, N, pos, Wt, delta, drift, rfd == RPB_RFD_ONE_SIDED))) return rc;
+    } else {
+        // kT = 0: no Brownian increment and no drift (both carry a factor kT); the deterministic
+        // scheme needs neither the noise nor M^{1/2}
+        if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "clear g")) ||
+            (rc = cuda_fail(cudaMemsetAsync(drift, 0, 3 * N * sizeof(double), ctx->stream), "clear drift")))
+            return rc;
+        err = 0.0;
+        conv = 1;
+    }
     const double noise = sqrt(2.0 * ctx->p.kT * dt);
     // Euler-Maruyama is the update with U^{n-1} := U^n (Eq. EM); AB uses that only on the first step
     const int em = scheme == RPB_SCHEME_EM || step == 0;

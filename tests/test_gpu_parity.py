@@ -406,3 +406,22 @@ def test_periodic_invalid(gpu_lib):
             ctx.set_periodic(float("nan"), 10.0)
     finally:
         ctx.close()
+
+
+def test_deterministic_step_kT0(gpu_lib):
+    """kT = 0: the step is the deterministic Adams-Bashforth step (the oracle computes and multiplies
+    the stochastic terms by zero; the library skips them)."""
+    N = 200
+    pos0 = inputs.monolayer(N, seed=14)
+    Uprev = inputs.vectors(N, 15, scale=0.01)
+    ctx = gpu_lib.Context(max_N=N, precision="fp64", max_iter=32, kT=0.0)
+    try:
+        q, U = dev(pos0), dev(Uprev)
+        st = ctx.step(q, U, 4, 3, scheme="AB", dt=0.05, delta=1e-6, tol=1e-3, torque=(0.0, 50.0, 0.0))
+    finally:
+        ctx.close()
+    new_ref, Un_ref, _ = O.ab_step(pos0, Uprev, 4, seed=3, dt=0.05, delta=1e-6, tol=1e-3, kT=0.0,
+                                   torque=(0.0, 50.0, 0.0))
+    assert st["m"] == 0 and st["converged"]
+    assert maxrel(host(U, N), Un_ref) <= 1e-10
+    assert maxrel(host(q, N) - pos0, new_ref - pos0) <= 1e-10
