@@ -864,8 +864,14 @@ def run_fingering(args, rank, world, local_rank):
         ctx.close()
         power = [s_[0] for s_ in samples]
         k = int(np.argmax(power))
+        # first time the band power reaches half its maximum (linear interpolation between samples):
+        # a companion of t* that does not depend on the noisy top of a plateau
+        half = 0.5 * power[k]
+        jh = next(j for j, v in enumerate(power) if v >= half)
+        t_half = times[jh] if jh == 0 else times[jh - 1] + (half - power[jh - 1]) / (power[jh] - power[jh - 1]) * (
+            times[jh] - times[jh - 1])
         every = max(1, len(times) // 80)
-        runs[name] = {"t_star_s": times[k], "t_star_at_end_of_run": k == len(power) - 1,
+        runs[name] = {"t_star_s": times[k], "t_star_at_end_of_run": k == len(power) - 1, "t_half_s": t_half,
                       "steps_per_s": args.fing_steps / wall, "lanczos_m_mean": float(np.mean(ms)),
                       "P_h_at_t_star": {"edges_a": h_edges.tolist(), "counts": samples[k][1].tolist()},
                       "rho_x_at_t_star": {"edges_a": x_edges.tolist(), "counts": samples[k][2].tolist()},
@@ -880,8 +886,11 @@ def run_fingering(args, rank, world, local_rank):
                       {"workload": f"roller fingering: N={N} strip 60a x 4915a, h_g={hg}a, U0=4kT, b=0.1a, "
                                    f"torque 8 pi eta a^3 omega (omega=62.8 rad/s), dt=0.016 s, "
                                    f"{args.fing_steps} steps per run, {args.precision} pairs", "N": N})
+    hd, hs = runs["deterministic"]["t_half_s"], runs["stochastic"]["t_half_s"]
     line.update({"fingering": {"t_star_s": {"deterministic": det, "stochastic": sto},
                                "ratio_stochastic_over_deterministic": sto / det if det > 0 else None,
+                               "t_half_s": {"deterministic": hd, "stochastic": hs},
+                               "t_half_ratio": hs / hd if hd > 0 else None,
                                "paper_t_star_s": ({"deterministic": paper[0], "stochastic": paper[1],
                                                    "ratio": paper[1] / paper[0]} if paper else None),
                                "reduced_units": units, "runs": runs},
