@@ -33,6 +33,12 @@ FLOPS_TT = 126      # algorithmic flops per pair, translation-translation block 
 FLOPS_FUSED = 185   # ... plus the translation-rotation block (counts derived in the design doc)
 FLOPS_SYM = 171     # per unordered pair when the block is evaluated once and applied both ways (81 + 2 x 45)
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one launch of the symmetric translation-translation kernel at
+# N = 65536, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the
+# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command); 3.54 MB read (the
+# packed sources), 152.5 MB written (source-column partials leaving L2).  Valid for this kernel
+# build only: reset to None when the kernel changes.
+SYM_TT_TRAFFIC_BYTES = {65536: 3.54e6 + 152.54e6}
 SM_MAX_MHZ = 2070.0
 
 
@@ -345,7 +351,9 @@ def run_ours(args, rank, world, local_rank):
                          "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
                                        if args.precision == "fp32" else "fp32 lanes (fp64 path: see DESIGN.md)",
                          "flops_per_launch": flops_tt,
-                         "flops_per_pair": FLOPS_SYM / 2 if sym else FLOPS_TT, "traffic": None},
+                         "flops_per_pair": FLOPS_SYM / 2 if sym else FLOPS_TT,
+                         "traffic": SYM_TT_TRAFFIC_BYTES.get(N) if sym else None,
+                         "traffic_unit": "bytes per launch"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": "Gpairs/s", "h2d_bytes_per_step": 2 * 3 * N * 8,
                     "d2h_bytes_per_step": 2 * 3 * N * 8},

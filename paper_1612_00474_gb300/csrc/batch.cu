@@ -70,7 +70,7 @@ __global__ void gather_kernel(const InstDesc *__restrict__ inst, const int *__re
 
 // ------------------------------------------------------------------ pair products
 template <bool TORQUE>
-__global__ void __launch_bounds__(kPairThreads) batch_pair_f32x2_kernel(
+__global__ void __launch_bounds__(kPairThreads, 6) batch_pair_f32x2_kernel(
     const SrcF32 *__restrict__ src, const InstDesc *__restrict__ inst, const BlockDesc *__restrict__ blocks,
     const int *__restrict__ active, int64_t total, X2Consts c, PairConsts<double> cd, double a, double scale,
     const double *__restrict__ pos, const double *__restrict__ F, const double *__restrict__ T, double *__restrict__ U)
@@ -260,7 +260,11 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
                                                            double weight, double U0, double b, float cut2,
                                                            double *__restrict__ F)
 {
-    __shared__ float4 sp[128];
+    // the screen and the near-pair evaluation of forces_kernel, within the block's own instance: the
+    // float32 screen takes two sources per lane (packed), near pairs are queued per thread and
+    // evaluated in float64 together, in index order
+    __shared__ float4 sp[64];
+    __shared__ float2 sz[64];
     const BlockDesc bd = blocks[blockIdx.x];
     const InstDesc d = inst[bd.inst];
     const int tid = threadIdx.x;
@@ -276,30 +280,57 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
     const float xf = (float)xi, yf = (float)yi, zf = (float)zi;
     const double f0 = U0 / b;
     double fx = 0.0, fy = 0.0, fz = 0.0;
+    constexpr int kQ = 32;
+    int queue[kQ];
+    int nq = 0;
+    auto flush = [&]() {
+        for (int q = 0; q < nq; ++q) {
+            const int64_t j = d.off + queue[q];
+            const double dx = xi - pos[j], dy = yi - pos[total + j], dz = zi - pos[2 * total + j];
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r > 0.0) {
+                const double m = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
+                fx += m * dx;
+                fy += m * dy;
+                fz += m * dz;
+            }
+        }
+        nq = 0;
+    };
+    float *fxy = reinterpret_cast<float *>(sp);
+    float *fz2 = reinterpret_cast<float *>(sz);
+    const float2 X = make_float2(xf, xf), Y = make_float2(yf, yf), Z = make_float2(zf, zf);
+    const int pp = tid >> 1, hh = tid & 1;
     for (int base = 0; base < d.N; base += 128) {
         const int jl = base + tid;
         const int64_t jt = d.off + jl;
-        sp[tid] = jl < d.N ? make_float4((float)pos[jt], (float)pos[total + jt], (float)pos[2 * total + jt], 0.f)
-                           : make_float4(1e18f, 0.f, 0.f, 0.f);
+        // slots past the instance's end hold a point far above the wall (never inside the screen)
+        const bool in = jl < d.N;
+        fxy[4 * pp + hh] = in ? (float)pos[jt] : 0.f;
+        fxy[4 * pp + 2 + hh] = in ? (float)pos[total + jt] : 0.f;
+        fz2[2 * pp + hh] = in ? (float)pos[2 * total + jt] : 1e18f;
         __syncthreads();
 #pragma unroll 8
-        for (int k = 0; k < 128; ++k) {
+        for (int k = 0; k < 64; ++k) {
             const float4 p = sp[k];
-            const float dxf = xf - p.x, dyf = yf - p.y, dzf = zf - p.z;
-            if (fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf)) < cut2 && base + k != il) {
-                const int64_t j = d.off + base + k;
-                const double dx = xi - pos[j], dy = yi - pos[total + j], dz = zi - pos[2 * total + j];
-                const double r = sqrt(dx * dx + dy * dy + dz * dz);
-                if (r > 0.0) {
-                    const double m = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
-                    fx += m * dx;
-                    fy += m * dy;
-                    fz += m * dz;
+            const float2 dx = sub2(X, make_float2(p.x, p.y)), dy = sub2(Y, make_float2(p.z, p.w));
+            const float2 dz = sub2(Z, sz[k]);
+            const float2 d2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+            if (d2.x < cut2 || d2.y < cut2) {
+                const int j0 = base + 2 * k;
+                if (d2.x < cut2 && j0 != il && j0 < d.N) {
+                    queue[nq++] = j0;
+                    if (nq == kQ) flush();
+                }
+                if (d2.y < cut2 && j0 + 1 != il && j0 + 1 < d.N) {
+                    queue[nq++] = j0 + 1;
+                    if (nq == kQ) flush();
                 }
             }
         }
         __syncthreads();
     }
+    flush();
     if (valid) {
         fz += (zi < a ? f0 : f0 * exp(-(zi - a) / b)) - weight;
         F[i] = fx;
