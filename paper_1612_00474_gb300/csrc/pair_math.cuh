@@ -194,6 +194,7 @@ __device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, 
 // two scalar ones.  Constants are passed as float2 pairs in the kernel parameters.
 struct X2Consts {
     float2 one, two_3_a2, m_two_a2, a2;
+    float lo_r2;  // squared distance below which the low parts of the positions are added (float32 kernels)
     float2 m10_3, c2_3, two, m2_3, m1, c70_3, m10, m6, m140_3, c40_3, c20, m4, c12, m20_3, m8_3, c6;
     float four_a2, near_c1, near_r, near_c2, near_tr, near_tr_r;
 };
@@ -228,6 +229,7 @@ inline X2Consts make_x2_consts(double a)
     c.near_c2 = (float)(1.0 / (8.0 * a * a));
     c.near_tr = (float)(1.0 / (2.0 * a * a * a));
     c.near_tr_r = (float)(3.0 / (8.0 * a));
+    c.lo_r2 = (float)(100.0 * a * a);
     return c;
 }
 
@@ -331,25 +333,25 @@ __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi
 // sign, the image height z_i + z_j, |R|, s, e_z and the rotlet coefficient are unchanged, and
 // t' = z~_i / |R| replaces t = z~_j / |R|.
 // F: source loads, G: target loads; T: source torques, H: target torques.
+// The caller gives the pair geometry: in-plane offset (rx, ry), rz = zi - zj, rho2 = rx^2 + ry^2,
+// r2 = rho2 + rz^2, and `close`, true (warp-uniformly) when some lane of the warp may hold an
+// overlapping pair (r < 2a); the overlap branch is then taken per lane.
 template <bool TORQUE>
-__device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 zi, float2 zj, float2 Fx, float2 Fy,
-                                            float2 Fz, float2 Gx, float2 Gy, float2 Gz, float2 Tx, float2 Ty,
-                                            float2 Tz, float2 Hx, float2 Hy, float2 Hz, const X2Consts &c,
-                                            float2 &ux, float2 &uy, float2 &uz, float2 &vx, float2 &vy, float2 &vz)
+__device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, float2 rho2, float2 r2, bool close,
+                                            float2 zi, float2 zj, float2 Fx, float2 Fy, float2 Fz, float2 Gx,
+                                            float2 Gy, float2 Gz, float2 Tx, float2 Ty, float2 Tz, float2 Hx,
+                                            float2 Hy, float2 Hz, const X2Consts &c, float2 &ux, float2 &uy,
+                                            float2 &uz, float2 &vx, float2 &vy, float2 &vz)
 {
-    const float2 rz = sub2(zi, zj);
-    const float2 rho2 = fma2(rx, rx, mul2(ry, ry));
-    const float2 r2 = fma2(rz, rz, rho2);
     const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 inv_r2 = mul2(inv_r, inv_r);
     const float2 ir3 = mul2(inv_r, inv_r2);
     float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
     float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
     float2 ct = ir3;
-    const bool n0 = r2.x < c.four_a2, n1 = r2.y < c.four_a2;
-    if (__any_sync(0xffffffffu, n0 || n1)) {
-        if (n0) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
-        if (n1) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
+    if (close) {
+        if (r2.x < c.four_a2) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
+        if (r2.y < c.four_a2) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
     }
     const float2 Rz = add2(zi, zj);
     const float2 R2 = fma2(Rz, Rz, rho2);

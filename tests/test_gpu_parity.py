@@ -425,3 +425,19 @@ def test_deterministic_step_kT0(gpu_lib):
     assert st["m"] == 0 and st["converged"]
     assert maxrel(host(U, N), Un_ref) <= 1e-10
     assert maxrel(host(q, N) - pos0, new_ref - pos0) <= 1e-10
+
+
+@pytest.mark.parametrize("with_T", [False, True])
+def test_mobility_fp32_far_from_origin(ctx32, with_T):
+    """Float32 offsets at large coordinates: a dense patch near (1000a, 4000a) (position ulp 2.4e-4a)
+    and spheres spread along a 5000a strip; both forms of the symmetric pass at 1e-5."""
+    rng = np.random.default_rng(91)
+    N1, N2 = 768, 512
+    p1 = np.column_stack([rng.uniform(1000, 1030, N1), rng.uniform(4000, 4030, N1), rng.uniform(0.9, 2.5, N1)])
+    p2 = np.column_stack([rng.uniform(0, 60, N2), rng.uniform(0, 5000, N2), rng.uniform(1.0, 3.0, N2)])
+    pos = np.vstack([p1, p2])
+    N = len(pos)
+    F, T = inputs.vectors(N, 92), (inputs.vectors(N, 93) if with_T else None)
+    got = host(ctx32.mobility_apply(dev(pos), dev(F), dev(T) if with_T else None), N)
+    ref = O.mobility_apply(pos, F, T)
+    assert maxrel(got, ref) <= 1e-5
