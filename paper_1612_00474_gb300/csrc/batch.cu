@@ -133,6 +133,8 @@ __global__ void __launch_bounds__(kPairThreads, 6) batch_pair_f32x2_kernel(
             const float4 av = sA[k], bv = sB[k], cc = sC[k], dv = sD[k];
             const float4 e = TORQUE ? sE[k] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float2 g = TORQUE ? sG[k] : zero2;
+            // instances are small (every warp iteration has some pair within 10a), so the low parts
+            // of the positions are always added
             const float2 rx = add2(sub2(txh, make_float2(av.x, av.y)), sub2(txl, make_float2(bv.x, bv.y)));
             const float2 ry = add2(sub2(tyh, make_float2(av.z, av.w)), sub2(tyl, make_float2(bv.z, bv.w)));
             float2 dx = zero2, dy = zero2, dz = zero2;

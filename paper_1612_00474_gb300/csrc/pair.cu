@@ -211,14 +211,15 @@ __global__ void __launch_bounds__(kPairThreads, 6) pair_f32x2_kernel(const SrcF3
         if (base != diag) {
 #pragma unroll 2
             for (int k = 0; k < P; ++k) {
-                const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
+                const float4 a = sA[k], cc = sC[k], d = sD[k];
                 const float4 e = TORQUE ? sE[k] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float2 g = TORQUE ? sG[k] : zero2;
-                const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
-                const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
-                pair_velocity_x2<TORQUE>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
-                                         make_float2(d.x, d.y), make_float2(d.z, d.w), make_float2(e.x, e.y),
-                                         make_float2(e.z, e.w), g, c, ux, uy, uz);
+                const float2 zj = make_float2(cc.x, cc.y);
+                float2 rx, ry, rz, rho2, r2;
+                const bool close = pair_offsets_x2(txh, tyh, txl, tyl, tz2, zj, a, &sB[k], c, rx, ry, rz, rho2, r2);
+                pair_velocity_x2_geo<TORQUE>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
+                                             make_float2(d.x, d.y), make_float2(d.z, d.w), make_float2(e.x, e.y),
+                                             make_float2(e.z, e.w), g, c, ux, uy, uz);
             }
         } else {
             for (int k = 0; k < P; ++k) {
@@ -390,22 +391,10 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                     const float4 a = sA[k + h], cc = sC[k + h], d = sD[k + h];
                     const float4 e = TORQUE ? sE[k + h] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float2 g = TORQUE ? sG[k + h] : zero2;
-                    // offsets from the high parts of the positions (error up to ulp(|x|), which is
-                    // small against |r| beyond 10a); the low parts are added, for the whole warp, when
-                    // some lane has a pair closer than that, which also covers every overlapping pair
-                    float2 rx = sub2(txh, make_float2(a.x, a.y)), ry = sub2(tyh, make_float2(a.z, a.w));
                     const float2 zj = make_float2(cc.x, cc.y);
-                    const float2 rz = sub2(tz2, zj);
-                    float2 rho2 = fma2(rx, rx, mul2(ry, ry));
-                    float2 r2 = fma2(rz, rz, rho2);
-                    const bool close = __any_sync(0xffffffffu, r2.x < c.lo_r2 || r2.y < c.lo_r2);
-                    if (close) {
-                        const float4 b = sB[k + h];
-                        rx = add2(rx, sub2(txl, make_float2(b.x, b.y)));
-                        ry = add2(ry, sub2(tyl, make_float2(b.z, b.w)));
-                        rho2 = fma2(rx, rx, mul2(ry, ry));
-                        r2 = fma2(rz, rz, rho2);
-                    }
+                    float2 rx, ry, rz, rho2, r2;
+                    const bool close =
+                        pair_offsets_x2(txh, tyh, txl, tyl, tz2, zj, a, &sB[k + h], c, rx, ry, rz, rho2, r2);
                     pair_sym_x2<TORQUE>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
                                         make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
                                         make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c, ux, uy, uz,

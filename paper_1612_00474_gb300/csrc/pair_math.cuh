@@ -263,6 +263,38 @@ __device__ __forceinline__ void near_fix(float r2, float inv_r, const X2Consts &
     ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
 }
 
+// Offsets of the target from two sources (packed), from the high parts of the positions; the low
+// parts are added, for the whole warp, when some lane has a pair closer than sqrt(c.lo_r2) = 10a (the
+// error of a high-part offset, up to ulp(|x|), is small against |r| beyond that).  Returns that
+// warp-uniform flag, which also covers every overlapping pair (r < 2a).  Must be called by all 32
+// lanes.  hi: (x_hi, x_hi', y_hi, y_hi') of the two sources; lo: their low parts, read only if needed.
+__device__ __forceinline__ bool pair_offsets_x2(float2 txh, float2 tyh, float2 txl, float2 tyl, float2 zi, float2 zj,
+                                                const float4 &hi, const float4 *lo, const X2Consts &c, float2 &rx,
+                                                float2 &ry, float2 &rz, float2 &rho2, float2 &r2)
+{
+    rx = sub2(txh, make_float2(hi.x, hi.y));
+    ry = sub2(tyh, make_float2(hi.z, hi.w));
+    rz = sub2(zi, zj);
+    rho2 = fma2(rx, rx, mul2(ry, ry));
+    r2 = fma2(rz, rz, rho2);
+    const bool close = __any_sync(0xffffffffu, r2.x < c.lo_r2 || r2.y < c.lo_r2);
+    if (close) {
+        const float4 l = *lo;
+        rx = add2(rx, sub2(txl, make_float2(l.x, l.y)));
+        ry = add2(ry, sub2(tyl, make_float2(l.z, l.w)));
+        rho2 = fma2(rx, rx, mul2(ry, ry));
+        r2 = fma2(rz, rz, rho2);
+    }
+    return close;
+}
+
+// pair_velocity_x2 from the geometry of pair_offsets_x2 (close: some lane may overlap).
+template <bool TORQUE>
+__device__ __forceinline__ void pair_velocity_x2_geo(float2 rx, float2 ry, float2 rz, float2 rho2, float2 r2,
+                                                     bool close, float2 zi, float2 zj, float2 Fx, float2 Fy,
+                                                     float2 Fz, float2 Tx, float2 Ty, float2 Tz, const X2Consts &c,
+                                                     float2 &ux, float2 &uy, float2 &uz);
+
 template <bool TORQUE>
 __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi, float2 zj, float2 Fx, float2 Fy,
                                                  float2 Fz, float2 Tx, float2 Ty, float2 Tz, const X2Consts &c,
@@ -271,16 +303,25 @@ __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi
     const float2 rz = sub2(zi, zj);
     const float2 rho2 = fma2(rx, rx, mul2(ry, ry));
     const float2 r2 = fma2(rz, rz, rho2);
+    const bool close = __any_sync(0xffffffffu, r2.x < c.four_a2 || r2.y < c.four_a2);
+    pair_velocity_x2_geo<TORQUE>(rx, ry, rz, rho2, r2, close, zi, zj, Fx, Fy, Fz, Tx, Ty, Tz, c, ux, uy, uz);
+}
+
+template <bool TORQUE>
+__device__ __forceinline__ void pair_velocity_x2_geo(float2 rx, float2 ry, float2 rz, float2 rho2, float2 r2,
+                                                     bool close, float2 zi, float2 zj, float2 Fx, float2 Fy,
+                                                     float2 Fz, float2 Tx, float2 Ty, float2 Tz, const X2Consts &c,
+                                                     float2 &ux, float2 &uy, float2 &uz)
+{
     const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 inv_r2 = mul2(inv_r, inv_r);
     const float2 ir3 = mul2(inv_r, inv_r2);
     float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
     float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
     float2 ct = ir3;
-    const bool n0 = r2.x < c.four_a2, n1 = r2.y < c.four_a2;
-    if (__any_sync(0xffffffffu, n0 || n1)) {
-        if (n0) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
-        if (n1) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
+    if (close) {
+        if (r2.x < c.four_a2) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
+        if (r2.y < c.four_a2) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
     }
     const float2 Rz = add2(zi, zj);
     const float2 R2 = fma2(Rz, Rz, rho2);
