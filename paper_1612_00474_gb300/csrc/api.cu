@@ -71,7 +71,7 @@ static int check_vec(const void *p, const char *name, bool nullable)
 
 static void free_ws(Workspace &w)
 {
-    void *dev[] = {w.src, w.partial, w.V, w.w, w.red, w.lz, w.pos_a, w.pos_b, w.pos_w,
+    void *dev[] = {w.src, w.partial, w.V, w.w, w.red, w.lz, w.pos_a, w.pos_b, w.pos_w, w.cells,
                    w.vec_a, w.vec_b, w.vec_c, w.vec_d, w.vec_e, w.vec_f, w.vec_g,
                    w.sym_index, w.sym_tgt, w.sym_src};
     for (void *p : dev)
@@ -161,6 +161,7 @@ int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, 
         {(void **)&w.pos_a, vb},
         {(void **)&w.pos_b, vb},
         {(void **)&w.pos_w, vb},
+        {&w.cells, cell_lists_bytes(max_N)},
         {(void **)&w.vec_a, vb},
         {(void **)&w.vec_b, vb},
         {(void **)&w.vec_c, vb},

@@ -23,6 +23,7 @@
 //     relative accuracy anywhere in a large box; per-tile float32 sums are added with Kahan
 //     compensation.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -1013,17 +1014,199 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
     return cuda_fail(cudaGetLastError(), "pair kernels");
 }
 
+// ------------------------------------------------------------------ cell lists for the force pass
+// Square cells of side h = the screen radius on an unbounded grid, hashed into G x G buckets by their
+// coordinates modulo G (G ~ sqrt(N), a power of two in [64, kCellGrid]; far-away cells that share a
+// bucket only add candidates, which the distance screen rejects); heights are not binned.  Buckets are filled by a
+// counting sort and each bucket's list is then sorted by sphere index, so that every force is summed
+// in a fixed order (buckets in a fixed order, spheres by index within a bucket).  A bucket with more
+// than kCellMaxSorted spheres sets the overfull flag and the all-pairs kernel takes the product.
+__device__ __forceinline__ void cell_coords(double x, double y, double inv_h, int &cx, int &cy)
+{
+    // clamped so that the conversion is defined for any input (non-finite positions land in one cell)
+    const double fx = floor(fmin(fmax(x * inv_h, -1e9), 1e9)), fy = floor(fmin(fmax(y * inv_h, -1e9), 1e9));
+    cx = fx == fx ? (int)fx : 0;
+    cy = fy == fy ? (int)fy : 0;
+}
+// G x G buckets, G a power of two in [64, kCellGrid] chosen by N (cell_grid)
+__device__ __forceinline__ int cell_bucket(int cx, int cy, int G)
+{
+    return (cy & (G - 1)) * G + (cx & (G - 1));
+}
+
+static int cell_grid(int64_t N)
+{
+    int G = 64;
+    while (G < kCellGrid && (int64_t)G * G < N) G *= 2;
+    return G;
+}
+
+__global__ void cell_count_kernel(const double *__restrict__ pos, int N, double inv_h, int G, int *__restrict__ count,
+                                  int *__restrict__ cellof)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int cx, cy;
+    cell_coords(pos[i], pos[N + i], inv_h, cx, cy);
+    const int c = cell_bucket(cx, cy, G);
+    cellof[i] = c;
+    atomicAdd(&count[c], 1);
+}
+
+// Exclusive scan of the nb = G^2 counts by one block: 1024 threads, nb / 1024 (a multiple of 4)
+// consecutive buckets each, read (twice: sums, then the running offsets) and written as int4.
+__global__ void __launch_bounds__(1024) cell_scan_kernel(const int *__restrict__ count, int nb, int *__restrict__ start,
+                                                         int *__restrict__ fill)
+{
+    const int per = nb / 1024;
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = tid * per;
+    const int4 *in4 = reinterpret_cast<const int4 *>(count + c0);
+    int s = 0;
+#pragma unroll 4
+    for (int k = 0; k < per / 4; ++k) {
+        const int4 q = in4[k];
+        s += (q.x + q.y) + (q.z + q.w);
+    }
+    int inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        wsum[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    int run = inc - s + (warp > 0 ? wsum[warp - 1] : 0);
+    int4 *s4 = reinterpret_cast<int4 *>(start + c0), *f4 = reinterpret_cast<int4 *>(fill + c0);
+#pragma unroll 4
+    for (int k = 0; k < per / 4; ++k) {
+        const int4 q = in4[k];
+        int4 o;
+        o.x = run;
+        o.y = o.x + q.x;
+        o.z = o.y + q.y;
+        o.w = o.z + q.z;
+        run = o.w + q.w;
+        s4[k] = o;
+        f4[k] = o;
+    }
+    if (tid == 1023) start[nb] = run;
+}
+
+__global__ void cell_fill_kernel(int N, const int *__restrict__ cellof, int *__restrict__ fill, int *__restrict__ idx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    idx[atomicAdd(&fill[cellof[i]], 1)] = i;
+}
+
+__global__ void cell_sort_kernel(const double *__restrict__ pos, int N, int nb, const int *__restrict__ start,
+                                 int *__restrict__ idx, float4 *__restrict__ posf, CellHeader *__restrict__ hdr)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nb) return;
+    const int a0 = start[c], a1 = start[c + 1];
+    if (a1 - a0 > kCellMaxSorted) {
+        hdr->overfull = 1;  // every writer stores the same value
+        return;
+    }
+    for (int m = a0 + 1; m < a1; ++m) {
+        const int v = idx[m];
+        int q = m - 1;
+        while (q >= a0 && idx[q] > v) {
+            idx[q + 1] = idx[q];
+            --q;
+        }
+        idx[q + 1] = v;
+    }
+    for (int m = a0; m < a1; ++m) {
+        const int j = idx[m];
+        posf[m] = make_float4((float)pos[j], (float)pos[N + j], (float)pos[2 * N + j], __int_as_float(j));
+    }
+}
+
+// Force pass over the buckets: threads take the spheres in bucket order (neighbouring threads search
+// the same buckets); candidates are screened in float32 against the radius of the all-pairs kernel,
+// queued per thread and evaluated in float64 after the search, in the same fixed order.
+__global__ void __launch_bounds__(128) forces_cell_kernel(const double *__restrict__ pos, int N, double a,
+                                                          double weight, double U0, double b, float cut2,
+                                                          double inv_h, int G, const CellHeader *__restrict__ hdr,
+                                                          const int *__restrict__ start, const int *__restrict__ idx,
+                                                          const float4 *__restrict__ posf, double *__restrict__ F)
+{
+    if (cell_overfull(hdr)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int i = idx[k];
+    const double xi = pos[i], yi = pos[N + i], zi = pos[2 * N + i];
+    const float xf = (float)xi, yf = (float)yi, zf = (float)zi;
+    int cx, cy;
+    cell_coords(xi, yi, inv_h, cx, cy);
+    const double f0 = U0 / b;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    // the bucket loops have different lengths in different lanes, so the float64 work waits until
+    // after them (all lanes flush together); a queue filled earlier (dense configurations) flushes
+    // on its own
+    constexpr int kQ = 64;
+    int queue[kQ];
+    int nq = 0;
+    auto flush = [&]() {
+        for (int q = 0; q < nq; ++q) {
+            const int j = queue[q];
+            const double dx = xi - pos[j], dy = yi - pos[N + j], dz = zi - pos[2 * N + j];
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r > 0.0) {
+                const double mm = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
+                fx += mm * dx;
+                fy += mm * dy;
+                fz += mm * dz;
+            }
+        }
+        nq = 0;
+    };
+    for (int dyc = -1; dyc <= 1; ++dyc)
+        for (int dxc = -1; dxc <= 1; ++dxc) {
+            const int cc = cell_bucket(cx + dxc, cy + dyc, G);
+            for (int m = start[cc]; m < start[cc + 1]; ++m) {
+                const float4 pj = posf[m];
+                const int j = __float_as_int(pj.w);
+                const float ex = xf - pj.x, ey = yf - pj.y, ez = zf - pj.z;
+                if (j != i && fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < cut2) {
+                    queue[nq++] = j;
+                    if (nq == kQ) flush();
+                }
+            }
+        }
+    flush();
+    fz += (zi < a ? f0 : f0 * exp(-(zi - a) / b)) - weight;
+    F[i] = fx;
+    F[N + i] = fy;
+    F[2 * N + i] = fz;
+}
+
 // ------------------------------------------------------------------ forces (Sec. III)
 // F_i = -weight z + sum_j f(|r_ij|) r_ij/|r_ij| + f_wall(z_i) z with f = -dU/dr of Eq. (soft_potential).
 // Pairs are screened in float32 against a cutoff with a generous margin; the ones inside are
 // evaluated in float64.
 // PER: pseudo-periodic boundaries (Appendix B), minimum image in x (period Lx) and y (period Ly); the
 // positions are then the ones folded into the unit cell.
+// gate: when given, the kernel runs only if the cell-list pass declined the configuration.
 template <bool PER>
 __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ pos, int N, double a, double weight,
                                                      double U0, double b, float cut2, double *__restrict__ F,
-                                                     double Lx = 0.0, double Ly = 0.0)
+                                                     double Lx = 0.0, double Ly = 0.0,
+                                                     const CellHeader *gate = nullptr)
 {
+    if (gate && !cell_overfull(gate)) return;
     __shared__ float4 sp[64];  // float32 copies of the tile's positions, for the screen only
     const int tid = threadIdx.x;
     const int i = blockIdx.x * 128 + tid;
@@ -1117,21 +1300,38 @@ __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ 
 int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_params *fp, double *F)
 {
     const double a = ctx->p.a;
-    const double rc = 2.0 * a + 50.0 * fp->b;
-    const double rcm = rc * 1.01 + 0.01 * a;
+    const double r_cut = 2.0 * a + 50.0 * fp->b;
+    const double rcm = r_cut * 1.01 + 0.01 * a;
     const float cut2 = (float)(rcm * rcm);
+    const int n = (int)N;
+    cudaStream_t st = ctx->stream;
     if (ctx->Lx > 0.0) {
         const int pb = 256;
-        wrap_kernel<<<(unsigned)((N + pb - 1) / pb), pb, 0, ctx->stream>>>(pos, (int)N, ctx->Lx, ctx->Ly, ctx->ws.pos_w);
-        forces_kernel<true><<<(unsigned)((N + 127) / 128), 128, 0, ctx->stream>>>(
-            ctx->ws.pos_w, (int)N, a, fp->weight, fp->U0, fp->b, cut2, F, ctx->Lx, ctx->Ly);
+        wrap_kernel<<<(unsigned)((N + pb - 1) / pb), pb, 0, st>>>(pos, n, ctx->Lx, ctx->Ly, ctx->ws.pos_w);
+        forces_kernel<true><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(ctx->ws.pos_w, n, a, fp->weight, fp->U0,
+                                                                         fp->b, cut2, F, ctx->Lx, ctx->Ly);
         count_launches(2);
-    } else {
-        forces_kernel<false><<<(unsigned)((N + 127) / 128), 128, 0, ctx->stream>>>(pos, (int)N, a, fp->weight, fp->U0,
-                                                                                    fp->b, cut2, F);
-        count_launches(1);
+        return cuda_fail(cudaGetLastError(), "forces kernel");
     }
-    return cuda_fail(cudaGetLastError(), "forces kernel");
+    // buckets of cells of side = the screen radius, then the bucket force pass; the all-pairs kernel
+    // runs instead when a bucket holds more than kCellMaxSorted spheres (it checks the flag itself)
+    CellLists L = cell_lists(ctx->ws.cells, ctx->max_N);
+    const double inv_h = 1.0 / rcm;
+    const int G = cell_grid(N), nb = G * G;
+    int rc;
+    // the header (overfull flag) and the bucket counts are contiguous: one clear
+    if ((rc = cuda_fail(cudaMemsetAsync(L.hdr, 0, 64 + sizeof(int) * (nb + 1), st), "clear cell counts")))
+        return rc;
+    cell_count_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(pos, n, inv_h, G, L.count, L.cellof);
+    cell_scan_kernel<<<1, 1024, 0, st>>>(L.count, nb, L.start, L.fill);
+    cell_fill_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(n, L.cellof, L.fill, L.idx);
+    cell_sort_kernel<<<nb / 256, 256, 0, st>>>(pos, n, nb, L.start, L.idx, L.posf, L.hdr);
+    forces_cell_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(pos, n, a, fp->weight, fp->U0, fp->b, cut2, inv_h,
+                                                                    G, L.hdr, L.start, L.idx, L.posf, F);
+    forces_kernel<false><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(pos, n, a, fp->weight, fp->U0, fp->b, cut2, F,
+                                                                      0.0, 0.0, L.hdr);
+    count_launches(6);
+    return cuda_fail(cudaGetLastError(), "forces kernels");
 }
 
 }  // namespace rpb

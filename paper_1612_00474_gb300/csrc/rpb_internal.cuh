@@ -59,6 +59,47 @@ inline PairConsts<R> make_consts(double a)
     return c;
 }
 
+// Cell lists of the force pass (pair.cu): header, then int arrays in one allocation.
+constexpr int kCellGrid = 256;                  // at most kCellGrid x kCellGrid buckets (cells hashed modulo G)
+constexpr int kCells = kCellGrid * kCellGrid;
+constexpr int kCellMaxSorted = 512;             // a fuller cell hands the force pass to the all-pairs kernel
+struct CellHeader {
+    int overfull, pad[15];  // 64 bytes, followed by the bucket counts
+};
+__device__ __forceinline__ bool cell_overfull(const CellHeader *h)
+{
+    return *(volatile const int *)&h->overfull != 0;
+}
+struct CellLists {
+    CellHeader *hdr;
+    int *count, *start, *fill, *cellof, *idx;
+    float4 *posf;  // float32 copies (x, y, z, index bits) in bucket order
+};
+// count, start and fill hold kCells + 1 entries each and are read and written as int4, so each array
+// starts on a 16-byte boundary: stride kCellStride (a multiple of 4 ints) after a 64-byte header, in
+// an allocation that cudaMalloc aligns to 256 bytes.
+constexpr int kCellStride = kCells + 4;
+static_assert(kCellStride % 4 == 0 && kCellStride >= kCells + 1, "bucket array stride");
+inline size_t cell_lists_bytes(int64_t max_N)
+{
+    return 64 + sizeof(int) * (size_t)3 * kCellStride + sizeof(float4) * (size_t)max_N +
+           sizeof(int) * (size_t)2 * max_N;
+}
+inline CellLists cell_lists(void *base, int64_t max_N)
+{
+    CellLists L;
+    char *p = (char *)base;
+    L.hdr = (CellHeader *)p;
+    int *q = (int *)(p + 64);
+    L.count = q;
+    L.start = q + kCellStride;
+    L.fill = q + 2 * kCellStride;
+    L.posf = (float4 *)(q + 3 * kCellStride);  // 64 + 12 kCellStride bytes: 16-byte aligned
+    L.cellof = (int *)(L.posf + max_N);
+    L.idx = L.cellof + max_N;
+    return L;
+}
+
 // Scratch owned by a context.
 struct Workspace {
     void *src = nullptr;          // packed sources, max_N records (SrcF64 size)
@@ -72,6 +113,7 @@ struct Workspace {
     double *pos_a = nullptr;      // displaced positions (RFD), 3 max_N
     double *pos_b = nullptr;
     double *pos_w = nullptr;      // positions folded into the unit cell (pseudo-periodic mode), 3 max_N
+    void *cells = nullptr;        // cell lists of the force pass (cell_lists_bytes)
     double *vec_a = nullptr;      // 3 max_N scratch vectors for the AB step
     double *vec_b = nullptr;
     double *vec_c = nullptr;

@@ -188,8 +188,8 @@ class Context:
 
     def close(self):
         if self._h:
-            _check(load().rpb_destroy(self._h))
-            self._h = None
+            h, self._h = self._h, None  # never destroyed twice, even when destroy reports an error
+            _check(load().rpb_destroy(h))
 
     def __del__(self):
         try:
@@ -308,8 +308,8 @@ class BatchContext:
 
     def close(self):
         if self._h:
-            _check(load().rpb_batch_destroy(self._h))
-            self._h = None
+            h, self._h = self._h, None  # never destroyed twice, even when destroy reports an error
+            _check(load().rpb_batch_destroy(h))
 
     def __del__(self):
         try:
