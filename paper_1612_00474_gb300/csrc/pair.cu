@@ -1326,8 +1326,10 @@ int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_para
     cell_scan_kernel<<<1, 1024, 0, st>>>(L.count, nb, L.start, L.fill);
     cell_fill_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(n, L.cellof, L.fill, L.idx);
     cell_sort_kernel<<<nb / 256, 256, 0, st>>>(pos, n, nb, L.start, L.idx, L.posf, L.hdr);
-    forces_cell_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(pos, n, a, fp->weight, fp->U0, fp->b, cut2, inv_h,
-                                                                    G, L.hdr, L.start, L.idx, L.posf, F);
+    // small systems in 32-sphere blocks: their float64 near pairs then spread over more SMs
+    const int fb = N < 128 * ctx->num_sms ? 32 : 128;
+    forces_cell_kernel<<<(unsigned)((N + fb - 1) / fb), fb, 0, st>>>(pos, n, a, fp->weight, fp->U0, fp->b, cut2, inv_h,
+                                                                     G, L.hdr, L.start, L.idx, L.posf, F);
     forces_kernel<false><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(pos, n, a, fp->weight, fp->U0, fp->b, cut2, F,
                                                                       0.0, 0.0, L.hdr);
     count_launches(6);
