@@ -451,33 +451,51 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
 
 // Row partials of the targets plus column partials of the sources, fixed order; float64 self term
 // (with the torque's wall self coupling when T is given); s_i / (8 pi eta).
-__global__ void pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
+__global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
                                        const int *__restrict__ row_seg, const int *__restrict__ col_start, int N,
                                        const double *__restrict__ pos, const double *__restrict__ F,
                                        const double *__restrict__ T, PairConsts<double> c, double a, double scale,
                                        double *__restrict__ U)
 {
-    // one CTA per 128-sphere tile b, thread (q, l) = (component, sphere): coalesced column sums
+    // one CTA of 2 x 384 threads per 128-sphere tile, the longest columns first; thread (half, q, l):
+    // component q of sphere l, rows of its column with parity `half`
     __shared__ double s[3][kTile];
-    const int b = blockIdx.x;
-    const int q = threadIdx.x / kTile, l = threadIdx.x - q * kTile;
-    double acc = 0.0;
-    for (int k = row_seg[b]; k < row_seg[b + 1]; ++k) acc += tgt_part[((size_t)k * 3 + q) * kTile + l];
-    // column of float32 partials: compensated float32 sum (GB300's float64 rate would make a float64
-    // add per partial the bottleneck), converted once
+    __shared__ double s1[3][kTile];
+    const int nb = gridDim.x;
+    const int b = nb - 1 - (int)blockIdx.x;
+    const int half = threadIdx.x / (3 * kTile);
+    const int r = threadIdx.x - half * 3 * kTile;
+    const int q = r / kTile, l = r - q * kTile;
+    // column of float32 partials: four independent compensated float32 sums per thread (GB300's
+    // float64 rate would make a float64 add per partial the bottleneck; one chain per thread would
+    // leave the column latency-bound), converted once and added in a fixed order
     const float *col = src_part + (size_t)col_start[b] * 3 * kTile + q * kTile + l;
-    float cs = 0.f, cc = 0.f;
-#pragma unroll 4
-    for (int bb = 0; bb < b; ++bb) {
-        const float yv = col[(size_t)bb * 3 * kTile] - cc;
-        const float tv = cs + yv;
-        cc = (tv - cs) - yv;
-        cs = tv;
+    float cs[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int bb = half; bb < b; bb += 8) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int row = bb + 2 * u;
+            if (row < b) {
+                const float yv = col[(size_t)row * 3 * kTile] - cc[u];
+                const float tv = cs[u] + yv;
+                cc[u] = (tv - cs[u]) - yv;
+                cs[u] = tv;
+            }
+        }
     }
-    s[q][l] = acc + ((double)cs - (double)cc);
+    double v = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v += (double)cs[u] - (double)cc[u];
+    if (half == 1) s1[q][l] = v;
+    __syncthreads();
+    if (half == 0) {
+        double acc = 0.0;
+        for (int k = row_seg[b]; k < row_seg[b + 1]; ++k) acc += tgt_part[((size_t)k * 3 + q) * kTile + l];
+        s[q][l] = acc + (v + s1[q][l]);
+    }
     __syncthreads();
     const int i = b * kTile + l;
-    if (q != 0 || i >= N) return;
+    if (half != 0 || q != 0 || i >= N) return;
     double ux = s[0][l], uy = s[1][l], uz = s[2][l];
     const double z = pos[2 * N + i];
     const double si = H0(z / a);
@@ -617,7 +635,7 @@ static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F,
             pair_f32x2_sym_kernel<6, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
                                                                                  w.sym_src);
     }
-    pair_sym_reduce_kernel<<<(N + kTile - 1) / kTile, 3 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
+    pair_sym_reduce_kernel<<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
                                                              cs, N, pos, F, T, make_consts<double>(a), a,
                                                              1.0 / (8.0 * kPi * ctx->p.eta), U);
     count_launches(3);

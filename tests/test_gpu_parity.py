@@ -441,3 +441,28 @@ def test_mobility_fp32_far_from_origin(ctx32, with_T):
     got = host(ctx32.mobility_apply(dev(pos), dev(F), dev(T) if with_T else None), N)
     ref = O.mobility_apply(pos, F, T)
     assert maxrel(got, ref) <= 1e-5
+
+
+def test_forces_bucket_overflow_fallback(ctx64):
+    """600 spheres piled into one 6a x 6a column (one bucket holds more than 512): the cell-list pass
+    declines and the all-pairs kernel computes the forces."""
+    rng = np.random.default_rng(71)
+    N = 600
+    pos = np.column_stack([rng.uniform(0, 6, N), rng.uniform(0, 6, N), rng.uniform(0.5, 40.0, N)])
+    got = host(ctx64.forces(dev(pos), weight=1.0, U0=1.0, b=0.1), N)
+    assert maxrel(got, O.forces(pos, 1.0, 1.0, 1.0, 0.1)) <= 1e-12
+
+
+def test_forces_hashed_buckets_far_apart(ctx64):
+    """Clusters far apart along a 2e5 a strip and on a diagonal, so that distant cells share buckets
+    (cells are hashed modulo the bucket grid): the screen must reject the aliased candidates."""
+    rng = np.random.default_rng(72)
+    parts = []
+    for cx in (0.0, 64 * 7.08, 2e5, -3e4):
+        for cy in (0.0, 64 * 7.08 * 3, -5e3):
+            parts.append(np.column_stack([cx + rng.uniform(0, 8, 40), cy + rng.uniform(0, 8, 40),
+                                          rng.uniform(0.8, 3.0, 40)]))
+    pos = np.vstack(parts)
+    N = len(pos)
+    got = host(ctx64.forces(dev(pos), weight=1.0, U0=1.0, b=0.1), N)
+    assert maxrel(got, O.forces(pos, 1.0, 1.0, 1.0, 0.1)) <= 1e-12
