@@ -58,6 +58,17 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return r;  // valid in thread 0
 }
 
+// Sum of n partials by one warp in a fixed order (lane-strided sums, then a butterfly); every lane
+// returns the total.
+__device__ __forceinline__ double warp_sum_partials(const double *__restrict__ p, int n)
+{
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int b = lane; b < n; b += 32) v += p[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // red[k * G + b] = sum over block b's rows of V[k][r] * w[r], k = 0 .. nvec-1 (grid = (G, nvec)).
 __global__ void __launch_bounds__(kBlasThreads) dots_kernel(const double *__restrict__ V, size_t ld, int64_t n,
                                                              const double *__restrict__ w, double *__restrict__ red)
@@ -83,11 +94,13 @@ __global__ void __launch_bounds__(kBlasThreads) project_out_kernel(const double 
 {
     __shared__ double coef[kMaxIter + 1];
     __shared__ double sh[kBlasThreads / 32];
-    for (int k = threadIdx.x; k < nvec; k += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < Gred; ++b) s += red[(size_t)k * Gred + b];
-        coef[k] = s;
-        if (blockIdx.x == 0) coef_out[k] = s;
+    const int warp = threadIdx.x >> 5;
+    for (int k = warp; k < nvec; k += kBlasThreads / 32) {
+        const double s = warp_sum_partials(red + (size_t)k * Gred, Gred);
+        if ((threadIdx.x & 31) == 0) {
+            coef[k] = s;
+            if (blockIdx.x == 0) coef_out[k] = s;
+        }
     }
     __syncthreads();
     double acc = 0.0;
@@ -115,9 +128,8 @@ __global__ void scale_kernel(const double *__restrict__ w, int64_t n, const doub
 // |W| from its squared-norm partials.
 __global__ void norm_init_kernel(const double *__restrict__ red, int G, double *__restrict__ status)
 {
+    const double s = warp_sum_partials(red, G);  // launched as one warp
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < G; ++b) s += red[b];
         const double nw = sqrt(s);
         status[ST_NW] = nw;
         status[ST_INV_NW] = nw > 0.0 ? 1.0 / nw : 0.0;
@@ -134,8 +146,7 @@ __global__ void __launch_bounds__(32) lanczos_tail_kernel(double *__restrict__ l
     __shared__ double q0[kMaxIter];
     __shared__ double sl[kMaxIter];
     __shared__ double red[32];
-    double bn = 0.0;
-    for (int b = 0; b < Gred; ++b) bn += red_norm[b];  // identical order in every lane
+    const double bn = warp_sum_partials(red_norm, Gred);  // the same value in every lane
     lanczos_tail_warp(lz, L, k, tol, lz[L.c1 + k] + lz[L.c2 + k], sqrt(bn), q0, sl, red);
 }
 
