@@ -73,7 +73,7 @@ static void free_ws(Workspace &w)
 {
     void *dev[] = {w.src, w.partial, w.V, w.w, w.red, w.lz, w.pos_a, w.pos_b, w.pos_w, w.cells,
                    w.vec_a, w.vec_b, w.vec_c, w.vec_d, w.vec_e, w.vec_f, w.vec_g,
-                   w.sym_index, w.sym_tgt, w.sym_src};
+                   w.sym_index, w.sym_tgt, w.sym_src, w.src2};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (w.host_status) cudaFreeHost(w.host_status);
@@ -187,12 +187,20 @@ int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, 
         const size_t src_bytes = sym_src_part_bytes(max_N);
         c->sym_enabled = p->precision == RPB_FP32 && !(v && strcmp(v, "0") == 0) && max_N >= 2 * kTile &&
                          src_bytes <= ((size_t)8 << 30);
+        // the two-right-hand-side pass (fused product and the first Lanczos product of a step) keeps
+        // six components per partial: twice the scratch, used while that stays below 8 GB too;
+        // RPB_FP32_SYM_RHS2=0 turns it off
+        const char *v2 = getenv("RPB_FP32_SYM_RHS2");
+        c->sym_rhs2 = c->sym_enabled && p->wall && !(v2 && strcmp(v2, "0") == 0) && 2 * src_bytes <= ((size_t)8 << 30);
+        const size_t mult = c->sym_rhs2 ? 2 : 1;
         if (c->sym_enabled) {
             w.sym_index_ints = sym_index_ints(max_N, c->num_sms);
-            w.sym_tgt_bytes = sym_tgt_part_bytes(max_N, c->num_sms);
+            w.sym_tgt_bytes = mult * sym_tgt_part_bytes(max_N, c->num_sms);
+            w.sym_src_bytes = mult * src_bytes;
             if (cudaMalloc(&w.sym_index, w.sym_index_ints * sizeof(int)) != cudaSuccess ||
                 cudaMalloc(&w.sym_tgt, w.sym_tgt_bytes) != cudaSuccess ||
-                cudaMalloc(&w.sym_src, src_bytes) != cudaSuccess) {
+                cudaMalloc(&w.sym_src, w.sym_src_bytes) != cudaSuccess ||
+                (c->sym_rhs2 && cudaMalloc(&w.src2, (size_t)max_N * sizeof(float4)) != cudaSuccess)) {
                 cudaGetLastError();
                 set_error("cudaMalloc of the symmetric-pass scratch (%zu bytes) failed", src_bytes);
                 free_ws(w);
@@ -369,17 +377,33 @@ int rpb_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step,
     double *F = w.vec_a, *T = w.vec_b, *Un = w.vec_c, *W = w.vec_d, *Wt = w.vec_e, *g = w.vec_f, *drift = w.vec_g;
     if ((rc = forces_impl(ctx, N, pos, fp, F))) return rc;
     if ((rc = fill_torque(ctx, N, fp->torque, T))) return rc;
-    if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
     int iters = 0, conv = 0;
     double err = -1.0;
     int lrc = RPB_OK;
     if (ctx->p.kT > 0.0) {
         if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 0u, 0u, W))) return rc;
         if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 1u, 0u, Wt))) return rc;
-        lrc = lanczos_impl(ctx, N, pos, W, g, tol, max_iter, &iters, &err, &conv);
+        if (mobility_apply2_ok(ctx, N)) {
+            // the deterministic velocity and the first Lanczos product M v_0 share one pair pass
+            bool zero = false;
+            if ((rc = lanczos_init(ctx, N, W, &zero))) return rc;
+            if (zero) {
+                if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
+                if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "zero g")))
+                    return rc;
+                conv = 1;
+            } else {
+                if ((rc = mobility_apply2_impl(ctx, N, pos, F, T, w.V, Un, w.w))) return rc;
+                lrc = lanczos_run(ctx, N, pos, g, tol, max_iter, true, &iters, &err, &conv);
+            }
+        } else {
+            if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
+            lrc = lanczos_impl(ctx, N, pos, W, g, tol, max_iter, &iters, &err, &conv);
+        }
         if (lrc != RPB_OK && lrc != RPB_ENOCONV) return lrc;
         if ((rc = rfd_impl(ctx, N, pos, Wt, delta, drift, rfd == RPB_RFD_ONE_SIDED))) return rc;
     } else {
+        if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
         // kT = 0: no Brownian increment and no drift (both carry a factor kT); the deterministic
         // scheme needs neither the noise nor M^{1/2}
         if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "clear g")) ||

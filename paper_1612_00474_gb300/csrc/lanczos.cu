@@ -164,8 +164,46 @@ __global__ void combine_kernel(const double *__restrict__ V, size_t ld, int64_t 
     }
 }
 
+int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero)
+{
+    cudaStream_t st = ctx->stream;
+    const int64_t n = 3 * N;
+    const LzLayout L(ctx->max_iter);
+    double *status = ctx->ws.lz + L.status;
+    double *red = ctx->ws.red;
+    double *hs = ctx->ws.host_status;
+    const int G = blas_grid(n, ctx->num_sms);
+    int rc;
+    // |W| and v_0 = W / |W|
+    dots_kernel<<<dim3(G, 1), kBlasThreads, 0, st>>>(W, 0, n, W, red);
+    norm_init_kernel<<<1, 32, 0, st>>>(red, G, status);
+    scale_kernel<<<G, kBlasThreads, 0, st>>>(W, n, status, ST_INV_NW, ctx->ws.V);
+    count_launches(3);
+    if ((rc = cuda_fail(cudaMemcpyAsync(hs, status, 8 * sizeof(double), cudaMemcpyDeviceToHost, st), "status copy")))
+        return rc;
+    if ((rc = cuda_fail(cudaStreamSynchronize(st), "lanczos init"))) return rc;
+    *nw_zero = hs[ST_NW] == 0.0;
+    return RPB_OK;
+}
+
 int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol, int max_iter,
                  int *iters_out, double *err_out, int *converged_out)
+{
+    bool zero = false;
+    int rc;
+    if ((rc = lanczos_init(ctx, N, W, &zero))) return rc;
+    if (zero) {
+        if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "zero g"))) return rc;
+        if (iters_out) *iters_out = 0;
+        if (err_out) *err_out = -1.0;
+        if (converged_out) *converged_out = 1;
+        return RPB_OK;
+    }
+    return lanczos_run(ctx, N, pos, g, tol, max_iter, false, iters_out, err_out, converged_out);
+}
+
+int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double tol, int max_iter, bool first_done,
+                int *iters_out, double *err_out, int *converged_out)
 {
     cudaStream_t st = ctx->stream;
     const int64_t n = 3 * N;
@@ -180,28 +218,12 @@ int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, do
     const int G = blas_grid(n, ctx->num_sms);
     double *red_norm = red + (size_t)(ctx->max_iter + 1) * G;
     int rc;
-
-    // |W| and v_0 = W / |W|
-    dots_kernel<<<dim3(G, 1), kBlasThreads, 0, st>>>(W, 0, n, W, red);
-    norm_init_kernel<<<1, 32, 0, st>>>(red, G, status);
-    scale_kernel<<<G, kBlasThreads, 0, st>>>(W, n, status, ST_INV_NW, V);
-    count_launches(3);
-    if ((rc = cuda_fail(cudaMemcpyAsync(hs, status, 8 * sizeof(double), cudaMemcpyDeviceToHost, st), "status copy")))
-        return rc;
-    if ((rc = cuda_fail(cudaStreamSynchronize(st), "lanczos init"))) return rc;
-    if (hs[ST_NW] == 0.0) {
-        if ((rc = cuda_fail(cudaMemsetAsync(g, 0, n * sizeof(double), st), "zero g"))) return rc;
-        if (iters_out) *iters_out = 0;
-        if (err_out) *err_out = -1.0;
-        if (converged_out) *converged_out = 1;
-        return RPB_OK;
-    }
     int m = 0;
     bool stopped = false;
     double eps = -1.0;
     for (int k = 0; k < max_iter; ++k) {
         const double *vk = V + (size_t)k * ld;
-        if ((rc = mobility_apply_impl(ctx, N, pos, vk, nullptr, w))) return rc;
+        if (!(k == 0 && first_done) && (rc = mobility_apply_impl(ctx, N, pos, vk, nullptr, w))) return rc;
         const int nv = k + 1;
         dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
         project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c1, nullptr);

@@ -50,6 +50,16 @@ __global__ void pack_f32_kernel(const double *__restrict__ pos, const double *__
     out[i] = o;
 }
 
+// Second right-hand side of the two-RHS symmetric pass: s_j P_j as float32 (x, y, z, 0).
+__global__ void pack_rhs2_kernel(const double *__restrict__ pos, const double *__restrict__ P, int N, double a,
+                                 float4 *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double s = H0(pos[2 * N + i] / a);
+    out[i] = make_float4((float)(s * P[i]), (float)(s * P[N + i]), (float)(s * P[2 * N + i]), 0.f);
+}
+
 __global__ void pack_f64_kernel(const double *__restrict__ pos, const double *__restrict__ F,
                                 const double *__restrict__ T, int N, double a, int wall, SrcF64 *__restrict__ out)
 {
@@ -292,20 +302,26 @@ struct SymSeg {
     int b, t0, t1, pad;
 };
 
-template <int MINB, bool TORQUE>
+// RHS2: a second translation-translation right-hand side (src2: s_j P_j per sphere) evaluated with
+// the same pair blocks; components 3..5 of the partials carry it.
+template <int MINB, bool TORQUE, bool RHS2 = false>
 __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(const SrcF32 *__restrict__ src, int N,
                                                                              const SymCta *__restrict__ ctas,
                                                                              const SymSeg *__restrict__ segs,
                                                                              X2Consts c,
                                                                              const int *__restrict__ col_start,
                                                                              double *__restrict__ tgt_part,
-                                                                             float *__restrict__ src_part)
+                                                                             float *__restrict__ src_part,
+                                                                             const float4 *__restrict__ src2 = nullptr)
 {
     constexpr int P = kTile / 2;
+    constexpr int NC = RHS2 ? 6 : 3;
     __shared__ float4 sA[P], sB[P], sC[P], sD[P];
     __shared__ float4 sE[TORQUE ? P : 1];
     __shared__ float2 sG[TORQUE ? P : 1];
-    __shared__ float sv[4][3][kTile];
+    __shared__ float4 sP[RHS2 ? P : 1];
+    __shared__ float2 sQ[RHS2 ? P : 1];
+    __shared__ float sv[4][NC][kTile];
     const SymCta cd = ctas[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2 zero2 = make_float2(0.f, 0.f);
@@ -317,31 +333,39 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     float *fD = reinterpret_cast<float *>(sD);
     float *fE = reinterpret_cast<float *>(sE);
     float *fG = reinterpret_cast<float *>(sG);
+    float *fP = reinterpret_cast<float *>(sP);
+    float *fQ = reinterpret_cast<float *>(sQ);
     for (int sg = cd.s0; sg < cd.s1; ++sg) {
     const SymSeg seg = segs[sg];
     const int i = seg.b * kTile + tid;
     float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 tf = make_float4(1.f, 0.f, 0.f, 0.f);
     float4 th = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < N) {
         tp = src[i].p;
         tf = src[i].f;
         if (TORQUE) th = src[i].t;
+        if (RHS2) tq = src2[i];
     }
     const float2 txh = make_float2(tp.x, tp.x), tyh = make_float2(tp.y, tp.y);
     const float2 txl = make_float2(tp.z, tp.z), tyl = make_float2(tp.w, tp.w);
     const float2 tz2 = make_float2(tf.x, tf.x);
     const float2 Gx = make_float2(tf.y, tf.y), Gy = make_float2(tf.z, tf.z), Gz = make_float2(tf.w, tf.w);
     const float2 Hx = make_float2(th.x, th.x), Hy = make_float2(th.y, th.y), Hz = make_float2(th.z, th.z);
-    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    const float2 Qx = make_float2(tq.x, tq.x), Qy = make_float2(tq.y, tq.y), Qz = make_float2(tq.z, tq.z);
+    float ks[NC], kc[NC];  // compensated per-tile sums of the target side
+#pragma unroll
+    for (int q = 0; q < NC; ++q) ks[q] = kc[q] = 0.f;
     for (int t = seg.t0; t < seg.t1; ++t) {
         const int j = t * kTile + tid;
         float4 sp_ = make_float4(1e18f, 0.f, 0.f, 0.f), sf_ = make_float4(1.f, 0.f, 0.f, 0.f);
-        float4 st_ = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 st_ = make_float4(0.f, 0.f, 0.f, 0.f), sq_ = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j < N) {
             sp_ = src[j].p;
             sf_ = src[j].f;
             if (TORQUE) st_ = src[j].t;
+            if (RHS2) sq_ = src2[j];
         }
         fA[4 * pp + hh] = sp_.x;
         fA[4 * pp + 2 + hh] = sp_.y;
@@ -356,8 +380,15 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
             fE[4 * pp + 2 + hh] = st_.y;
             fG[2 * pp + hh] = st_.z;
         }
+        if (RHS2) {
+            fP[4 * pp + hh] = sq_.x;
+            fP[4 * pp + 2 + hh] = sq_.y;
+            fQ[2 * pp + hh] = sq_.z;
+        }
         __syncthreads();
-        float2 ux = zero2, uy = zero2, uz = zero2;
+        float2 u[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) u[q] = zero2;
         if (t == seg.b) {
             for (int k = 0; k < P; ++k) {
                 const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
@@ -365,46 +396,55 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 const float2 g = TORQUE ? sG[k] : zero2;
                 const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
                 const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
-                float2 dx = zero2, dy = zero2, dz = zero2;
+                float2 dd[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) dd[q] = zero2;
                 pair_velocity_x2<TORQUE>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
                                          make_float2(d.x, d.y), make_float2(d.z, d.w), make_float2(e.x, e.y),
-                                         make_float2(e.z, e.w), g, c, dx, dy, dz);
-                if (k == pp) {
-                    if (hh == 0) {
-                        dx.x = 0.f;
-                        dy.x = 0.f;
-                        dz.x = 0.f;
-                    } else {
-                        dx.y = 0.f;
-                        dy.y = 0.f;
-                        dz.y = 0.f;
+                                         make_float2(e.z, e.w), g, c, dd[0], dd[1], dd[2]);
+                if (RHS2) {
+                    const float4 pv = sP[k];
+                    pair_velocity_x2<false>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(pv.x, pv.y),
+                                            make_float2(pv.z, pv.w), sQ[k], zero2, zero2, zero2, c, dd[3 % NC],
+                                            dd[4 % NC], dd[5 % NC]);
+                }
+                if (k == pp) {  // source 2k + hh is this thread's own sphere
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) {
+                        if (hh == 0)
+                            dd[q].x = 0.f;
+                        else
+                            dd[q].y = 0.f;
                     }
                 }
-                ux = add2(ux, dx);
-                uy = add2(uy, dy);
-                uz = add2(uz, dz);
+#pragma unroll
+                for (int q = 0; q < NC; ++q) u[q] = add2(u[q], dd[q]);
             }
         } else {
             for (int k = 0; k < P; k += 2) {
-                float2 v[2][3];
+                float2 v[2][NC];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float4 a = sA[k + h], cc = sC[k + h], d = sD[k + h];
                     const float4 e = TORQUE ? sE[k + h] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float2 g = TORQUE ? sG[k + h] : zero2;
+                    const float4 pv = RHS2 ? sP[k + h] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float2 pz = RHS2 ? sQ[k + h] : zero2;
                     const float2 zj = make_float2(cc.x, cc.y);
                     float2 rx, ry, rz, rho2, r2;
                     const bool close =
                         pair_offsets_x2(txh, tyh, txl, tyl, tz2, zj, a, &sB[k + h], c, rx, ry, rz, rho2, r2);
-                    pair_sym_x2<TORQUE>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
-                                        make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
-                                        make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c, ux, uy, uz,
-                                        v[h][0], v[h][1], v[h][2]);
+                    pair_sym_x2<TORQUE, RHS2>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
+                                              make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
+                                              make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c, u[0],
+                                              u[1], u[2], v[h][0], v[h][1], v[h][2], make_float2(pv.x, pv.y),
+                                              make_float2(pv.z, pv.w), pz, Qx, Qy, Qz, RHS2 ? &u[3 % NC] : nullptr,
+                                              RHS2 ? &v[h][3 % NC] : nullptr);
                 }
                 // reduce-scatter of the four sources 2k .. 2k+3 over the warp: lane L ends with the
                 // sum for source 2k + 2 bit4(L) + bit3(L); lanes 0, 8, 16, 24 store it
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
+                for (int q = 0; q < NC; ++q) {
                     const float2 keep = bit4 ? v[1][q] : v[0][q];
                     const float2 send = bit4 ? v[0][q] : v[1][q];
                     const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 16),
@@ -420,63 +460,59 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 }
             }
         }
-        {
-            const float tx = ux.x + ux.y, ty = uy.x + uy.y, tzs = uz.x + uz.y;
-            float yv = tx - cx, tv = sx + yv;
-            cx = (tv - sx) - yv;
-            sx = tv;
-            yv = ty - cy;
-            tv = sy + yv;
-            cy = (tv - sy) - yv;
-            sy = tv;
-            yv = tzs - cz;
-            tv = sz + yv;
-            cz = (tv - sz) - yv;
-            sz = tv;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            const float yv = (u[q].x + u[q].y) - kc[q];
+            const float tv = ks[q] + yv;
+            kc[q] = (tv - ks[q]) - yv;
+            ks[q] = tv;
         }
         __syncthreads();
         if (t != seg.b) {
-            float *o = src_part + (size_t)(col_start[t] + seg.b) * 3 * kTile;
+            float *o = src_part + (size_t)(col_start[t] + seg.b) * NC * kTile;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) o[q * kTile + tid] = (sv[0][q][tid] + sv[1][q][tid]) + (sv[2][q][tid] + sv[3][q][tid]);
+            for (int q = 0; q < NC; ++q) o[q * kTile + tid] = (sv[0][q][tid] + sv[1][q][tid]) + (sv[2][q][tid] + sv[3][q][tid]);
         }
         __syncthreads();
     }
-    double *o = tgt_part + (size_t)sg * 3 * kTile;
-    o[tid] = (double)sx - (double)cx;
-    o[kTile + tid] = (double)sy - (double)cy;
-    o[2 * kTile + tid] = (double)sz - (double)cz;
+    double *o = tgt_part + (size_t)sg * NC * kTile;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) o[q * kTile + tid] = (double)ks[q] - (double)kc[q];
     }
 }
 
 // Row partials of the targets plus column partials of the sources, fixed order; float64 self term
-// (with the torque's wall self coupling when T is given); s_i / (8 pi eta).
+// (with the torque's wall self coupling when T is given); s_i / (8 pi eta).  NC = 6: the partials also
+// carry a second translation-translation right-hand side P, written to U2 with its own self term.
+template <int NC>
 __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
                                        const int *__restrict__ row_seg, const int *__restrict__ col_start, int N,
                                        const double *__restrict__ pos, const double *__restrict__ F,
                                        const double *__restrict__ T, PairConsts<double> c, double a, double scale,
-                                       double *__restrict__ U)
+                                       double *__restrict__ U, const double *__restrict__ P = nullptr,
+                                       double *__restrict__ U2 = nullptr)
 {
-    // one CTA of 2 x 384 threads per 128-sphere tile, the longest columns first; thread (half, q, l):
-    // component q of sphere l, rows of its column with parity `half`
-    __shared__ double s[3][kTile];
-    __shared__ double s1[3][kTile];
+    // one CTA of 768 threads per 128-sphere tile, the longest columns first; thread (half, q, l):
+    // component q of sphere l, rows of its column congruent to `half` modulo HALVES
+    constexpr int HALVES = 6 / NC;
+    __shared__ double s[NC][kTile];
+    __shared__ double s1[NC][kTile];
     const int nb = gridDim.x;
     const int b = nb - 1 - (int)blockIdx.x;
-    const int half = threadIdx.x / (3 * kTile);
-    const int r = threadIdx.x - half * 3 * kTile;
+    const int half = threadIdx.x / (NC * kTile);
+    const int r = threadIdx.x - half * NC * kTile;
     const int q = r / kTile, l = r - q * kTile;
     // column of float32 partials: four independent compensated float32 sums per thread (GB300's
     // float64 rate would make a float64 add per partial the bottleneck; one chain per thread would
     // leave the column latency-bound), converted once and added in a fixed order
-    const float *col = src_part + (size_t)col_start[b] * 3 * kTile + q * kTile + l;
+    const float *col = src_part + (size_t)col_start[b] * NC * kTile + q * kTile + l;
     float cs[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int bb = half; bb < b; bb += 8) {
+    for (int bb = half; bb < b; bb += 4 * HALVES) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int row = bb + 2 * u;
+            const int row = bb + HALVES * u;
             if (row < b) {
-                const float yv = col[(size_t)row * 3 * kTile] - cc[u];
+                const float yv = col[(size_t)row * NC * kTile] - cc[u];
                 const float tv = cs[u] + yv;
                 cc[u] = (tv - cs[u]) - yv;
                 cs[u] = tv;
@@ -486,31 +522,42 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
     double v = 0.0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) v += (double)cs[u] - (double)cc[u];
-    if (half == 1) s1[q][l] = v;
+    if (HALVES == 2 && half == 1) s1[q][l] = v;
     __syncthreads();
     if (half == 0) {
         double acc = 0.0;
-        for (int k = row_seg[b]; k < row_seg[b + 1]; ++k) acc += tgt_part[((size_t)k * 3 + q) * kTile + l];
-        s[q][l] = acc + (v + s1[q][l]);
+        for (int k = row_seg[b]; k < row_seg[b + 1]; ++k) acc += tgt_part[((size_t)k * NC + q) * kTile + l];
+        s[q][l] = acc + (HALVES == 2 ? v + s1[q][l] : v);
     }
     __syncthreads();
     const int i = b * kTile + l;
-    if (half != 0 || q != 0 || i >= N) return;
-    double ux = s[0][l], uy = s[1][l], uz = s[2][l];
+    if (half != 0 || i >= N || (q != 0 && q != 3)) return;
     const double z = pos[2 * N + i];
     const double si = H0(z / a);
     const double zc = fmax(z, a);
-    if (T)
-        pair_velocity<double, true>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], si * T[i],
-                                    si * T[N + i], si * T[2 * N + i], c, ux, uy, uz);
-    else
-        pair_velocity<double, false>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], 0.0, 0.0, 0.0, c,
-                                     ux, uy, uz);
     const double k = si * scale;
-    U[i] = k * ux;
-    U[N + i] = k * uy;
-    U[2 * N + i] = k * uz;
+    if (q == 0) {
+        double ux = s[0][l], uy = s[1][l], uz = s[2][l];
+        if (T)
+            pair_velocity<double, true>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], si * T[i],
+                                        si * T[N + i], si * T[2 * N + i], c, ux, uy, uz);
+        else
+            pair_velocity<double, false>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], 0.0, 0.0,
+                                         0.0, c, ux, uy, uz);
+        U[i] = k * ux;
+        U[N + i] = k * uy;
+        U[2 * N + i] = k * uz;
+    } else if (NC == 6) {
+        double ux = s[3 % NC][l], uy = s[4 % NC][l], uz = s[5 % NC][l];
+        pair_velocity<double, false>(0.0, 0.0, zc, zc, si * P[i], si * P[N + i], si * P[2 * N + i], 0.0, 0.0, 0.0,
+                                     c, ux, uy, uz);
+        U2[i] = k * ux;
+        U2[N + i] = k * uy;
+        U2[2 * N + i] = k * uz;
+    }
 }
+
+constexpr int kRhs2MinBlocks = 4;  // resident CTAs per SM of the two-right-hand-side form
 
 // Upper-triangle schedule for N targets: the nb (nb + 1) / 2 units (b, t >= b) in row-major order
 // cut into ncta runs of equal length, each run split into segments at row ends.  ncta = 30 x SMs
@@ -581,37 +628,47 @@ size_t sym_index_ints(int64_t max_N, int num_sms)
 }
 
 // Symmetric translation-translation product (float32 pairs); requires ctx->ws.sym_* scratch.
+// Schedule of the symmetric pass for N (built and copied to the device when N changes).
+static int sym_prepare(rpb_ctx *ctx, int N)
+{
+    Workspace &w = ctx->ws;
+    if (w.sym_N == N) return RPB_OK;
+    cudaStream_t st = ctx->stream;
+    std::vector<int> cta4, seg4, row_seg, col_start;
+    sym_schedule(N, ctx->num_sms, cta4, seg4, row_seg, col_start);
+    const size_t need = cta4.size() + seg4.size() + row_seg.size() + col_start.size();
+    if (need > w.sym_index_ints || seg4.size() / 4 * 3 * kTile * sizeof(double) > w.sym_tgt_bytes) {
+        set_error("internal: symmetric schedule larger than its scratch (N=%d)", N);
+        return RPB_EINVAL;
+    }
+    std::vector<int> host(need);
+    size_t o = 0;
+    for (const std::vector<int> *v : {&cta4, &seg4, &row_seg, &col_start}) {
+        std::copy(v->begin(), v->end(), host.begin() + o);
+        o += v->size();
+    }
+    int rc;
+    if ((rc = cuda_fail(cudaMemcpyAsync(w.sym_index, host.data(), need * sizeof(int), cudaMemcpyHostToDevice, st),
+                        "symmetric schedule copy")))
+        return rc;
+    if ((rc = cuda_fail(cudaStreamSynchronize(st), "symmetric schedule copy"))) return rc;
+    w.sym_N = N;
+    w.sym_ncta = (int)(cta4.size() / 4);
+    w.sym_nseg = (int)(seg4.size() / 4);
+    w.sym_seg_off = (int)cta4.size();
+    w.sym_row_off = (int)(cta4.size() + seg4.size());
+    w.sym_col_off = (int)(cta4.size() + seg4.size() + row_seg.size());
+    return RPB_OK;
+}
+
 // Symmetric product (float32 pairs), translation-translation or, with T, the fused product;
 // requires ctx->ws.sym_* scratch.
 static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F, const double *T, double *U)
 {
     cudaStream_t st = ctx->stream;
     Workspace &w = ctx->ws;
-    if (w.sym_N != N) {
-        std::vector<int> cta4, seg4, row_seg, col_start;
-        sym_schedule(N, ctx->num_sms, cta4, seg4, row_seg, col_start);
-        const size_t need = cta4.size() + seg4.size() + row_seg.size() + col_start.size();
-        if (need > w.sym_index_ints || seg4.size() / 4 * 3 * kTile * sizeof(double) > w.sym_tgt_bytes) {
-            set_error("internal: symmetric schedule larger than its scratch (N=%d)", N);
-            return RPB_EINVAL;
-        }
-        std::vector<int> host(need);
-        size_t o = 0;
-        for (const std::vector<int> *v : {&cta4, &seg4, &row_seg, &col_start}) {
-            std::copy(v->begin(), v->end(), host.begin() + o);
-            o += v->size();
-        }
-        int rc;
-        if ((rc = cuda_fail(cudaMemcpyAsync(w.sym_index, host.data(), need * sizeof(int), cudaMemcpyHostToDevice, st),
-                            "symmetric schedule copy")))
-            return rc;
-        if ((rc = cuda_fail(cudaStreamSynchronize(st), "symmetric schedule copy"))) return rc;
-        w.sym_N = N;
-        w.sym_ncta = (int)(cta4.size() / 4);
-        w.sym_seg_off = (int)cta4.size();
-        w.sym_row_off = (int)(cta4.size() + seg4.size());
-        w.sym_col_off = (int)(cta4.size() + seg4.size() + row_seg.size());
-    }
+    int rc;
+    if ((rc = sym_prepare(ctx, N))) return rc;
     const double a = ctx->p.a;
     SrcF32 *src = (SrcF32 *)w.src;
     const int pb = 256;
@@ -635,11 +692,47 @@ static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F,
             pair_f32x2_sym_kernel<6, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
                                                                                  w.sym_src);
     }
-    pair_sym_reduce_kernel<<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
+    pair_sym_reduce_kernel<3><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
                                                              cs, N, pos, F, T, make_consts<double>(a), a,
                                                              1.0 / (8.0 * kPi * ctx->p.eta), U);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "symmetric pair kernels");
+}
+
+bool mobility_apply2_ok(const rpb_ctx *ctx, int64_t N)
+{
+    return ctx->sym_rhs2 && ctx->sym_enabled && ctx->p.wall && !(ctx->Lx > 0.0) && N >= 2 * kTile;
+}
+
+int mobility_apply2_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T,
+                         const double *P, double *U, double *U2)
+{
+    const int N = (int)N64;
+    cudaStream_t st = ctx->stream;
+    Workspace &w = ctx->ws;
+    int rc;
+    if ((rc = sym_prepare(ctx, N))) return rc;
+    if ((size_t)w.sym_nseg * 6 * kTile * sizeof(double) > w.sym_tgt_bytes ||
+        sym_src_part_bytes(N) * 2 > w.sym_src_bytes) {
+        set_error("internal: two-right-hand-side scratch too small (N=%d)", N);
+        return RPB_EINVAL;
+    }
+    const double a = ctx->p.a;
+    SrcF32 *src = (SrcF32 *)w.src;
+    float4 *src2 = (float4 *)w.src2;
+    const int pb = 256;
+    pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, 1, src);
+    pack_rhs2_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, P, N, a, src2);
+    const SymCta *ctas = (const SymCta *)w.sym_index;
+    const SymSeg *segs = (const SymSeg *)(w.sym_index + w.sym_seg_off);
+    const int *cs = w.sym_index + w.sym_col_off;
+    pair_f32x2_sym_kernel<kRhs2MinBlocks, true, true><<<w.sym_ncta, kPairThreads, 0, st>>>(
+        src, N, ctas, segs, make_x2_consts(a), cs, w.sym_tgt, w.sym_src, src2);
+    pair_sym_reduce_kernel<6><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(
+        w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off, cs, N, pos, F, T, make_consts<double>(a), a,
+        1.0 / (8.0 * kPi * ctx->p.eta), U, P, U2);
+    count_launches(4);
+    return cuda_fail(cudaGetLastError(), "two-right-hand-side symmetric kernels");
 }
 
 template <bool TORQUE, bool WALL = true>

@@ -373,16 +373,53 @@ __device__ __forceinline__ void pair_velocity_x2_geo(float2 rx, float2 ry, float
 // v_j += M_tr(j,i) H_i.  For the reversed pair the in-plane offset and the height difference change
 // sign, the image height z_i + z_j, |R|, s, e_z and the rotlet coefficient are unchanged, and
 // t' = z~_i / |R| replaces t = z~_j / |R|.
+// Coefficients of a translation-translation pair block (packed pairs) and its two applications.
+struct TTBlock {
+    float2 rx, ry, rz, Rz, invR, invR2, c2, cF, B, C, D, E;
+};
+// target side: u += M_ij F_j
+__device__ __forceinline__ void tt_apply_target(const TTBlock &m, float2 Fx, float2 Fy, float2 Fz, float2 &ux,
+                                                float2 &uy, float2 &uz)
+{
+    const float2 pF = fma2(m.rx, Fx, mul2(m.ry, Fy));
+    const float2 q = mul2(fma2(m.Rz, Fz, pF), m.invR);
+    const float2 k2 = mul2(m.c2, fma2(m.rz, Fz, pF));
+    const float2 ke = mul2(fma2(m.B, q, mul2(m.C, Fz)), m.invR2);
+    const float2 kz = mul2(fma2(m.D, q, mul2(m.E, Fz)), m.invR);
+    const float2 kk = add2(k2, ke);
+    ux = fma2(m.cF, Fx, fma2(kk, m.rx, ux));
+    uy = fma2(m.cF, Fy, fma2(kk, m.ry, uy));
+    uz = fma2(m.cF, Fz, fma2(k2, m.rz, fma2(ke, m.Rz, add2(uz, kz))));
+}
+// source side: v = M_ij^T G_i (C and D exchanged)
+__device__ __forceinline__ void tt_apply_source(const TTBlock &m, float2 Gx, float2 Gy, float2 Gz, float2 &vx,
+                                                float2 &vy, float2 &vz)
+{
+    const float2 pF = fma2(m.rx, Gx, mul2(m.ry, Gy));
+    const float2 q = mul2(fma2(m.Rz, Gz, pF), m.invR);
+    const float2 k2 = mul2(m.c2, fma2(m.rz, Gz, pF));
+    const float2 ke = mul2(fma2(m.B, q, mul2(m.D, Gz)), m.invR2);
+    const float2 kz = mul2(fma2(m.C, q, mul2(m.E, Gz)), m.invR);
+    const float2 kk = add2(k2, ke);
+    vx = fma2(m.cF, Gx, mul2(kk, m.rx));
+    vy = fma2(m.cF, Gy, mul2(kk, m.ry));
+    vz = fma2(m.cF, Gz, fma2(k2, m.rz, fma2(ke, m.Rz, kz)));
+}
+
 // F: source loads, G: target loads; T: source torques, H: target torques.
 // The caller gives the pair geometry: in-plane offset (rx, ry), rz = zi - zj, rho2 = rx^2 + ry^2,
 // r2 = rho2 + rz^2, and `close`, true (warp-uniformly) when some lane of the warp may hold an
 // overlapping pair (r < 2a); the overlap branch is then taken per lane.
-template <bool TORQUE>
+// RHS2: a second translation-translation right-hand side applied with the same block, P (sources)
+// and Q (targets) -> u2 (target side, accumulated) and v2 (source side, returned).
+template <bool TORQUE, bool RHS2 = false>
 __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, float2 rho2, float2 r2, bool close,
                                             float2 zi, float2 zj, float2 Fx, float2 Fy, float2 Fz, float2 Gx,
                                             float2 Gy, float2 Gz, float2 Tx, float2 Ty, float2 Tz, float2 Hx,
                                             float2 Hy, float2 Hz, const X2Consts &c, float2 &ux, float2 &uy,
-                                            float2 &uz, float2 &vx, float2 &vy, float2 &vz)
+                                            float2 &uz, float2 &vx, float2 &vy, float2 &vz, float2 Px = {},
+                                            float2 Py = {}, float2 Pz = {}, float2 Qx = {}, float2 Qy = {},
+                                            float2 Qz = {}, float2 *u2 = nullptr, float2 *v2 = nullptr)
 {
     const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 inv_r2 = mul2(inv_r, inv_r);
@@ -410,29 +447,12 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, flo
     const float2 D = fma2(c.m20_3, mul2(s2, ez), add2(t, t));
     const float2 E = fma2(s2, fma2(c.c20, ez2, c.m8_3), mul2(c.m4, fma2(s, ez2, t2)));
     const float2 cF = fma2(A, invR, c1);
-    // target side: M_ij F_j
-    {
-        const float2 pF = fma2(rx, Fx, mul2(ry, Fy));
-        const float2 q = mul2(fma2(Rz, Fz, pF), invR);
-        const float2 k2 = mul2(c2, fma2(rz, Fz, pF));
-        const float2 ke = mul2(fma2(B, q, mul2(C, Fz)), invR2);
-        const float2 kz = mul2(fma2(D, q, mul2(E, Fz)), invR);
-        const float2 kk = add2(k2, ke);
-        ux = fma2(cF, Fx, fma2(kk, rx, ux));
-        uy = fma2(cF, Fy, fma2(kk, ry, uy));
-        uz = fma2(cF, Fz, fma2(k2, rz, fma2(ke, Rz, add2(uz, kz))));
-    }
-    // source side: M_ij^T F_i (C and D exchanged)
-    {
-        const float2 pF = fma2(rx, Gx, mul2(ry, Gy));
-        const float2 q = mul2(fma2(Rz, Gz, pF), invR);
-        const float2 k2 = mul2(c2, fma2(rz, Gz, pF));
-        const float2 ke = mul2(fma2(B, q, mul2(D, Gz)), invR2);
-        const float2 kz = mul2(fma2(C, q, mul2(E, Gz)), invR);
-        const float2 kk = add2(k2, ke);
-        vx = fma2(cF, Gx, mul2(kk, rx));
-        vy = fma2(cF, Gy, mul2(kk, ry));
-        vz = fma2(cF, Gz, fma2(k2, rz, fma2(ke, Rz, kz)));
+    const TTBlock m{rx, ry, rz, Rz, invR, invR2, c2, cF, B, C, D, E};
+    tt_apply_target(m, Fx, Fy, Fz, ux, uy, uz);
+    tt_apply_source(m, Gx, Gy, Gz, vx, vy, vz);
+    if (RHS2) {
+        tt_apply_target(m, Px, Py, Pz, u2[0], u2[1], u2[2]);
+        tt_apply_source(m, Qx, Qy, Qz, v2[0], v2[1], v2[2]);
     }
     if (TORQUE) {
         // the rotation coupling of pair_velocity_x2 (c_t T x r - p T x R + |R|^-2 [...]), with the

@@ -128,7 +128,9 @@ struct Workspace {
     double *sym_tgt = nullptr;
     size_t sym_tgt_bytes = 0;
     float *sym_src = nullptr;
-    int sym_N = -1, sym_ncta = 0, sym_seg_off = 0, sym_row_off = 0, sym_col_off = 0;
+    size_t sym_src_bytes = 0;
+    void *src2 = nullptr;          // second right-hand side of the two-RHS symmetric pass (float4 per sphere)
+    int sym_N = -1, sym_ncta = 0, sym_nseg = 0, sym_seg_off = 0, sym_row_off = 0, sym_col_off = 0;
 };
 
 }  // namespace rpb
@@ -144,6 +146,7 @@ struct rpb_ctx {
     int sym_enabled;   // float32 translation-translation products use the symmetric pass; env RPB_FP32_SYM=0 off
     int sym_minb;      // symmetric kernels compiled for 6 or 5 resident CTAs per SM; env RPB_SYM_MINB
     int sym_fused;     // products with torques also use the symmetric pass; env RPB_FP32_SYM_FUSED=0 off
+    int sym_rhs2;      // a step's fused product and first Lanczos product share one pass; env RPB_FP32_SYM_RHS2=0 off
     double Lx = 0.0, Ly = 0.0;  // pseudo-periodic periods (0: unbounded in-plane), rpb_set_periodic
     int f32_slots[2] = {0, 0};  // resident CTAs of the float32 one-way pair kernels (tt, with torques)
     rpb::Workspace ws;
@@ -161,6 +164,11 @@ int cuda_fail(cudaError_t e, const char *what);
 // All pointers device, SoA float64.  Enqueued on ctx->stream.
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
                         double *U);
+// Whether mobility_apply2_impl can take this product (float32 symmetric pass with two right-hand sides).
+bool mobility_apply2_ok(const rpb_ctx *ctx, int64_t N);
+// U = M_tt F + M_tr T and U2 = M_tt P in one symmetric pass (F, T, P non-null).
+int mobility_apply2_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
+                         const double *P, double *U, double *U2);
 
 // Packed source records from float64 SoA inputs (pair.cu); also used by the batched path.
 __global__ void pack_f32_kernel(const double *__restrict__ pos, const double *__restrict__ F,
@@ -182,6 +190,11 @@ int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t 
                 double *out);
 int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol, int max_iter,
                  int *iters_out, double *err_out, int *converged_out);
+// The two halves of lanczos_impl: |W| and v_0 = W/|W| into ws.V (synchronises; *nw_zero when W = 0),
+// then the iterations; with first_done the first product M v_0 is already in ws.w.
+int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero);
+int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double tol, int max_iter, bool first_done,
+                int *iters_out, double *err_out, int *converged_out);
 int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift,
              int one_sided = 0);
 int ab_update_impl(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, const double *Un, const double *g,

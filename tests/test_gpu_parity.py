@@ -466,3 +466,29 @@ def test_forces_hashed_buckets_far_apart(ctx64):
     N = len(pos)
     got = host(ctx64.forces(dev(pos), weight=1.0, U0=1.0, b=0.1), N)
     assert maxrel(got, O.forces(pos, 1.0, 1.0, 1.0, 0.1)) <= 1e-12
+
+
+def test_fp32_step_two_rhs(gpu_lib, monkeypatch):
+    """Float32 step at N = 600: the deterministic velocity and the first Lanczos product run as one
+    symmetric pass with two right-hand sides; compared with the oracle (same delta) and with the same
+    step with that pass switched off (RPB_FP32_SYM_RHS2=0, read when a context is created)."""
+    N = 600
+    pos0 = inputs.monolayer(N, seed=17)
+    Uprev = inputs.vectors(N, 18, scale=0.01)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("RPB_FP32_SYM_RHS2", flag)
+        ctx = gpu_lib.Context(max_N=N, precision="fp32", max_iter=64)
+        try:
+            q, U = dev(pos0), dev(Uprev)
+            st = ctx.step(q, U, 3, 9, dt=0.01, delta=5e-3, tol=1e-3)
+            res[flag] = (host(q, N), host(U, N), st)
+        finally:
+            ctx.close()
+    new_ref, Un_ref, info = O.ab_step(pos0, Uprev, 3, seed=9, dt=0.01, delta=5e-3, tol=1e-3)
+    for flag in ("1", "0"):
+        q, U, st = res[flag]
+        assert st["m"] == info["m"]
+        assert maxrel(U, Un_ref) <= 1e-5
+        assert maxrel(q - pos0, new_ref - pos0) <= 2e-5
+    assert maxrel(res["1"][1], res["0"][1]) <= 1e-5
