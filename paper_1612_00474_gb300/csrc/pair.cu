@@ -560,17 +560,17 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
 constexpr int kRhs2MinBlocks = 4;  // resident CTAs per SM of the two-right-hand-side form
 
 // Upper-triangle schedule for N targets: the nb (nb + 1) / 2 units (b, t >= b) in row-major order
-// cut into ncta runs of equal length, each run split into segments at row ends.  ncta = 30 x SMs
-// (when there are that many units) fills whole waves both at 5 and at 6 resident CTAs per SM, the
-// occupancies of the kernel's two forms (with and without torques).  cta4: (s0, s1, 0, 0) per CTA; seg4: (b, t0, t1, 0) per segment, in unit
-// order, so row b's segments are [row_seg[b], row_seg[b + 1]); col_start[t]: first source-partial
-// slot of column t.
+// cut into ncta runs of equal length, each run split into segments at row ends.  ncta = 60 x SMs
+// (when there are that many units) fills whole waves at 4, 5 and 6 resident CTAs per SM, the
+// occupancies of the kernel's forms (two right-hand sides, with torques, translation only).
+// cta4: (s0, s1, 0, 0) per CTA; seg4: (b, t0, t1, 0) per segment, in unit order, so row b's segments
+// are [row_seg[b], row_seg[b + 1]); col_start[t]: first source-partial slot of column t.
 void sym_schedule(int64_t N, int num_sms, std::vector<int> &cta4, std::vector<int> &seg4, std::vector<int> &row_seg,
                   std::vector<int> &col_start)
 {
     const int nb = (int)((N + kTile - 1) / kTile);
     const int64_t units = (int64_t)nb * (nb + 1) / 2;
-    int64_t ncta = std::min<int64_t>(units, 30 * (int64_t)num_sms);
+    int64_t ncta = std::min<int64_t>(units, 60 * (int64_t)num_sms);
     const int64_t L = (units + ncta - 1) / ncta;
     cta4.clear();
     seg4.clear();
@@ -606,7 +606,7 @@ void sym_schedule(int64_t N, int num_sms, std::vector<int> &cta4, std::vector<in
 }
 
 // Capacity of the schedule: at most kSymMaxCtaPerSm x SMs CTAs and that many plus nb segments.
-constexpr int kSymMaxCtaPerSm = 32;
+constexpr int kSymMaxCtaPerSm = 64;
 
 size_t sym_src_part_bytes(int64_t max_N)
 {
