@@ -129,15 +129,13 @@ __device__ __forceinline__ void lanczos_tail_warp(double *__restrict__ lz, const
         num += (y1 - p1) * (y1 - p1);
         den += p1 * p1;
     }
-    red[lane] = num;
-    __syncwarp();
-    double snum = 0.0, sden = 0.0;
-    for (int t = 0; t < 32; ++t) snum += red[t];
-    __syncwarp();
-    red[lane] = den;
-    __syncwarp();
-    for (int t = 0; t < 32; ++t) sden += red[t];
-    __syncwarp();
+    // warp sums by a butterfly (a fixed order; every lane ends with the same totals)
+    double snum = num, sden = den;
+    for (int o = 16; o > 0; o >>= 1) {
+        snum += __shfl_xor_sync(0xffffffffu, snum, o);
+        sden += __shfl_xor_sync(0xffffffffu, sden, o);
+    }
+    (void)red;
     if (lane < n) {
         lz[L.y + lane] = y0;
         lz[L.yprev + lane] = y0;
