@@ -316,7 +316,7 @@ __device__ __forceinline__ void pair_velocity_x2_geo(float2 rx, float2 ry, float
     const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 inv_r2 = mul2(inv_r, inv_r);
     const float2 ir3 = mul2(inv_r, inv_r2);
-    float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
+    float2 c1 = fma2(c.two_3_a2, ir3, inv_r);  // (1 + 2a^2/(3 r^2)) / r
     float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
     float2 ct = ir3;
     if (close) {
@@ -374,18 +374,21 @@ __device__ __forceinline__ void pair_velocity_x2_geo(float2 rx, float2 ry, float
 // sign, the image height z_i + z_j, |R|, s, e_z and the rotlet coefficient are unchanged, and
 // t' = z~_i / |R| replaces t = z~_j / |R|.
 // Coefficients of a translation-translation pair block (packed pairs) and its two applications.
+// With w = R.F = R_z F_z + r_x F_x + r_y F_y (R and r share their in-plane part) the wall terms are
+// (B w / |R|^3 + C F_z / |R|^2) R and (D w / |R|^2 + E F_z / |R|) z_hat, so the inverse powers of |R|
+// are folded into the coefficients once per pair: B3 = B/|R|^3, C2 = C/|R|^2, D2 = D/|R|^2, E1 = E/|R|.
 struct TTBlock {
-    float2 rx, ry, rz, Rz, invR, invR2, c2, cF, B, C, D, E;
+    float2 rx, ry, rz, Rz, c2, cF, B3, C2, D2, E1;
 };
 // target side: u += M_ij F_j
 __device__ __forceinline__ void tt_apply_target(const TTBlock &m, float2 Fx, float2 Fy, float2 Fz, float2 &ux,
                                                 float2 &uy, float2 &uz)
 {
     const float2 pF = fma2(m.rx, Fx, mul2(m.ry, Fy));
-    const float2 q = mul2(fma2(m.Rz, Fz, pF), m.invR);
+    const float2 w = fma2(m.Rz, Fz, pF);
     const float2 k2 = mul2(m.c2, fma2(m.rz, Fz, pF));
-    const float2 ke = mul2(fma2(m.B, q, mul2(m.C, Fz)), m.invR2);
-    const float2 kz = mul2(fma2(m.D, q, mul2(m.E, Fz)), m.invR);
+    const float2 ke = fma2(m.B3, w, mul2(m.C2, Fz));
+    const float2 kz = fma2(m.D2, w, mul2(m.E1, Fz));
     const float2 kk = add2(k2, ke);
     ux = fma2(m.cF, Fx, fma2(kk, m.rx, ux));
     uy = fma2(m.cF, Fy, fma2(kk, m.ry, uy));
@@ -396,10 +399,10 @@ __device__ __forceinline__ void tt_apply_source(const TTBlock &m, float2 Gx, flo
                                                 float2 &vy, float2 &vz)
 {
     const float2 pF = fma2(m.rx, Gx, mul2(m.ry, Gy));
-    const float2 q = mul2(fma2(m.Rz, Gz, pF), m.invR);
+    const float2 w = fma2(m.Rz, Gz, pF);
     const float2 k2 = mul2(m.c2, fma2(m.rz, Gz, pF));
-    const float2 ke = mul2(fma2(m.B, q, mul2(m.D, Gz)), m.invR2);
-    const float2 kz = mul2(fma2(m.C, q, mul2(m.E, Gz)), m.invR);
+    const float2 ke = fma2(m.B3, w, mul2(m.D2, Gz));
+    const float2 kz = fma2(m.C2, w, mul2(m.E1, Gz));
     const float2 kk = add2(k2, ke);
     vx = fma2(m.cF, Gx, mul2(kk, m.rx));
     vy = fma2(m.cF, Gy, mul2(kk, m.ry));
@@ -424,7 +427,7 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, flo
     const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 inv_r2 = mul2(inv_r, inv_r);
     const float2 ir3 = mul2(inv_r, inv_r2);
-    float2 c1 = mul2(inv_r, fma2(c.two_3_a2, inv_r2, c.one));
+    float2 c1 = fma2(c.two_3_a2, ir3, inv_r);  // (1 + 2a^2/(3 r^2)) / r
     float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
     float2 ct = ir3;
     if (close) {
@@ -447,7 +450,9 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, flo
     const float2 D = fma2(c.m20_3, mul2(s2, ez), add2(t, t));
     const float2 E = fma2(s2, fma2(c.c20, ez2, c.m8_3), mul2(c.m4, fma2(s, ez2, t2)));
     const float2 cF = fma2(A, invR, c1);
-    const TTBlock m{rx, ry, rz, Rz, invR, invR2, c2, cF, B, C, D, E};
+    const float2 invR3 = mul2(invR2, invR);
+    const float2 C2 = mul2(C, invR2);
+    const TTBlock m{rx, ry, rz, Rz, c2, cF, mul2(B, invR3), C2, mul2(D, invR2), mul2(E, invR)};
     tt_apply_target(m, Fx, Fy, Fz, ux, uy, uz);
     tt_apply_source(m, Gx, Gy, Gz, vx, vy, vz);
     if (RHS2) {
@@ -457,7 +462,7 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, flo
     if (TORQUE) {
         // the rotation coupling of pair_velocity_x2 (c_t T x r - p T x R + |R|^-2 [...]), with the
         // factors that do not depend on the direction computed once
-        const float2 p = mul2(invR2, invR);
+        const float2 p = invR3;
         const float2 dcp = sub2(ct, p);
         const float2 ctrz = mul2(ct, rz), pRz = mul2(p, Rz);
         const float2 se = mul2(s, ez);
