@@ -35,10 +35,10 @@ FLOPS_SYM = 171     # per unordered pair when the block is evaluated once and ap
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the symmetric translation-translation kernel at
 # N = 65536, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the
-# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command); 3.64 MB read (the
-# packed sources), 164.76 MB written (segment and source-column partials leaving L2).  Valid for
+# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command); 3.52 MB read (the
+# packed sources), 164.78 MB written (segment and source-column partials leaving L2).  Valid for
 # this kernel build only: reset to None when the kernel changes.
-SYM_TT_TRAFFIC_BYTES = {65536: 3.64e6 + 164.76e6}
+SYM_TT_TRAFFIC_BYTES = {65536: 3.52e6 + 164.78e6}
 SM_MAX_MHZ = 2070.0
 
 

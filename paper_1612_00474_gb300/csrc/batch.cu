@@ -808,7 +808,7 @@ static int batch_step_body(rpb_batch *bt, double dt, double delta, double tol, i
     const int ge = grid_for(n, bt->num_sms);
     int rc;
     const double a = bt->p.a;
-    const double rcut = (2.0 * a + 50.0 * fp->b) * 1.01 + 0.01 * a;
+    const double rcut = (2.0 * a + kForceCutoffB * fp->b) * 1.01 + 0.01 * a;
     batch_forces_kernel<<<bt->nblocks, 128, 0, st>>>(v[V_POS], bt->d_inst, bt->d_blocks, total, a, fp->weight, fp->U0,
                                                      fp->b, (float)(rcut * rcut), v[V_F]);
     batch_fill3_kernel<<<ge, 256, 0, st>>>(v[V_T], total, fp->torque[0], fp->torque[1], fp->torque[2]);

@@ -1411,7 +1411,7 @@ __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ 
 int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_params *fp, double *F)
 {
     const double a = ctx->p.a;
-    const double r_cut = 2.0 * a + 50.0 * fp->b;
+    const double r_cut = 2.0 * a + kForceCutoffB * fp->b;
     const double rcm = r_cut * 1.01 + 0.01 * a;
     const float cut2 = (float)(rcm * rcm);
     const int n = (int)N;

@@ -59,6 +59,10 @@ inline PairConsts<R> make_consts(double a)
     return c;
 }
 
+// Pair forces beyond 2a + kForceCutoffB b are left out: there the soft repulsion is below
+// e^{-40} U0/b ~ 4e-18 U0/b, far under the float64 rounding of any force it would be added to.
+constexpr double kForceCutoffB = 40.0;
+
 // Cell lists of the force pass (pair.cu): header, then int arrays in one allocation.
 constexpr int kCellGrid = 256;                  // at most kCellGrid x kCellGrid buckets (cells hashed modulo G)
 constexpr int kCells = kCellGrid * kCellGrid;
