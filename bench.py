@@ -30,9 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "wall-RPY matvec Gpairs/s; BD steps/s at N=65536; p50/p99 solve latency"
 FLOPS_TT = 126      # algorithmic flops per pair, translation-translation block applied to a vector
-FLOPS_FUSED = 185   # ... plus the translation-rotation block (counts derived in the design doc)
+FLOPS_FUSED = 185   # ... plus the translation-rotation block (counted from the closed form of the pair block)
 FLOPS_SYM = 171     # per unordered pair when the block is evaluated once and applied both ways (81 + 2 x 45)
 FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25  # dense FP64 rate of a GB300 (vector pipe)
 # DRAM bytes (read + write) of one launch of the symmetric translation-translation kernel at
 # N = 65536, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the
 # default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command); 3.52 MB read (the
@@ -316,7 +317,12 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0:
         sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-        peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        if args.precision == "fp32":
+            peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            peak_basis = f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
+        else:
+            peak = FP64_NOMINAL_TFLOPS
+            peak_basis = "nominal GB300 FP64 rate (no measured FP64 figure)"
         sym = (args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256
                and not args.periodic)
         if args.periodic:
@@ -348,8 +354,7 @@ def run_ours(args, rank, world, local_rank):
                        "tt_gpairs_s": images * N * N / t_tt / 1e9, "fused_gpairs_s": images * N * N / t_fused / 1e9},
             "roofline": {"bound": "alu", "kernel": kernel,
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
-                                       if args.precision == "fp32" else "fp32 lanes (fp64 path: see DESIGN.md)",
+                         "peak_basis": peak_basis,
                          "flops_per_launch": flops_tt,
                          "flops_per_pair": FLOPS_SYM / 2 if sym else FLOPS_TT,
                          "traffic": SYM_TT_TRAFFIC_BYTES.get(N) if sym else None,
