@@ -323,13 +323,15 @@ def run_ours(args, rank, world, local_rank):
         else:
             peak = FP64_NOMINAL_TFLOPS
             peak_basis = "nominal GB300 FP64 rate (no measured FP64 figure)"
-        sym = (args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256
-               and not args.periodic)
-        if args.periodic:
+        sym = args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256
+        diag = float(N) * 128
+        if args.periodic and sym:  # nine images of each unordered pair once, both ways
+            flops_tt = 9.0 * (FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag)
+            kernel = "pair_f32x2_sym_kernel, pseudo-periodic form (translation-translation, reciprocity, 9 images)"
+        elif args.periodic:
             flops_tt = 9.0 * N * N * FLOPS_TT
             kernel = f"pair_periodic_f{args.precision[2:]}_kernel<false,true> (translation-translation, 9 images)"
         elif sym:  # each unordered pair once (171 flop) except inside the 128-wide diagonal tiles (126 flop each way)
-            diag = float(N) * 128
             flops_tt = FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag
             kernel = "pair_f32x2_sym_kernel (translation-translation, reciprocity)"
         else:
@@ -357,7 +359,7 @@ def run_ours(args, rank, world, local_rank):
                          "peak_basis": peak_basis,
                          "flops_per_launch": flops_tt,
                          "flops_per_pair": FLOPS_SYM / 2 if sym else FLOPS_TT,
-                         "traffic": SYM_TT_TRAFFIC_BYTES.get(N) if sym else None,
+                         "traffic": SYM_TT_TRAFFIC_BYTES.get(N) if sym and not args.periodic else None,
                          "traffic_unit": "bytes per launch"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": "Gpairs/s", "h2d_bytes_per_step": 2 * 3 * N * 8,

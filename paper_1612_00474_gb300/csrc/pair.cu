@@ -302,9 +302,33 @@ struct SymSeg {
     int b, t0, t1, pad;
 };
 
+// Periods of the pseudo-periodic mode for the float32 kernels: L = L_hi + L_lo, and 1 / L_hi.
+struct PerLen {
+    float xh, xl, yh, yl, ix, iy;
+};
+// Minimum image of an in-plane offset (positions folded into the unit cell: |d| < L).
+__device__ __forceinline__ float min_image_f(float d, float Lh, float Ll, float inv)
+{
+    const float m = rintf(d * inv);
+    return fmaf(-m, Ll, fmaf(-m, Lh, d));
+}
+__device__ __forceinline__ float2 min_image2(float2 d, float Lh, float Ll, float inv)
+{
+    return make_float2(min_image_f(d.x, Lh, Ll, inv), min_image_f(d.y, Lh, Ll, inv));
+}
+// d + n L for the image shift n in {-1, 0, 1}
+__device__ __forceinline__ float2 shift2(float2 d, float n, float Lh, float Ll)
+{
+    return make_float2(fmaf(n, Ll, fmaf(n, Lh, d.x)), fmaf(n, Ll, fmaf(n, Lh, d.y)));
+}
+
 // RHS2: a second translation-translation right-hand side (src2: s_j P_j per sphere) evaluated with
 // the same pair blocks; components 3..5 of the partials carry it.
-template <int MINB, bool TORQUE, bool RHS2 = false>
+// PER: pseudo-periodic boundaries (Appendix B): each pair's offset is taken at its minimum image and
+// the block is summed over that image and its eight shifts by one period (reciprocity holds image by
+// image: the reversed pair's image at -s is the transposed block); the sphere's own unshifted image
+// is the self term of the reduce kernel.
+template <int MINB, bool TORQUE, bool RHS2 = false, bool PER = false>
 __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(const SrcF32 *__restrict__ src, int N,
                                                                              const SymCta *__restrict__ ctas,
                                                                              const SymSeg *__restrict__ segs,
@@ -312,10 +336,13 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                                                                              const int *__restrict__ col_start,
                                                                              double *__restrict__ tgt_part,
                                                                              float *__restrict__ src_part,
-                                                                             const float4 *__restrict__ src2 = nullptr)
+                                                                             const float4 *__restrict__ src2 = nullptr,
+                                                                             PerLen pl = PerLen{})
 {
     constexpr int P = kTile / 2;
     constexpr int NC = RHS2 ? 6 : 3;
+    constexpr int NS = PER ? 9 : 1;  // image shifts per pair
+    static_assert(!(PER && RHS2), "the two-right-hand-side form has no pseudo-periodic variant");
     __shared__ float4 sA[P], sB[P], sC[P], sD[P];
     __shared__ float4 sE[TORQUE ? P : 1];
     __shared__ float2 sG[TORQUE ? P : 1];
@@ -394,31 +421,40 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
                 const float4 e = TORQUE ? sE[k] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float2 g = TORQUE ? sG[k] : zero2;
-                const float2 rx = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
-                const float2 ry = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
-                float2 dd[NC];
-#pragma unroll
-                for (int q = 0; q < NC; ++q) dd[q] = zero2;
-                pair_velocity_x2<TORQUE>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
-                                         make_float2(d.x, d.y), make_float2(d.z, d.w), make_float2(e.x, e.y),
-                                         make_float2(e.z, e.w), g, c, dd[0], dd[1], dd[2]);
-                if (RHS2) {
-                    const float4 pv = sP[k];
-                    pair_velocity_x2<false>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(pv.x, pv.y),
-                                            make_float2(pv.z, pv.w), sQ[k], zero2, zero2, zero2, c, dd[3 % NC],
-                                            dd[4 % NC], dd[5 % NC]);
+                float2 rx0 = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
+                float2 ry0 = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
+                if (PER) {
+                    rx0 = min_image2(rx0, pl.xh, pl.xl, pl.ix);
+                    ry0 = min_image2(ry0, pl.yh, pl.yl, pl.iy);
                 }
-                if (k == pp) {  // source 2k + hh is this thread's own sphere
+                for (int sh = 0; sh < NS; ++sh) {
+                    const float2 rx = PER ? shift2(rx0, (float)(sh / 3 - 1), pl.xh, pl.xl) : rx0;
+                    const float2 ry = PER ? shift2(ry0, (float)(sh % 3 - 1), pl.yh, pl.yl) : ry0;
+                    float2 dd[NC];
 #pragma unroll
-                    for (int q = 0; q < NC; ++q) {
-                        if (hh == 0)
-                            dd[q].x = 0.f;
-                        else
-                            dd[q].y = 0.f;
+                    for (int q = 0; q < NC; ++q) dd[q] = zero2;
+                    pair_velocity_x2<TORQUE>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(cc.z, cc.w),
+                                             make_float2(d.x, d.y), make_float2(d.z, d.w), make_float2(e.x, e.y),
+                                             make_float2(e.z, e.w), g, c, dd[0], dd[1], dd[2]);
+                    if (RHS2) {
+                        const float4 pv = sP[k];
+                        pair_velocity_x2<false>(rx, ry, tz2, make_float2(cc.x, cc.y), make_float2(pv.x, pv.y),
+                                                make_float2(pv.z, pv.w), sQ[k], zero2, zero2, zero2, c, dd[3 % NC],
+                                                dd[4 % NC], dd[5 % NC]);
                     }
-                }
+                    // source 2k + hh is this thread's own sphere: its unshifted image is the self term
+                    if (k == pp && (!PER || sh == 4)) {
 #pragma unroll
-                for (int q = 0; q < NC; ++q) u[q] = add2(u[q], dd[q]);
+                        for (int q = 0; q < NC; ++q) {
+                            if (hh == 0)
+                                dd[q].x = 0.f;
+                            else
+                                dd[q].y = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) u[q] = add2(u[q], dd[q]);
+                }
             }
         } else {
             for (int k = 0; k < P; k += 2) {
@@ -431,15 +467,42 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                     const float4 pv = RHS2 ? sP[k + h] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float2 pz = RHS2 ? sQ[k + h] : zero2;
                     const float2 zj = make_float2(cc.x, cc.y);
-                    float2 rx, ry, rz, rho2, r2;
-                    const bool close =
-                        pair_offsets_x2(txh, tyh, txl, tyl, tz2, zj, a, &sB[k + h], c, rx, ry, rz, rho2, r2);
-                    pair_sym_x2<TORQUE, RHS2>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
-                                              make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
-                                              make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c, u[0],
-                                              u[1], u[2], v[h][0], v[h][1], v[h][2], make_float2(pv.x, pv.y),
-                                              make_float2(pv.z, pv.w), pz, Qx, Qy, Qz, RHS2 ? &u[3 % NC] : nullptr,
-                                              RHS2 ? &v[h][3 % NC] : nullptr);
+                    if (!PER) {
+                        float2 rx, ry, rz, rho2, r2;
+                        const bool close =
+                            pair_offsets_x2(txh, tyh, txl, tyl, tz2, zj, a, &sB[k + h], c, rx, ry, rz, rho2, r2);
+                        pair_sym_x2<TORQUE, RHS2>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
+                                                  make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
+                                                  make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c,
+                                                  u[0], u[1], u[2], v[h][0], v[h][1], v[h][2],
+                                                  make_float2(pv.x, pv.y), make_float2(pv.z, pv.w), pz, Qx, Qy, Qz,
+                                                  RHS2 ? &u[3 % NC] : nullptr, RHS2 ? &v[h][3 % NC] : nullptr);
+                    } else {
+                        // minimum image from the full offsets, then the nine images summed both ways
+                        const float4 bl = sB[k + h];
+                        const float2 rx0 = min_image2(add2(sub2(txh, make_float2(a.x, a.y)),
+                                                           sub2(txl, make_float2(bl.x, bl.y))), pl.xh, pl.xl, pl.ix);
+                        const float2 ry0 = min_image2(add2(sub2(tyh, make_float2(a.z, a.w)),
+                                                           sub2(tyl, make_float2(bl.z, bl.w))), pl.yh, pl.yl, pl.iy);
+                        const float2 rz = sub2(tz2, zj);
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) v[h][q] = zero2;
+                        for (int sh = 0; sh < 9; ++sh) {
+                            const float2 rx = shift2(rx0, (float)(sh / 3 - 1), pl.xh, pl.xl);
+                            const float2 ry = shift2(ry0, (float)(sh % 3 - 1), pl.yh, pl.yl);
+                            const float2 rho2 = fma2(rx, rx, mul2(ry, ry));
+                            const float2 r2 = fma2(rz, rz, rho2);
+                            const bool close = __any_sync(0xffffffffu, r2.x < c.four_a2 || r2.y < c.four_a2);
+                            float2 vx, vy, vz;
+                            pair_sym_x2<TORQUE>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
+                                                make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
+                                                make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c,
+                                                u[0], u[1], u[2], vx, vy, vz);
+                            v[h][0] = add2(v[h][0], vx);
+                            v[h][1] = add2(v[h][1], vy);
+                            v[h][2] = add2(v[h][2], vz);
+                        }
+                    }
                 }
                 // reduce-scatter of the four sources 2k .. 2k+3 over the warp: lane L ends with the
                 // sum for source 2k + 2 bit4(L) + bit3(L); lanes 0, 8, 16, 24 store it
@@ -558,6 +621,7 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
 }
 
 constexpr int kRhs2MinBlocks = 4;  // resident CTAs per SM of the two-right-hand-side form
+constexpr int kPerMinBlocks = 5;   // resident CTAs per SM of the pseudo-periodic forms
 
 // Upper-triangle schedule for N targets: the nb (nb + 1) / 2 units (b, t >= b) in row-major order
 // cut into ncta runs of equal length, each run split into segments at row ends.  ncta = 60 x SMs
@@ -697,6 +761,43 @@ static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F,
                                                              1.0 / (8.0 * kPi * ctx->p.eta), U);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "symmetric pair kernels");
+}
+
+// The symmetric product in pseudo-periodic mode: positions already folded into the unit cell
+// (pos_w; the self terms use the heights of pos, which the fold leaves unchanged).
+static int mobility_sym_periodic(rpb_ctx *ctx, int N, const double *pos_w, const double *pos, const double *F,
+                                 const double *T, double *U)
+{
+    cudaStream_t st = ctx->stream;
+    Workspace &w = ctx->ws;
+    int rc;
+    if ((rc = sym_prepare(ctx, N))) return rc;
+    const double a = ctx->p.a;
+    SrcF32 *src = (SrcF32 *)w.src;
+    const int pb = 256;
+    pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos_w, F, T, N, a, 1, src);
+    const SymCta *ctas = (const SymCta *)w.sym_index;
+    const SymSeg *segs = (const SymSeg *)(w.sym_index + w.sym_seg_off);
+    const X2Consts c = make_x2_consts(a);
+    const int *cs = w.sym_index + w.sym_col_off;
+    PerLen pl;
+    pl.xh = (float)ctx->Lx;
+    pl.xl = (float)(ctx->Lx - (double)pl.xh);
+    pl.yh = (float)ctx->Ly;
+    pl.yl = (float)(ctx->Ly - (double)pl.yh);
+    pl.ix = 1.f / pl.xh;
+    pl.iy = 1.f / pl.yh;
+    if (T)
+        pair_f32x2_sym_kernel<kPerMinBlocks, true, false, true><<<w.sym_ncta, kPairThreads, 0, st>>>(
+            src, N, ctas, segs, c, cs, w.sym_tgt, w.sym_src, nullptr, pl);
+    else
+        pair_f32x2_sym_kernel<kPerMinBlocks, false, false, true><<<w.sym_ncta, kPairThreads, 0, st>>>(
+            src, N, ctas, segs, c, cs, w.sym_tgt, w.sym_src, nullptr, pl);
+    pair_sym_reduce_kernel<3><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
+                                                             cs, N, pos, F, T, make_consts<double>(a), a,
+                                                             1.0 / (8.0 * kPi * ctx->p.eta), U);
+    count_launches(3);
+    return cuda_fail(cudaGetLastError(), "periodic symmetric pair kernels");
 }
 
 bool mobility_apply2_ok(const rpb_ctx *ctx, int64_t N)
@@ -1047,6 +1148,11 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
         const double Lx = ctx->Lx, Ly = ctx->Ly;
         wrap_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, N, Lx, Ly, ctx->ws.pos_w);
         const double *pw = ctx->ws.pos_w;
+        if (ctx->p.precision == RPB_FP32 && ctx->sym_enabled && ctx->p.wall && F && N >= 2 * kTile &&
+            (!T || ctx->sym_fused)) {
+            count_launches(1);
+            return mobility_sym_periodic(ctx, N, pw, pos, F, T, U);
+        }
         if (ctx->p.precision == RPB_FP32) {
             SrcF32 *src = (SrcF32 *)ctx->ws.src;
             pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pw, F, T, N, a, ctx->p.wall, src);
