@@ -15,6 +15,7 @@
 //                   same numbers the single-suspension path draws for that seed and step.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -592,6 +593,11 @@ struct rpb_batch {
     cudaEvent_t join = nullptr;
     unsigned long long *d_unconv = nullptr;
     unsigned long long *h_unconv = nullptr;
+    // float32 products by the symmetric pass (both directions of a pair from one evaluation):
+    // schedule and partial-sum scratch for the current batch sizes
+    bool sym_enabled = false;
+    bool sym_ok = false;
+    BatchSymPlan sym;
 };
 
 namespace rpb {
@@ -610,6 +616,7 @@ static void batch_free(rpb_batch *bt)
     for (void *p : host)
         if (p) cudaFreeHost(p);
     if (bt->d_unconv) cudaFree(bt->d_unconv);
+    batch_sym_free(bt->sym);
     if (bt->join) cudaEventDestroy(bt->join);
     if (bt->cap) cudaStreamDestroy(bt->cap);
 }
@@ -681,7 +688,10 @@ static int batch_setup(rpb_batch *bt, int B, const int64_t *N, const int64_t *st
         return rc;
     inst_of_kernel<<<B, 256, 0, bt->stream>>>(bt->d_inst, B, bt->d_inst_of);
     count_launches(1);
-    return cuda_fail(cudaGetLastError(), "inst_of");
+    if ((rc = cuda_fail(cudaGetLastError(), "inst_of"))) return rc;
+    bt->sym_ok = false;
+    if (bt->sym_enabled && (rc = batch_sym_plan(bt->sym, B, N, bt->stream, &bt->sym_ok))) return rc;
+    return RPB_OK;
 }
 
 static int batch_gather(rpb_batch *bt, int which, double *packed, int to_caller)
@@ -701,7 +711,12 @@ static int batch_product(rpb_batch *bt, const double *pos, const double *F, cons
     const double scale = 1.0 / (8.0 * kPi * bt->p.eta);
     const int pb = 256;
     const int gpack = (int)((total + pb - 1) / pb);
-    if (bt->p.precision == RPB_FP32) {
+    if (bt->p.precision == RPB_FP32 && bt->sym_ok) {
+        SrcF32 *src = (SrcF32 *)bt->src;
+        pack_f32_kernel<<<gpack, pb, 0, bt->stream>>>(pos, F, T, (int)total, a, 1, src);
+        count_launches(1);
+        return batch_sym_apply(bt->sym, bt->stream, src, total, pos, F, T, U, active, a, bt->p.eta);
+    } else if (bt->p.precision == RPB_FP32) {
         SrcF32 *src = (SrcF32 *)bt->src;
         pack_f32_kernel<<<gpack, pb, 0, bt->stream>>>(pos, F, T, (int)total, a, 1, src);
         const X2Consts c = make_x2_consts(a);
@@ -937,6 +952,11 @@ int rpb_batch_create(rpb_batch **out, const rpb_params *p, int64_t max_total_N, 
     bt->max_B = max_B;
     bt->max_iter = max_iter;
     bt->stream = (cudaStream_t)stream;
+    {
+        // RPB_FP32_BATCH_SYM=0: float32 products by the one-way kernel instead of the symmetric pass
+        const char *v = getenv("RPB_FP32_BATCH_SYM");
+        bt->sym_enabled = p->precision == RPB_FP32 && !(v && strcmp(v, "0") == 0);
+    }
     int dev = 0;
     if (cuda_fail(cudaGetDevice(&dev), "cudaGetDevice") ||
         cuda_fail(cudaDeviceGetAttribute(&bt->num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count")) {

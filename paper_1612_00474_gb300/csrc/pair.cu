@@ -328,7 +328,10 @@ __device__ __forceinline__ float2 shift2(float2 d, float n, float Lh, float Ll)
 // the block is summed over that image and its eight shifts by one period (reciprocity holds image by
 // image: the reversed pair's image at -s is the transposed block); the sphere's own unshifted image
 // is the self term of the reduce kernel.
-template <int MINB, bool TORQUE, bool RHS2 = false, bool PER = false>
+// BATCH: the tiles belong to many suspensions packed one after another (sinst: one record per
+// suspension; a segment's pad field names its suspension, whose tiles are numbered from tile0);
+// segments of suspensions with active[] == 0 are skipped.
+template <int MINB, bool TORQUE, bool RHS2 = false, bool PER = false, bool BATCH = false>
 __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(const SrcF32 *__restrict__ src, int N,
                                                                              const SymCta *__restrict__ ctas,
                                                                              const SymSeg *__restrict__ segs,
@@ -337,12 +340,15 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                                                                              double *__restrict__ tgt_part,
                                                                              float *__restrict__ src_part,
                                                                              const float4 *__restrict__ src2 = nullptr,
-                                                                             PerLen pl = PerLen{})
+                                                                             PerLen pl = PerLen{},
+                                                                             const SymInst *__restrict__ sinst = nullptr,
+                                                                             const int *__restrict__ active = nullptr)
 {
     constexpr int P = kTile / 2;
     constexpr int NC = RHS2 ? 6 : 3;
     constexpr int NS = PER ? 9 : 1;  // image shifts per pair
     static_assert(!(PER && RHS2), "the two-right-hand-side form has no pseudo-periodic variant");
+    static_assert(!(BATCH && (PER || RHS2)), "the batched form is the plain or the torque form");
     __shared__ float4 sA[P], sB[P], sC[P], sD[P];
     __shared__ float4 sE[TORQUE ? P : 1];
     __shared__ float2 sG[TORQUE ? P : 1];
@@ -364,12 +370,22 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     float *fQ = reinterpret_cast<float *>(sQ);
     for (int sg = cd.s0; sg < cd.s1; ++sg) {
     const SymSeg seg = segs[sg];
-    const int i = seg.b * kTile + tid;
+    long long off = 0;
+    int Ni = N, tb = 0;
+    if (BATCH) {
+        if (active && !active[seg.pad]) continue;  // the same for the whole CTA
+        const SymInst si = sinst[seg.pad];
+        off = si.off;
+        Ni = si.N;
+        tb = si.tile0;
+    }
+    const int li = (seg.b - tb) * kTile + tid;
+    const long long i = off + li;
     float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 tf = make_float4(1.f, 0.f, 0.f, 0.f);
     float4 th = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < N) {
+    if (li < Ni) {
         tp = src[i].p;
         tf = src[i].f;
         if (TORQUE) th = src[i].t;
@@ -385,10 +401,11 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
 #pragma unroll
     for (int q = 0; q < NC; ++q) ks[q] = kc[q] = 0.f;
     for (int t = seg.t0; t < seg.t1; ++t) {
-        const int j = t * kTile + tid;
+        const int lj = (t - tb) * kTile + tid;
+        const long long j = off + lj;
         float4 sp_ = make_float4(1e18f, 0.f, 0.f, 0.f), sf_ = make_float4(1.f, 0.f, 0.f, 0.f);
         float4 st_ = make_float4(0.f, 0.f, 0.f, 0.f), sq_ = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < N) {
+        if (lj < Ni) {
             sp_ = src[j].p;
             sf_ = src[j].f;
             if (TORQUE) st_ = src[j].t;
@@ -547,13 +564,19 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
 // Row partials of the targets plus column partials of the sources, fixed order; float64 self term
 // (with the torque's wall self coupling when T is given); s_i / (8 pi eta).  NC = 6: the partials also
 // carry a second translation-translation right-hand side P, written to U2 with its own self term.
-template <int NC>
+// BATCH: tiles of many suspensions (tile_inst: the suspension of each tile; sinst as in the pair
+// kernel); the column of tile b holds the rows tile0 .. b - 1 of its suspension, summed in an order
+// relative to tile0 so that a suspension's result does not depend on its companions.
+template <int NC, bool BATCH = false>
 __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
                                        const int *__restrict__ row_seg, const int *__restrict__ col_start, int N,
                                        const double *__restrict__ pos, const double *__restrict__ F,
                                        const double *__restrict__ T, PairConsts<double> c, double a, double scale,
                                        double *__restrict__ U, const double *__restrict__ P = nullptr,
-                                       double *__restrict__ U2 = nullptr)
+                                       double *__restrict__ U2 = nullptr,
+                                       const SymInst *__restrict__ sinst = nullptr,
+                                       const int *__restrict__ tile_inst = nullptr,
+                                       const int *__restrict__ active = nullptr)
 {
     // one CTA of 768 threads per 128-sphere tile, the longest columns first; thread (half, q, l):
     // component q of sphere l, rows of its column congruent to `half` modulo HALVES
@@ -561,7 +584,17 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
     __shared__ double s[NC][kTile];
     __shared__ double s1[NC][kTile];
     const int nb = gridDim.x;
-    const int b = nb - 1 - (int)blockIdx.x;
+    const int b = BATCH ? (int)blockIdx.x : nb - 1 - (int)blockIdx.x;
+    long long off = 0;
+    int Ni = N, tb = 0;
+    if (BATCH) {
+        const int inst = tile_inst[b];
+        if (active && !active[inst]) return;  // the same for the whole CTA
+        const SymInst si = sinst[inst];
+        off = si.off;
+        Ni = si.N;
+        tb = si.tile0;
+    }
     const int half = threadIdx.x / (NC * kTile);
     const int r = threadIdx.x - half * NC * kTile;
     const int q = r / kTile, l = r - q * kTile;
@@ -570,7 +603,7 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
     // leave the column latency-bound), converted once and added in a fixed order
     const float *col = src_part + (size_t)col_start[b] * NC * kTile + q * kTile + l;
     float cs[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int bb = half; bb < b; bb += 4 * HALVES) {
+    for (int bb = tb + half; bb < b; bb += 4 * HALVES) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int row = bb + HALVES * u;
@@ -593,8 +626,9 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
         s[q][l] = acc + (HALVES == 2 ? v + s1[q][l] : v);
     }
     __syncthreads();
-    const int i = b * kTile + l;
-    if (half != 0 || i >= N || (q != 0 && q != 3)) return;
+    const int lb = (b - tb) * kTile + l;
+    if (half != 0 || lb >= Ni || (q != 0 && q != 3)) return;
+    const long long i = off + lb;
     const double z = pos[2 * N + i];
     const double si = H0(z / a);
     const double zc = fmax(z, a);
@@ -798,6 +832,144 @@ static int mobility_sym_periodic(rpb_ctx *ctx, int N, const double *pos_w, const
                                                              1.0 / (8.0 * kPi * ctx->p.eta), U);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "periodic symmetric pair kernels");
+}
+
+// ------------------------------------------------------------------ batched symmetric pass
+// Each suspension's rows of tiles are cut by a fixed rule (runs of at most kBatchSegTiles tiles), so
+// that the partial sums a suspension's result is made of do not depend on the other suspensions; one
+// CTA per run, longest runs first.
+constexpr int kBatchSegTiles = 8;
+constexpr size_t kBatchSymScratchLimit = (size_t)4 << 30;
+
+void batch_sym_free(BatchSymPlan &pl)
+{
+    void *d[] = {pl.index, pl.sinst, pl.tgt, pl.srcp};
+    for (void *x : d)
+        if (x) cudaFree(x);
+    pl = BatchSymPlan();
+}
+
+static int grow(void **ptr, size_t *cap, size_t need, const char *what)
+{
+    if (need <= *cap) return RPB_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMalloc(ptr, need) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        set_error("cudaMalloc of %zu bytes (%s) failed", need, what);
+        return RPB_ENOMEM;
+    }
+    *cap = need;
+    return RPB_OK;
+}
+
+int batch_sym_plan(BatchSymPlan &pl, int B, const int64_t *N, cudaStream_t st, bool *ok)
+{
+    *ok = false;
+    std::vector<int64_t> sizes(N, N + B);
+    if (pl.valid && sizes == pl.sizes) {
+        *ok = true;
+        return RPB_OK;
+    }
+    pl.valid = false;
+    std::vector<SymInst> si(B);
+    std::vector<int> seg4, row_seg, col_start, tile_inst;
+    int64_t off = 0, srows = 0;
+    int g = 0;
+    for (int k = 0; k < B; ++k) {
+        const int nb = (int)((N[k] + kTile - 1) / kTile);
+        si[k].off = off;
+        si[k].N = (int)N[k];
+        si[k].tile0 = g;
+        for (int r = 0; r < nb; ++r) {
+            row_seg.push_back((int)(seg4.size() / 4));
+            tile_inst.push_back(k);
+            for (int t0 = g + r; t0 < g + nb; t0 += kBatchSegTiles) {
+                seg4.push_back(g + r);
+                seg4.push_back(t0);
+                seg4.push_back(std::min(g + nb, t0 + kBatchSegTiles));
+                seg4.push_back(k);
+            }
+            col_start.push_back((int)(srows - g));  // slot of row b in column g + r: col_start + b
+            srows += r;
+        }
+        off += N[k];
+        g += nb;
+    }
+    const int nseg = (int)(seg4.size() / 4);
+    row_seg.push_back(nseg);
+    const size_t src_bytes = (size_t)srows * 3 * kTile * sizeof(float);
+    const size_t tgt_bytes = (size_t)nseg * 3 * kTile * sizeof(double);
+    if (src_bytes + tgt_bytes > kBatchSymScratchLimit) return RPB_OK;  // one-way kernels instead
+    std::vector<int> order(nseg);
+    for (int q = 0; q < nseg; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return seg4[4 * x + 2] - seg4[4 * x + 1] > seg4[4 * y + 2] - seg4[4 * y + 1]; });
+    std::vector<int> host;
+    host.reserve(4 * nseg + seg4.size() + row_seg.size() + col_start.size() + tile_inst.size());
+    for (int q : order) {
+        host.push_back(q);
+        host.push_back(q + 1);
+        host.push_back(0);
+        host.push_back(0);
+    }
+    const int seg_off = (int)host.size();
+    host.insert(host.end(), seg4.begin(), seg4.end());
+    const int row_off = (int)host.size();
+    host.insert(host.end(), row_seg.begin(), row_seg.end());
+    const int col_off = (int)host.size();
+    host.insert(host.end(), col_start.begin(), col_start.end());
+    const int inst_off = (int)host.size();
+    host.insert(host.end(), tile_inst.begin(), tile_inst.end());
+    int rc;
+    size_t icap = pl.index_cap * sizeof(int), scap = (size_t)pl.sinst_cap * sizeof(SymInst);
+    if ((rc = grow((void **)&pl.index, &icap, host.size() * sizeof(int), "batched symmetric schedule")) ||
+        (rc = grow((void **)&pl.sinst, &scap, (size_t)B * sizeof(SymInst), "batched symmetric instances")) ||
+        (rc = grow((void **)&pl.tgt, &pl.tgt_cap, tgt_bytes, "batched symmetric partials")) ||
+        (rc = grow((void **)&pl.srcp, &pl.src_cap, std::max<size_t>(src_bytes, 16), "batched symmetric partials")))
+        return rc;
+    pl.index_cap = icap / sizeof(int);
+    pl.sinst_cap = (int)(scap / sizeof(SymInst));
+    if ((rc = cuda_fail(cudaMemcpyAsync(pl.index, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice, st),
+                        "batched symmetric schedule copy")) ||
+        (rc = cuda_fail(cudaMemcpyAsync(pl.sinst, si.data(), (size_t)B * sizeof(SymInst), cudaMemcpyHostToDevice, st),
+                        "batched symmetric instances copy")) ||
+        (rc = cuda_fail(cudaStreamSynchronize(st), "batched symmetric plan")))
+        return rc;
+    pl.ncta = nseg;
+    pl.nseg = nseg;
+    pl.ntiles = g;
+    pl.seg_off = seg_off;
+    pl.row_off = row_off;
+    pl.col_off = col_off;
+    pl.inst_off = inst_off;
+    pl.sizes = sizes;
+    pl.valid = true;
+    *ok = true;
+    return RPB_OK;
+}
+
+int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, int64_t total, const double *pos,
+                    const double *F, const double *T, double *U, const int *active, double a, double eta)
+{
+    const SymCta *ctas = (const SymCta *)pl.index;
+    const SymSeg *segs = (const SymSeg *)(pl.index + pl.seg_off);
+    const int *cs = pl.index + pl.col_off;
+    const X2Consts c = make_x2_consts(a);
+    const int n = (int)total;
+    if (T)
+        pair_f32x2_sym_kernel<5, true, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
+            src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
+    else
+        pair_f32x2_sym_kernel<6, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
+            src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
+    pair_sym_reduce_kernel<3, true><<<pl.ntiles, 6 * kTile, 0, st>>>(
+        pl.tgt, pl.srcp, pl.index + pl.row_off, cs, n, pos, F, T, make_consts<double>(a), a, 1.0 / (8.0 * kPi * eta),
+        U, nullptr, nullptr, pl.sinst, pl.index + pl.inst_off, active);
+    count_launches(2);
+    return cuda_fail(cudaGetLastError(), "batched symmetric kernels");
 }
 
 bool mobility_apply2_ok(const rpb_ctx *ctx, int64_t N)

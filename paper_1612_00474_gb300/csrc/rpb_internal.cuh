@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/rpb.h"
 
 namespace rpb {
@@ -104,6 +106,30 @@ inline CellLists cell_lists(void *base, int64_t max_N)
     return L;
 }
 
+// One suspension of a batch in the symmetric pass: its first sphere in the packed layout, its size and
+// its first tile in the batch's tile numbering.
+struct SymInst {
+    long long off;
+    int N;
+    int tile0;
+};
+
+// Symmetric pass over a batch of suspensions (float32): schedule and scratch, built by
+// batch_sym_plan and owned by the batch context.
+struct BatchSymPlan {
+    int *index = nullptr;         // device: CTA table, segment table, row_seg, col_start, tile_inst
+    size_t index_cap = 0;         // ints
+    SymInst *sinst = nullptr;     // device, one per suspension
+    int sinst_cap = 0;
+    double *tgt = nullptr;        // segment partials, 3 x 128 doubles each
+    size_t tgt_cap = 0;           // bytes
+    float *srcp = nullptr;        // column partials, 3 x 128 floats each
+    size_t src_cap = 0;           // bytes
+    int ncta = 0, nseg = 0, ntiles = 0, seg_off = 0, row_off = 0, col_off = 0, inst_off = 0;
+    bool valid = false;
+    std::vector<int64_t> sizes;   // the suspension sizes the plan was built for
+};
+
 // Scratch owned by a context.
 struct Workspace {
     void *src = nullptr;          // packed sources, max_N records (SrcF64 size)
@@ -190,6 +216,17 @@ size_t sym_tgt_part_bytes(int64_t max_N, int num_sms);
 size_t sym_index_ints(int64_t max_N, int num_sms);
 
 int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_params *fp, double *F);
+
+// Build (or keep, when the sizes are unchanged) the batched symmetric plan for B suspensions of sizes N
+// packed one after another; grows the plan's scratch (not inside a stream capture).  Returns RPB_OK,
+// or an error; *ok is false when the plan would need more than the scratch limit (the caller then uses
+// the one-way kernels).
+int batch_sym_plan(BatchSymPlan &pl, int B, const int64_t *N, cudaStream_t st, bool *ok);
+void batch_sym_free(BatchSymPlan &pl);
+// U_b = M_tt F_b (+ M_tr T_b) for every suspension of the plan, from packed float32 sources; active
+// masks suspensions (null: all).
+int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, int64_t total, const double *pos,
+                    const double *F, const double *T, double *U, const int *active, double a, double eta);
 int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t stream_id, uint32_t instance,
                 double *out);
 int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol, int max_iter,

@@ -170,3 +170,49 @@ def test_batch_run_graph_equals_steps(batch32, batch64, precision):
     assert [s["m"] for s in sa] == [s["m"] for s in sb]
     for k in range(len(sizes)):
         assert torch.equal(qa[k], qb[k]) and torch.equal(Ua[k], Ub[k]), k
+
+
+LONG = [2100, 1030, 17, 640]
+
+
+def test_batch_mobility_fp32_long_rows(batch32):
+    """Suspensions of more than eight tiles: rows of the symmetric pass cut into several runs."""
+    poss = [overlapping(N, 80 + k) for k, N in enumerate(LONG)]
+    Fs = [inputs.vectors(N, 90 + k) for k, N in enumerate(LONG)]
+    Ts = [inputs.vectors(N, 95 + k) for k, N in enumerate(LONG)]
+    out = batch32.mobility_apply([dev(p) for p in poss], [dev(f) for f in Fs], [dev(t) for t in Ts])
+    outF = batch32.mobility_apply([dev(p) for p in poss], [dev(f) for f in Fs], None)
+    for k, N in enumerate(LONG):
+        assert maxrel(host(out[k], N), O.mobility_apply(poss[k], Fs[k], Ts[k])) <= 1e-5, (k, N)
+        assert maxrel(host(outF[k], N), O.mobility_apply(poss[k], Fs[k], None)) <= 1e-5, (k, N)
+
+
+def test_batch_fp32_symmetric_equals_one_way(batch32, gpu_lib, monkeypatch):
+    """The symmetric pass and the one-way kernel (RPB_FP32_BATCH_SYM=0) give the same products up to
+    float32 summation order."""
+    monkeypatch.setenv("RPB_FP32_BATCH_SYM", "0")
+    one = gpu_lib.BatchContext(max_total_N=20000, max_B=8, precision="fp32", max_iter=8)
+    try:
+        poss = [overlapping(N, 110 + k) for k, N in enumerate(LONG)]
+        Fs = [inputs.vectors(N, 120 + k) for k, N in enumerate(LONG)]
+        Ts = [inputs.vectors(N, 130 + k) for k, N in enumerate(LONG)]
+        a = batch32.mobility_apply([dev(p) for p in poss], [dev(f) for f in Fs], [dev(t) for t in Ts])
+        b = one.mobility_apply([dev(p) for p in poss], [dev(f) for f in Fs], [dev(t) for t in Ts])
+        for k, N in enumerate(LONG):
+            assert maxrel(host(a[k], N), host(b[k], N)) <= 2e-6, (k, N)
+    finally:
+        one.close()
+
+
+def test_batch_fp32_alone_vs_mixed_products_bitwise(batch32):
+    """A suspension's product does not depend on its companions or its place in the batch."""
+    p = overlapping(2100, 140)
+    f, t = inputs.vectors(2100, 141), inputs.vectors(2100, 142)
+    alone = host(batch32.mobility_apply([dev(p)], [dev(f)], [dev(t)])[0], 2100)
+    others = [overlapping(N, 150 + k) for k, N in enumerate([333, 5, 1500])]
+    mix = [others[0], others[1], p, others[2]]
+    fs = [inputs.vectors(len(x), 160 + k) for k, x in enumerate(mix)]
+    ts = [inputs.vectors(len(x), 170 + k) for k, x in enumerate(mix)]
+    fs[2], ts[2] = f, t
+    mixed = host(batch32.mobility_apply([dev(x) for x in mix], [dev(x) for x in fs], [dev(x) for x in ts])[2], 2100)
+    assert np.array_equal(alone, mixed)
