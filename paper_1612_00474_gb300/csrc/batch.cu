@@ -179,10 +179,9 @@ __global__ void __launch_bounds__(kPairThreads, 6) batch_pair_f32x2_kernel(
         const double si = H0(z / a), zc = fmax(z, a);
         const double Fx = F ? si * F[i] : 0.0, Fy = F ? si * F[total + i] : 0.0, Fz = F ? si * F[2 * total + i] : 0.0;
         if (TORQUE)
-            pair_velocity<double, true>(0.0, 0.0, zc, zc, Fx, Fy, Fz, si * T[i], si * T[total + i], si * T[2 * total + i],
-                                        cd, ux, uy, uz);
+            self_velocity<true>(zc, Fx, Fy, Fz, si * T[i], si * T[total + i], cd, ux, uy, uz);
         else
-            pair_velocity<double, false>(0.0, 0.0, zc, zc, Fx, Fy, Fz, 0.0, 0.0, 0.0, cd, ux, uy, uz);
+            self_velocity<false>(zc, Fx, Fy, Fz, 0.0, 0.0, cd, ux, uy, uz);
         const double k = si * scale;
         U[i] = k * ux;
         U[total + i] = k * uy;
@@ -246,10 +245,9 @@ __global__ void __launch_bounds__(kPairThreads) batch_pair_f64_kernel(
         const double si = H0(z / a), zc = fmax(z, a);
         const double Fx = F ? si * F[i] : 0.0, Fy = F ? si * F[total + i] : 0.0, Fz = F ? si * F[2 * total + i] : 0.0;
         if (TORQUE)
-            pair_velocity<double, true>(0.0, 0.0, zc, zc, Fx, Fy, Fz, si * T[i], si * T[total + i], si * T[2 * total + i],
-                                        c, ux, uy, uz);
+            self_velocity<true>(zc, Fx, Fy, Fz, si * T[i], si * T[total + i], c, ux, uy, uz);
         else
-            pair_velocity<double, false>(0.0, 0.0, zc, zc, Fx, Fy, Fz, 0.0, 0.0, 0.0, c, ux, uy, uz);
+            self_velocity<false>(zc, Fx, Fy, Fz, 0.0, 0.0, c, ux, uy, uz);
         const double k = si * scale;
         U[i] = k * ux;
         U[total + i] = k * uy;

@@ -636,18 +636,16 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
     if (q == 0) {
         double ux = s[0][l], uy = s[1][l], uz = s[2][l];
         if (T)
-            pair_velocity<double, true>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], si * T[i],
-                                        si * T[N + i], si * T[2 * N + i], c, ux, uy, uz);
+            self_velocity<true>(zc, si * F[i], si * F[N + i], si * F[2 * N + i], si * T[i], si * T[N + i], c, ux, uy,
+                                uz);
         else
-            pair_velocity<double, false>(0.0, 0.0, zc, zc, si * F[i], si * F[N + i], si * F[2 * N + i], 0.0, 0.0,
-                                         0.0, c, ux, uy, uz);
+            self_velocity<false>(zc, si * F[i], si * F[N + i], si * F[2 * N + i], 0.0, 0.0, c, ux, uy, uz);
         U[i] = k * ux;
         U[N + i] = k * uy;
         U[2 * N + i] = k * uz;
     } else if (NC == 6) {
         double ux = s[3 % NC][l], uy = s[4 % NC][l], uz = s[5 % NC][l];
-        pair_velocity<double, false>(0.0, 0.0, zc, zc, si * P[i], si * P[N + i], si * P[2 * N + i], 0.0, 0.0, 0.0,
-                                     c, ux, uy, uz);
+        self_velocity<false>(zc, si * P[i], si * P[N + i], si * P[2 * N + i], 0.0, 0.0, c, ux, uy, uz);
         U2[i] = k * ux;
         U2[N + i] = k * uy;
         U2[2 * N + i] = k * uz;
@@ -1213,11 +1211,11 @@ __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, 
     const double si = wall ? H0(z / a) : 1.0;
     const double zc = wall ? fmax(z, a) : z;
     const double Fx = F ? si * F[i] : 0.0, Fy = F ? si * F[N + i] : 0.0, Fz = F ? si * F[2 * N + i] : 0.0;
-    const double Tx = T ? si * T[i] : 0.0, Ty = T ? si * T[N + i] : 0.0, Tz = T ? si * T[2 * N + i] : 0.0;
+    const double Tx = T ? si * T[i] : 0.0, Ty = T ? si * T[N + i] : 0.0;
     if (wall)
-        pair_velocity<double, true, true>(0.0, 0.0, zc, zc, Fx, Fy, Fz, Tx, Ty, Tz, c, ux, uy, uz);
+        self_velocity<true, true>(zc, Fx, Fy, Fz, Tx, Ty, c, ux, uy, uz);
     else
-        pair_velocity<double, true, false>(0.0, 0.0, zc, zc, Fx, Fy, Fz, Tx, Ty, Tz, c, ux, uy, uz);
+        self_velocity<true, false>(zc, Fx, Fy, Fz, Tx, Ty, c, ux, uy, uz);
     const double k = si * scale;
     U[i] = k * ux;
     U[N + i] = k * uy;

@@ -103,6 +103,42 @@ __device__ __forceinline__ void pair_velocity(R rx, R ry, R zi, R zj, R Fx, R Fy
     }
 }
 
+// Self term M_ii (F, T) in float64, in units of 1/(8 pi eta), F and T with s_i folded in, at the
+// clamped height h: the r = 0 limit of pair_velocity in closed form.  With x = a/h the wall-corrected
+// self mobilities are mu0 (1 - 9x/16 + x^3/8 - x^5/16) parallel and mu0 (1 - 9x/8 + x^3/2 - x^5/8)
+// normal to the wall (the image sum of Sec. II.B at R = 2h e_z), and the translation-rotation self
+// coupling is a^2/(8 h^4) e_z x T (Sec. III); mu0 = 4/(3a).  One division instead of the general
+// pair's two float64 reciprocal square roots and its wall coefficients: float64 runs at a small
+// fraction of the float32 rate on this GPU, and the epilogues that add this term are short.
+template <bool TORQUE, bool WALL = true>
+__device__ __forceinline__ void self_velocity(double h, double Fx, double Fy, double Fz, double Tx, double Ty,
+                                              const PairConsts<double> &c, double &ux, double &uy, double &uz)
+{
+    const double mu0 = c.near_c1;
+    if (!WALL) {
+        ux += mu0 * Fx;
+        uy += mu0 * Fy;
+        uz += mu0 * Fz;
+        return;
+    }
+    const double ih = 1.0 / h;
+    const double x = 0.5 * c.two_a * ih;  // a / h
+    const double x2 = x * x;
+    const double x3 = x2 * x;
+    const double x5 = x3 * x2;
+    const double mpar = mu0 * (1.0 - 0.5625 * x + 0.125 * x3 - 0.0625 * x5);
+    const double mperp = mu0 * (1.0 - 1.125 * x + 0.5 * x3 - 0.125 * x5);
+    ux += mpar * Fx;
+    uy += mpar * Fy;
+    uz += mperp * Fz;
+    if (TORQUE) {
+        const double ih2 = ih * ih;
+        const double ct = 0.125 * c.a2 * ih2 * ih2;
+        ux += ct * Ty;
+        uy -= ct * Tx;
+    }
+}
+
 // Float32 form of pair_velocity for the hot loop, hand-fused and algebraically rearranged (same
 // mathematics): the wall terms use the unnormalised image vector R, the free-space c1 and wall A/|R|
 // share one multiply-add into F, r.F and R.F share their in-plane part, the free-space rotlet
