@@ -430,11 +430,16 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
             fQ[2 * pp + hh] = sq_.z;
         }
         __syncthreads();
+        // a batched suspension's last tile is ragged: the loops stop after its last live source (the
+        // padding sources carry zero force, so what they would add is an exact zero; the column
+        // partial slots of padding sources then hold stale values, which no output reads)
+        const int nsrc = BATCH ? min(kTile, Ni - (t - tb) * kTile) : kTile;
         float2 u[NC];
 #pragma unroll
         for (int q = 0; q < NC; ++q) u[q] = zero2;
         if (t == seg.b) {
-            for (int k = 0; k < P; ++k) {
+            const int kend = BATCH ? (nsrc + 1) >> 1 : P;
+            for (int k = 0; k < kend; ++k) {
                 const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
                 const float4 e = TORQUE ? sE[k] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float2 g = TORQUE ? sG[k] : zero2;
@@ -474,7 +479,8 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 }
             }
         } else {
-            for (int k = 0; k < P; k += 2) {
+            const int kend = BATCH ? min(P, ((nsrc + 3) >> 2) << 1) : P;
+            for (int k = 0; k < kend; k += 2) {
                 float2 v[2][NC];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
