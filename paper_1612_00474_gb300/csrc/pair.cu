@@ -484,16 +484,19 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 float2 v[2][NC];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float4 a = sA[k + h], cc = sC[k + h], d = sD[k + h];
-                    const float4 e = TORQUE ? sE[k + h] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float2 g = TORQUE ? sG[k + h] : zero2;
-                    const float4 pv = RHS2 ? sP[k + h] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float2 pz = RHS2 ? sQ[k + h] : zero2;
+                    // the upper half-warp takes the second pair first, so that v[0] holds the pair
+                    // each lane keeps in the reduce-scatter below and v[1] the pair it sends
+                    const int kh = k + (h ^ (int)bit4);
+                    const float4 a = sA[kh], cc = sC[kh], d = sD[kh];
+                    const float4 e = TORQUE ? sE[kh] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float2 g = TORQUE ? sG[kh] : zero2;
+                    const float4 pv = RHS2 ? sP[kh] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float2 pz = RHS2 ? sQ[kh] : zero2;
                     const float2 zj = make_float2(cc.x, cc.y);
                     if (!PER) {
                         float2 rx, ry, rz, rho2, r2;
                         const bool close =
-                            pair_offsets_x2(txh, tyh, txl, tyl, tz2, zj, a, &sB[k + h], c, rx, ry, rz, rho2, r2);
+                            pair_offsets_x2(txh, tyh, txl, tyl, tz2, zj, a, &sB[kh], c, rx, ry, rz, rho2, r2);
                         pair_sym_x2<TORQUE, RHS2>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
                                                   make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
                                                   make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c,
@@ -502,7 +505,7 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                                                   RHS2 ? &u[3 % NC] : nullptr, RHS2 ? &v[h][3 % NC] : nullptr);
                     } else {
                         // minimum image from the full offsets, then the nine images summed both ways
-                        const float4 bl = sB[k + h];
+                        const float4 bl = sB[kh];
                         const float2 rx0 = min_image2(add2(sub2(txh, make_float2(a.x, a.y)),
                                                            sub2(txl, make_float2(bl.x, bl.y))), pl.xh, pl.xl, pl.ix);
                         const float2 ry0 = min_image2(add2(sub2(tyh, make_float2(a.z, a.w)),
@@ -531,11 +534,9 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 // sum for source 2k + 2 bit4(L) + bit3(L); lanes 0, 8, 16, 24 store it
 #pragma unroll
                 for (int q = 0; q < NC; ++q) {
-                    const float2 keep = bit4 ? v[1][q] : v[0][q];
-                    const float2 send = bit4 ? v[0][q] : v[1][q];
-                    const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 16),
-                                                   __shfl_xor_sync(0xffffffffu, send.y, 16));
-                    const float2 w2 = add2(keep, got);
+                    const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, v[1][q].x, 16),
+                                                   __shfl_xor_sync(0xffffffffu, v[1][q].y, 16));
+                    const float2 w2 = add2(v[0][q], got);
                     float w = bit3 ? w2.y : w2.x;
                     const float o = bit3 ? w2.x : w2.y;
                     w += __shfl_xor_sync(0xffffffffu, o, 8);
