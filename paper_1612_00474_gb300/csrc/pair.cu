@@ -349,17 +349,23 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     constexpr int NS = PER ? 9 : 1;  // image shifts per pair
     static_assert(!(PER && RHS2), "the two-right-hand-side form has no pseudo-periodic variant");
     static_assert(!(BATCH && (PER || RHS2)), "the batched form is the plain or the torque form");
-    __shared__ float4 sA[P], sB[P], sC[P], sD[P];
-    __shared__ float4 sE[TORQUE ? P : 1];
-    __shared__ float2 sG[TORQUE ? P : 1];
-    __shared__ float4 sP[RHS2 ? P : 1];
-    __shared__ float2 sQ[RHS2 ? P : 1];
+    // each source array holds the tile's pairs (2p, 2p+1) at [p] and the same pairs swapped at
+    // [SW + p]: lanes with bit 3 set read the swapped copy, so that the element each lane keeps in the
+    // reduce-scatter is always .x (SW = P + 2 puts the two copies in different banks)
+    constexpr int SW = P + 2;
+    __shared__ float4 sA[SW + P], sB[SW + P], sC[SW + P], sD[SW + P];
+    __shared__ float4 sE[TORQUE ? SW + P : 1];
+    __shared__ float2 sG[TORQUE ? SW + P : 1];
+    __shared__ float4 sP[RHS2 ? SW + P : 1];
+    __shared__ float2 sQ[RHS2 ? SW + P : 1];
     __shared__ float sv[4][NC][kTile];
     const SymCta cd = ctas[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2 zero2 = make_float2(0.f, 0.f);
     const int pp = tid >> 1, hh = tid & 1;
     const bool bit4 = (lane >> 4) & 1, bit3 = (lane >> 3) & 1;
+    // this lane's offsets of the pair it keeps (k0) and the pair it sends (k1) in the source arrays
+    const int k0 = (int)bit4 + (bit3 ? SW : 0), k1 = 1 - (int)bit4 + (bit3 ? SW : 0);
     float *fA = reinterpret_cast<float *>(sA);
     float *fB = reinterpret_cast<float *>(sB);
     float *fC = reinterpret_cast<float *>(sC);
@@ -411,23 +417,27 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
             if (TORQUE) st_ = src[j].t;
             if (RHS2) sq_ = src2[j];
         }
-        fA[4 * pp + hh] = sp_.x;
-        fA[4 * pp + 2 + hh] = sp_.y;
-        fB[4 * pp + hh] = sp_.z;
-        fB[4 * pp + 2 + hh] = sp_.w;
-        fC[4 * pp + hh] = sf_.x;
-        fC[4 * pp + 2 + hh] = sf_.y;
-        fD[4 * pp + hh] = sf_.z;
-        fD[4 * pp + 2 + hh] = sf_.w;
-        if (TORQUE) {
-            fE[4 * pp + hh] = st_.x;
-            fE[4 * pp + 2 + hh] = st_.y;
-            fG[2 * pp + hh] = st_.z;
-        }
-        if (RHS2) {
-            fP[4 * pp + hh] = sq_.x;
-            fP[4 * pp + 2 + hh] = sq_.y;
-            fQ[2 * pp + hh] = sq_.z;
+#pragma unroll
+        for (int cp = 0; cp < 2; ++cp) {
+            const int o4 = 4 * (cp * SW + pp) + (hh ^ cp), o2 = 2 * (cp * SW + pp) + (hh ^ cp);
+            fA[o4] = sp_.x;
+            fA[o4 + 2] = sp_.y;
+            fB[o4] = sp_.z;
+            fB[o4 + 2] = sp_.w;
+            fC[o4] = sf_.x;
+            fC[o4 + 2] = sf_.y;
+            fD[o4] = sf_.z;
+            fD[o4 + 2] = sf_.w;
+            if (TORQUE) {
+                fE[o4] = st_.x;
+                fE[o4 + 2] = st_.y;
+                fG[o2] = st_.z;
+            }
+            if (RHS2) {
+                fP[o4] = sq_.x;
+                fP[o4 + 2] = sq_.y;
+                fQ[o2] = sq_.z;
+            }
         }
         __syncthreads();
         // a batched suspension's last tile is ragged: the loops stop after its last live source (the
@@ -486,7 +496,7 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 for (int h = 0; h < 2; ++h) {
                     // the upper half-warp takes the second pair first, so that v[0] holds the pair
                     // each lane keeps in the reduce-scatter below and v[1] the pair it sends
-                    const int kh = k + (h ^ (int)bit4);
+                    const int kh = k + (h ? k1 : k0);
                     const float4 a = sA[kh], cc = sC[kh], d = sD[kh];
                     const float4 e = TORQUE ? sE[kh] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float2 g = TORQUE ? sG[kh] : zero2;
@@ -537,9 +547,8 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                     const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, v[1][q].x, 16),
                                                    __shfl_xor_sync(0xffffffffu, v[1][q].y, 16));
                     const float2 w2 = add2(v[0][q], got);
-                    float w = bit3 ? w2.y : w2.x;
-                    const float o = bit3 ? w2.x : w2.y;
-                    w += __shfl_xor_sync(0xffffffffu, o, 8);
+                    float w = w2.x;
+                    w += __shfl_xor_sync(0xffffffffu, w2.y, 8);
                     w += __shfl_xor_sync(0xffffffffu, w, 4);
                     w += __shfl_xor_sync(0xffffffffu, w, 2);
                     w += __shfl_xor_sync(0xffffffffu, w, 1);
