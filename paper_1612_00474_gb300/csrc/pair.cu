@@ -797,11 +797,11 @@ static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F,
             pair_f32x2_sym_kernel<5, true><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
                                                                                 w.sym_src);
     } else {
-        if (ctx->sym_minb == 5)
-            pair_f32x2_sym_kernel<5, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
+        if (ctx->sym_minb == 6)
+            pair_f32x2_sym_kernel<6, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
                                                                                  w.sym_src);
         else
-            pair_f32x2_sym_kernel<6, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
+            pair_f32x2_sym_kernel<5, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
                                                                                  w.sym_src);
     }
     pair_sym_reduce_kernel<3><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
@@ -977,7 +977,7 @@ int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, 
         pair_f32x2_sym_kernel<5, true, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
             src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
     else
-        pair_f32x2_sym_kernel<6, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
+        pair_f32x2_sym_kernel<5, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
             src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
     pair_sym_reduce_kernel<3, true><<<pl.ntiles, 6 * kTile, 0, st>>>(
         pl.tgt, pl.srcp, pl.index + pl.row_off, cs, n, pos, F, T, make_consts<double>(a), a, 1.0 / (8.0 * kPi * eta),
