@@ -302,6 +302,12 @@ struct SymSeg {
     int b, t0, t1, pad;
 };
 
+// both halves of a float2 from the lane lane ^ m
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
 // Periods of the pseudo-periodic mode for the float32 kernels: L = L_hi + L_lo, and 1 / L_hi.
 struct PerLen {
     float xh, xl, yh, yl, ix, iy;
@@ -349,10 +355,14 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     constexpr int NS = PER ? 9 : 1;  // image shifts per pair
     static_assert(!(PER && RHS2), "the two-right-hand-side form has no pseudo-periodic variant");
     static_assert(!(BATCH && (PER || RHS2)), "the batched form is the plain or the torque form");
-    // each source array holds the tile's pairs (2p, 2p+1) at [p] and the same pairs swapped at
-    // [SW + p]: lanes with bit 3 set read the swapped copy, so that the element each lane keeps in the
-    // reduce-scatter is always .x (SW = P + 2 puts the two copies in different banks)
-    constexpr int SW = P + 2;
+    // G source pairs (2G sources) are evaluated per step and then reduce-scattered over the warp:
+    // four for the translation-translation form, two for the forms with torques, a second
+    // right-hand side or nine images (their registers do not allow four).  Each source array holds
+    // the tile's pairs (2p, 2p+1) at [p] and the same pairs swapped at [SW + p]; lanes with bit 3
+    // (G = 2) or bit 2 (G = 4) set read the swapped copy, so that the element each lane keeps in the
+    // reduce-scatter is always .x (SW puts the two copies in different banks for the 2G lane groups)
+    constexpr int G = (TORQUE || RHS2 || PER) ? 2 : 4;
+    constexpr int SW = G == 4 ? P + 4 : P + 2;
     __shared__ float4 sA[SW + P], sB[SW + P], sC[SW + P], sD[SW + P];
     __shared__ float4 sE[TORQUE ? SW + P : 1];
     __shared__ float2 sG[TORQUE ? SW + P : 1];
@@ -363,9 +373,12 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2 zero2 = make_float2(0.f, 0.f);
     const int pp = tid >> 1, hh = tid & 1;
-    const bool bit4 = (lane >> 4) & 1, bit3 = (lane >> 3) & 1;
-    // this lane's offsets of the pair it keeps (k0) and the pair it sends (k1) in the source arrays
-    const int k0 = (int)bit4 + (bit3 ? SW : 0), k1 = 1 - (int)bit4 + (bit3 ? SW : 0);
+    const bool bit4 = (lane >> 4) & 1, bit3 = (lane >> 3) & 1, bit2 = (lane >> 2) & 1;
+    // pk: the pair of a step this lane keeps in the reduce-scatter (it evaluates pairs in the order
+    // h ^ pk, so v[0] is that pair and the pairs it sends come in the order its partners keep them);
+    // swz: its copy of the source arrays
+    const int pk = G == 4 ? ((2 * (int)bit4) ^ (int)bit3) : (int)bit4;
+    const int swz = (G == 4 ? bit2 : bit3) ? SW : 0;
     float *fA = reinterpret_cast<float *>(sA);
     float *fB = reinterpret_cast<float *>(sB);
     float *fC = reinterpret_cast<float *>(sC);
@@ -489,14 +502,12 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 }
             }
         } else {
-            const int kend = BATCH ? min(P, ((nsrc + 3) >> 2) << 1) : P;
-            for (int k = 0; k < kend; k += 2) {
-                float2 v[2][NC];
+            const int kend = BATCH ? min(P, (nsrc + 2 * G - 1) / (2 * G) * G) : P;
+            for (int k = 0; k < kend; k += G) {
+                float2 v[G][NC];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    // the upper half-warp takes the second pair first, so that v[0] holds the pair
-                    // each lane keeps in the reduce-scatter below and v[1] the pair it sends
-                    const int kh = k + (h ? k1 : k0);
+                for (int h = 0; h < G; ++h) {
+                    const int kh = k + (h ^ pk) + swz;
                     const float4 a = sA[kh], cc = sC[kh], d = sD[kh];
                     const float4 e = TORQUE ? sE[kh] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float2 g = TORQUE ? sG[kh] : zero2;
@@ -540,19 +551,25 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                         }
                     }
                 }
-                // reduce-scatter of the four sources 2k .. 2k+3 over the warp: lane L ends with the
-                // sum for source 2k + 2 bit4(L) + bit3(L); lanes 0, 8, 16, 24 store it
+                // reduce-scatter of the 2G sources 2k .. 2k + 2G - 1 over the warp.  G = 2: lane L ends
+                // with the sum for source 2(k + pk) + bit3(L), stored by lanes 0, 8, 16, 24; G = 4:
+                // with source 2(k + pk) + bit2(L), stored by lanes 0, 4, .., 28
 #pragma unroll
                 for (int q = 0; q < NC; ++q) {
-                    const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, v[1][q].x, 16),
-                                                   __shfl_xor_sync(0xffffffffu, v[1][q].y, 16));
-                    const float2 w2 = add2(v[0][q], got);
-                    float w = w2.x;
-                    w += __shfl_xor_sync(0xffffffffu, w2.y, 8);
-                    w += __shfl_xor_sync(0xffffffffu, w, 4);
+                    float w;
+                    if (G == 2) {
+                        const float2 w2 = add2(v[0][q], shfl_xor2(v[1 % G][q], 16));
+                        w = w2.x + __shfl_xor_sync(0xffffffffu, w2.y, 8);
+                    } else {
+                        const float2 a0 = add2(v[0][q], shfl_xor2(v[2 % G][q], 16));
+                        const float2 a1 = add2(v[1 % G][q], shfl_xor2(v[3 % G][q], 16));
+                        const float2 x2 = add2(a0, shfl_xor2(a1, 8));
+                        w = x2.x + __shfl_xor_sync(0xffffffffu, x2.y, 4);
+                    }
+                    if (G == 2) w += __shfl_xor_sync(0xffffffffu, w, 4);
                     w += __shfl_xor_sync(0xffffffffu, w, 2);
                     w += __shfl_xor_sync(0xffffffffu, w, 1);
-                    if ((lane & 7) == 0) sv[warp][q][2 * k + 2 * bit4 + bit3] = w;
+                    if ((lane & (G == 4 ? 3 : 7)) == 0) sv[warp][q][2 * (k + pk) + (G == 4 ? bit2 : bit3)] = w;
                 }
             }
         }
