@@ -373,12 +373,15 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2 zero2 = make_float2(0.f, 0.f);
     const int pp = tid >> 1, hh = tid & 1;
-    const bool bit4 = (lane >> 4) & 1, bit3 = (lane >> 3) & 1, bit2 = (lane >> 2) & 1;
+    const bool bit4 = (lane >> 4) & 1, bit3 = (lane >> 3) & 1;
     // pk: the pair of a step this lane keeps in the reduce-scatter (it evaluates pairs in the order
     // h ^ pk, so v[0] is that pair and the pairs it sends come in the order its partners keep them);
     // swz: its copy of the source arrays
     const int pk = G == 4 ? ((2 * (int)bit4) ^ (int)bit3) : (int)bit4;
-    const int swz = (G == 4 ? bit2 : bit3) ? SW : 0;
+    const bool bsw = G == 4 ? (lane >> 2) & 1 : bit3;  // the lane reads the swapped copy
+    const int swz = bsw ? SW : 0;
+    // G = 2: offsets of the pair this lane keeps (k0) and of the pair it sends (k1)
+    const int k0 = (int)bit4 + (bit3 ? SW : 0), k1 = 1 - (int)bit4 + (bit3 ? SW : 0);
     float *fA = reinterpret_cast<float *>(sA);
     float *fB = reinterpret_cast<float *>(sB);
     float *fC = reinterpret_cast<float *>(sC);
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                 float2 v[G][NC];
 #pragma unroll
                 for (int h = 0; h < G; ++h) {
-                    const int kh = k + (h ^ pk) + swz;
+                    const int kh = G == 2 ? k + (h ? k1 : k0) : k + (h ^ pk) + swz;
                     const float4 a = sA[kh], cc = sC[kh], d = sD[kh];
                     const float4 e = TORQUE ? sE[kh] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float2 g = TORQUE ? sG[kh] : zero2;
@@ -569,7 +572,9 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                     if (G == 2) w += __shfl_xor_sync(0xffffffffu, w, 4);
                     w += __shfl_xor_sync(0xffffffffu, w, 2);
                     w += __shfl_xor_sync(0xffffffffu, w, 1);
-                    if ((lane & (G == 4 ? 3 : 7)) == 0) sv[warp][q][2 * (k + pk) + (G == 4 ? bit2 : bit3)] = w;
+                    // (the two-pair index is spelled 2k + 2 bit4 + bit3: the equal 2(k + pk) + bit3 cost the
+                    // two-right-hand-side form, at its 128-register cap, 14% in time)
+                    if ((lane & (G == 4 ? 3 : 7)) == 0) sv[warp][q][G == 4 ? 2 * (k + pk) + bsw : 2 * k + 2 * bit4 + bit3] = w;
                 }
             }
         }
