@@ -356,12 +356,12 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     static_assert(!(PER && RHS2), "the two-right-hand-side form has no pseudo-periodic variant");
     static_assert(!(BATCH && (PER || RHS2)), "the batched form is the plain or the torque form");
     // G source pairs (2G sources) are evaluated per step and then reduce-scattered over the warp:
-    // four for the translation-translation form, two for the forms with torques, a second
-    // right-hand side or nine images (their registers do not allow four).  Each source array holds
+    // four, or two for the pseudo-periodic forms (nine images per pair already share one
+    // reduce-scatter there, and their registers do not allow four).  Each source array holds
     // the tile's pairs (2p, 2p+1) at [p] and the same pairs swapped at [SW + p]; lanes with bit 3
     // (G = 2) or bit 2 (G = 4) set read the swapped copy, so that the element each lane keeps in the
     // reduce-scatter is always .x (SW puts the two copies in different banks for the 2G lane groups)
-    constexpr int G = (TORQUE || RHS2 || PER) ? 2 : 4;
+    constexpr int G = PER ? 2 : 4;
     constexpr int SW = G == 4 ? P + 4 : P + 2;
     __shared__ float4 sA[SW + P], sB[SW + P], sC[SW + P], sD[SW + P];
     __shared__ float4 sE[TORQUE ? SW + P : 1];
@@ -690,7 +690,8 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
     }
 }
 
-constexpr int kRhs2MinBlocks = 4;  // resident CTAs per SM of the two-right-hand-side form
+constexpr int kFusedMinBlocks = 4;  // resident CTAs per SM of the form with torques
+constexpr int kRhs2MinBlocks = 3;  // resident CTAs per SM of the two-right-hand-side form
 constexpr int kPerMinBlocks = 5;   // resident CTAs per SM of the pseudo-periodic forms
 
 // Upper-triangle schedule for N targets: the nb (nb + 1) / 2 units (b, t >= b) in row-major order
@@ -812,12 +813,8 @@ static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F,
     const X2Consts c = make_x2_consts(a);
     const int *cs = w.sym_index + w.sym_col_off;
     if (T) {
-        if (ctx->sym_minb == 6)
-            pair_f32x2_sym_kernel<6, true><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
-                                                                                w.sym_src);
-        else
-            pair_f32x2_sym_kernel<5, true><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
-                                                                                w.sym_src);
+        pair_f32x2_sym_kernel<kFusedMinBlocks, true><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs,
+                                                                                      w.sym_tgt, w.sym_src);
     } else {
         if (ctx->sym_minb == 6)
             pair_f32x2_sym_kernel<6, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
@@ -996,7 +993,7 @@ int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, 
     const X2Consts c = make_x2_consts(a);
     const int n = (int)total;
     if (T)
-        pair_f32x2_sym_kernel<5, true, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
+        pair_f32x2_sym_kernel<kFusedMinBlocks, true, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
             src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
     else
         pair_f32x2_sym_kernel<5, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
