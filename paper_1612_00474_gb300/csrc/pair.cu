@@ -355,13 +355,12 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     constexpr int NS = PER ? 9 : 1;  // image shifts per pair
     static_assert(!(PER && RHS2), "the two-right-hand-side form has no pseudo-periodic variant");
     static_assert(!(BATCH && (PER || RHS2)), "the batched form is the plain or the torque form");
-    // G source pairs (2G sources) are evaluated per step and then reduce-scattered over the warp:
-    // four, or two for the pseudo-periodic forms (nine images per pair already share one
-    // reduce-scatter there, and their registers do not allow four).  Each source array holds
+    // G source pairs (2G sources) are evaluated per step and then reduce-scattered over the warp
+    // (G = 2 is kept as an option: every form measured faster with four).  Each source array holds
     // the tile's pairs (2p, 2p+1) at [p] and the same pairs swapped at [SW + p]; lanes with bit 3
     // (G = 2) or bit 2 (G = 4) set read the swapped copy, so that the element each lane keeps in the
     // reduce-scatter is always .x (SW puts the two copies in different banks for the 2G lane groups)
-    constexpr int G = PER ? 2 : 4;
+    constexpr int G = 4;
     constexpr int SW = G == 4 ? P + 4 : P + 2;
     __shared__ float4 sA[SW + P], sB[SW + P], sC[SW + P], sD[SW + P];
     __shared__ float4 sE[TORQUE ? SW + P : 1];
@@ -692,7 +691,7 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
 
 constexpr int kFusedMinBlocks = 4;  // resident CTAs per SM of the form with torques
 constexpr int kRhs2MinBlocks = 3;  // resident CTAs per SM of the two-right-hand-side form
-constexpr int kPerMinBlocks = 5;   // resident CTAs per SM of the pseudo-periodic forms
+constexpr int kPerMinBlocks = 4;   // resident CTAs per SM of the pseudo-periodic forms
 
 // Upper-triangle schedule for N targets: the nb (nb + 1) / 2 units (b, t >= b) in row-major order
 // cut into ncta runs of equal length, each run split into segments at row ends.  ncta = 60 x SMs
