@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
         zi = pos[2 * total + i];
     }
     const float xf = (float)xi, yf = (float)yi, zf = (float)zi;
-    const double f0 = U0 / b;
+    const double f0 = U0 / b, inv_b = 1.0 / b;
     double fx = 0.0, fy = 0.0, fz = 0.0;
     constexpr int kQ = 32;
     int queue[kQ];
@@ -288,13 +288,10 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
         for (int q = 0; q < nq; ++q) {
             const int64_t j = d.off + queue[q];
             const double dx = xi - pos[j], dy = yi - pos[total + j], dz = zi - pos[2 * total + j];
-            const double r = sqrt(dx * dx + dy * dy + dz * dz);
-            if (r > 0.0) {
-                const double m = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
-                fx += m * dx;
-                fy += m * dy;
-                fz += m * dz;
-            }
+            const double m = steric_pair_factor(dx * dx + dy * dy + dz * dz, 2.0 * a, f0, inv_b);
+            fx += m * dx;
+            fy += m * dy;
+            fz += m * dz;
         }
         nq = 0;
     };

@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
 // kernel); the column of tile b holds the rows tile0 .. b - 1 of its suspension, summed in an order
 // relative to tile0 so that a suspension's result does not depend on its companions.
 template <int NC, bool BATCH = false>
-__global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
+__global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_reduce_kernel(const double *__restrict__ tgt_part, const float *__restrict__ src_part,
                                        const int *__restrict__ row_seg, const int *__restrict__ col_start, int N,
                                        const double *__restrict__ pos, const double *__restrict__ F,
                                        const double *__restrict__ T, PairConsts<double> c, double a, double scale,
@@ -615,9 +615,11 @@ __global__ void __launch_bounds__(768, 2) pair_sym_reduce_kernel(const double *_
                                        const int *__restrict__ tile_inst = nullptr,
                                        const int *__restrict__ active = nullptr)
 {
-    // one CTA of 768 threads per 128-sphere tile, the longest columns first; thread (half, q, l):
+    // one CTA of 768 threads (384 batched) per 128-sphere tile, the longest columns first; thread (half, q, l):
     // component q of sphere l, rows of its column congruent to `half` modulo HALVES
-    constexpr int HALVES = 6 / NC;
+    // (a batched suspension's columns are at most a few tiles long: one thread per (q, l) there, so
+    // that twice as many tiles are resident at once)
+    constexpr int HALVES = BATCH ? 1 : 6 / NC;
     __shared__ double s[NC][kTile];
     __shared__ double s1[NC][kTile];
     const int nb = gridDim.x;
@@ -997,7 +999,7 @@ int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, 
     else
         pair_f32x2_sym_kernel<5, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
             src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
-    pair_sym_reduce_kernel<3, true><<<pl.ntiles, 6 * kTile, 0, st>>>(
+    pair_sym_reduce_kernel<3, true><<<pl.ntiles, 3 * kTile, 0, st>>>(
         pl.tgt, pl.srcp, pl.index + pl.row_off, cs, n, pos, F, T, make_consts<double>(a), a, 1.0 / (8.0 * kPi * eta),
         U, nullptr, nullptr, pl.sinst, pl.index + pl.inst_off, active);
     count_launches(2);
@@ -1584,13 +1586,10 @@ __global__ void __launch_bounds__(128) forces_cell_kernel(const double *__restri
         for (int q = 0; q < nq; ++q) {
             const int j = queue[q];
             const double dx = xi - pos[j], dy = yi - pos[N + j], dz = zi - pos[2 * N + j];
-            const double r = sqrt(dx * dx + dy * dy + dz * dz);
-            if (r > 0.0) {
-                const double mm = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
-                fx += mm * dx;
-                fy += mm * dy;
-                fz += mm * dz;
-            }
+            const double mm = steric_pair_factor(dx * dx + dy * dy + dz * dz, 2.0 * a, f0, 1.0 / b);
+            fx += mm * dx;
+            fy += mm * dy;
+            fz += mm * dz;
         }
         nq = 0;
     };
@@ -1655,13 +1654,10 @@ __global__ void __launch_bounds__(128) forces_kernel(const double *__restrict__ 
                 dx -= Lx * rint(dx / Lx);
                 dy -= Ly * rint(dy / Ly);
             }
-            const double r = sqrt(dx * dx + dy * dy + dz * dz);
-            if (r > 0.0) {
-                const double m = (r < 2.0 * a ? f0 : f0 * exp(-(r - 2.0 * a) / b)) / r;
-                fx += m * dx;
-                fy += m * dy;
-                fz += m * dz;
-            }
+            const double m = steric_pair_factor(dx * dx + dy * dy + dz * dz, 2.0 * a, f0, 1.0 / b);
+            fx += m * dx;
+            fy += m * dy;
+            fz += m * dz;
         }
         nq = 0;
     };

@@ -533,6 +533,19 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, flo
     }
 }
 
+// Factor m of the pair steric force m (x_i - x_j) of Sec. III: U0/b inside contact (r < 2a),
+// (U0/b) e^{-(r - 2a)/b} beyond, divided by r; zero for coincident centres.  f0 = U0/b, inv_b = 1/b.
+// One float64 reciprocal square root gives r and 1/r (float64 runs at a small fraction of the
+// float32 rate on this GPU, and a square root plus two divisions per near pair made the batched
+// force pass float64-bound).
+__device__ __forceinline__ double steric_pair_factor(double r2, double two_a, double f0, double inv_b)
+{
+    if (!(r2 > 0.0)) return 0.0;
+    const double ir = rsqrt(r2);
+    const double r = r2 * ir;
+    return (r < two_a ? f0 : f0 * exp((two_a - r) * inv_b)) * ir;
+}
+
 __device__ __forceinline__ double H0(double x)
 {
     return x > 1.0 ? 1.0 : (x >= 0.0 ? x : 0.0);
