@@ -29,9 +29,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "wall-RPY matvec Gpairs/s; BD steps/s at N=65536; p50/p99 solve latency"
-FLOPS_TT = 126      # algorithmic flops per pair, translation-translation block applied to a vector
-FLOPS_FUSED = 185   # ... plus the translation-rotation block (counted from the closed form of the pair block)
-FLOPS_SYM = 171     # per unordered pair when the block is evaluated once and applied both ways (81 + 2 x 45)
+# Algorithmic flops of the pair block as the kernels evaluate its closed form (FMA = 2 flops, multiply
+# or add = 1; the two reciprocal square roots per pair are MUFU operations, not counted):
+FLOPS_TT = 106      # one direction, translation-translation: geometry 8 + coefficients 63 + application 35
+FLOPS_FUSED = 147   # one direction with the translation-rotation coupling (+ 41)
+FLOPS_SYM = 135     # per unordered pair, block evaluated once and applied both ways: geometry 8 +
+                    # coefficients with the |R| powers folded in 70 + target application 30 + source 27
+OPS_SYM = 88        # the same as FP32 operations (an FMA, a multiply or an add is one lane operation)
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25  # dense FP64 rate of a GB300 (vector pipe)
 # DRAM bytes (read + write) of one launch of the symmetric translation-translation kernel at
@@ -331,13 +335,22 @@ def run_ours(args, rank, world, local_rank):
         elif args.periodic:
             flops_tt = 9.0 * N * N * FLOPS_TT
             kernel = f"pair_periodic_f{args.precision[2:]}_kernel<false,true> (translation-translation, 9 images)"
-        elif sym:  # each unordered pair once (171 flop) except inside the 128-wide diagonal tiles (126 flop each way)
+        elif sym:  # each unordered pair once (135 flop) except inside the 128-wide diagonal tiles (106 flop each way)
             flops_tt = FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag
             kernel = "pair_f32x2_sym_kernel (translation-translation, reciprocity)"
         else:
             flops_tt = float(N) * N * FLOPS_TT
             kernel = f"pair_f{args.precision[2:]}_kernel<false> (translation-translation)"
         achieved = flops_tt / t_tt / 1e12
+        ops_view = None
+        if sym:
+            # the FP32 pipe's operation rate: one lane operation per lane per clock, whether an FMA, a
+            # multiply or an add (a third of the pair's operations are multiplies and adds that cannot be
+            # fused, so the flop fraction understates how busy the pipe is)
+            ops = (9.0 if args.periodic else 1.0) * OPS_SYM * (float(N) * N - diag) / 2
+            ops_peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+            ops_view = {"per_unordered_pair": OPS_SYM, "achieved": ops / t_tt / 1e12, "peak": ops_peak,
+                        "unit": "Top/s", "frac": ops / t_tt / 1e12 / ops_peak}
         value = pairs / total_s / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
@@ -360,7 +373,8 @@ def run_ours(args, rank, world, local_rank):
                          "flops_per_launch": flops_tt,
                          "flops_per_pair": FLOPS_SYM / 2 if sym else FLOPS_TT,
                          "traffic": SYM_TT_TRAFFIC_BYTES.get(N) if sym and not args.periodic else None,
-                         "traffic_unit": "bytes per launch"},
+                         "traffic_unit": "bytes per launch",
+                         "fp32_ops": ops_view},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": "Gpairs/s", "h2d_bytes_per_step": 2 * 3 * N * 8,
                     "d2h_bytes_per_step": 2 * 3 * N * 8},
