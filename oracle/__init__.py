@@ -15,7 +15,8 @@ Pieces and the passages they follow:
                  dense assembly, soft steric + gravity forces (Sec. III).
   wall_image.c   generated by derive_wall.py: Faxen operators applied to Blake's
                  image system (Eq. mobilityDifferential, Eq. mobilityDifferentialTR).
-  core.py        Lanczos M^{1/2} W (Sec. II.C), RFD drift (Sec. II.A), AB step (Eq. AB).
+  core.py        Lanczos M^{1/2} W (Sec. II.C; optionally with the block-diagonal
+                 preconditioner that section reports trying), RFD drift (Sec. II.A), AB step (Eq. AB).
   philox.py      Philox4x32-10 Gaussian noise (generator of Salmon et al., SC'11).
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
@@ -24,4 +25,5 @@ constants are the published ones and only the 4x64 round structure is pinned
 against numpy's Philox (see philox.py).
 """
 from .core import (ab_step, blake_image_raw, blake_image_raw_batch, dense, forces, freespace_tr, freespace_tt, lanczos_sqrt,  # noqa: F401
-                   mobility_apply, noise, pair_blocks, rel_err, rfd_drift, wall_image_tr, wall_image_tt)
+                   mobility_apply, noise, pair_blocks, rel_err, rfd_drift, self_diagonal, wall_image_tr,
+                   wall_image_tt)

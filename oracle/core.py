@@ -182,8 +182,30 @@ def _tridiag_sqrt_e1(alpha, beta):
     return Q @ (np.sqrt(lam) * Q[0, :])
 
 
+def self_diagonal(pos, a=1.0, eta=1.0, wall=True, periodic=None):
+    """Diagonal of the self blocks M_ii of M_tt, particle-major, shape (N, 3).
+
+    The block-diagonal preconditioner Sec. II.C mentions keeps each particle's self mobility,
+    including its interaction with the wall; the translation self block of the wall-corrected
+    (regularised) mobility is diagonal, so its diagonal is the block.  Taken from the oracle's own
+    self block (pair_blocks with same=True), or, in pseudo-periodic mode, by applying the periodic
+    mobility to a unit vector on one particle (its own images contribute to its self block)."""
+    pos = _c3(pos)
+    N = pos.shape[0]
+    D = np.zeros((N, 3))
+    for i in range(N):
+        if periodic is None and wall:
+            D[i] = np.diag(pair_blocks(pos[i], pos[i], same=True, a=a, eta=eta)[0])
+        else:
+            for c in range(3):
+                e = np.zeros((N, 3))
+                e[i, c] = 1.0
+                D[i, c] = mobility_apply(pos, e, None, a, eta, rows=(i, i + 1), wall=wall, periodic=periodic)[0, c]
+    return D
+
+
 def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.0, matvec=None, wall=True,
-                 periodic=None):
+                 periodic=None, precondition=False):
     """g_m ~ M_tt^{1/2} W by m steps of Lanczos with full reorthogonalisation.
 
     Readings where the paper is silent (it cites the Krylov method of Ando et al.):
@@ -197,6 +219,12 @@ def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.
       - W = 0 gives g = 0 with m = 0.
       - exact_iters=m runs exactly m iterations (unless breakdown) regardless of tol, so that
         two implementations can be compared at equal m.
+      - precondition=True: the block-diagonal preconditioner that Sec. II.C reports trying (the
+        paper's own runs do not use it).  With D the diagonal of the self blocks (self_diagonal)
+        and P = D^{-1/2} (0 where D = 0), the iteration runs on P M P with the same W, and
+        g = D^{1/2} y; then g = L W with L L^T = M, so the noise has the right covariance (it is a
+        different square root than M^{1/2}).  eps_k and the stop are taken on the iterate y of
+        the preconditioned operator (the paper states its criterion only without preconditioning).
     Returns (g (N,3), m, eps_m (nan if m < 2), converged)."""
     pos = _c3(pos)
     w0 = _c3(W).ravel()
@@ -204,6 +232,11 @@ def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.
     if matvec is None:
         def matvec(v):
             return mobility_apply(pos, v.reshape(-1, 3), None, a, eta, wall=wall, periodic=periodic).ravel()
+    if precondition:
+        D = self_diagonal(pos, a, eta, wall, periodic).ravel()
+        Pd = np.where(D > 0.0, 1.0 / np.sqrt(np.where(D > 0.0, D, 1.0)), 0.0)
+        y, m, eps, conv = lanczos_sqrt(pos, W, tol, max_iter, exact_iters, matvec=lambda v: Pd * matvec(Pd * v))
+        return (np.sqrt(D) * y.ravel()).reshape(-1, 3), m, eps, conv
     nW = float(np.sqrt(w0 @ w0))
     if nW == 0.0:
         return np.zeros_like(w0).reshape(-1, 3), 0, float("nan"), True
@@ -275,13 +308,14 @@ def noise(N, seed, step, stream, instance=0):
 # ---------------------------------------------------------------- AB step (Eq. AB)
 def ab_step(pos, U_prev, step, seed, dt=0.01, delta=1e-6, tol=1e-3, max_iter=100, kT=1.0, a=1.0, eta=1.0,
             weight=1.0, torque=(0.0, 1.0, 0.0), U0=1.0, b=0.1, exact_iters=None, detail=False, scheme="AB",
-            one_sided=False, periodic=None):
+            one_sided=False, periodic=None, precondition=False):
     """One stochastic Adams-Bashforth step (scheme="AB", Eq. AB) or Euler-Maruyama step
     (scheme="EM", Eq. EM: q^{n+1} = q^n + dt U^n + sqrt(2 kT dt) g + dt drift).
 
     Readings: the deterministic velocity U^n = M_tt F^n + M_tr T (Sec. III: M_C T is treated like
     M F); the first AB step (step == 0, no U^{n-1}) is Euler-Maruyama, i.e. U^{-1} := U^0; the torque
-    is the same constant vector on every particle.  one_sided selects the one-sided RFD.
+    is the same constant vector on every particle.  one_sided selects the one-sided RFD;
+    precondition the block-diagonal preconditioner of the Lanczos step (see lanczos_sqrt).
     Returns (q^{n+1}, U^n, info)."""
     pos = _c3(pos)
     N = pos.shape[0]
@@ -290,7 +324,8 @@ def ab_step(pos, U_prev, step, seed, dt=0.01, delta=1e-6, tol=1e-3, max_iter=100
     Un = mobility_apply(pos, F, T, a, eta, periodic=periodic)
     W = noise(N, seed, step, 0)
     Wt = noise(N, seed, step, 1)
-    g, m, eps, conv = lanczos_sqrt(pos, W, tol, max_iter, exact_iters, a, eta, periodic=periodic)
+    g, m, eps, conv = lanczos_sqrt(pos, W, tol, max_iter, exact_iters, a, eta, periodic=periodic,
+                                   precondition=precondition)
     d, up, um = rfd_drift(pos, Wt, delta, kT, a, eta, parts=True, one_sided=one_sided, periodic=periodic)
     Up = Un if (scheme == "EM" or step == 0 or U_prev is None) else _c3(U_prev)
     new = pos + dt * (1.5 * Un - 0.5 * Up) + math.sqrt(2.0 * kT * dt) * g + dt * d
