@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--periodic", action="store_true",
                     help="monolayer: pseudo-periodic boundaries with the monolayer's square as the unit cell")
+    ap.add_argument("--precondition", action="store_true",
+                    help="monolayer: block-diagonal Lanczos preconditioner (an option; the paper's runs use none)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy", "small",
                                            "fingering"],
@@ -90,8 +92,9 @@ def cell_side(N, phi=0.4):
 def workload_name(args):
     per = (f", pseudo-periodic {cell_side(args.N):.2f}a x {cell_side(args.N):.2f}a cell (unit cell + 8 neighbours)"
            if args.periodic else "")
+    pc = ", block-diagonal Lanczos preconditioner" if getattr(args, "precondition", False) else ""
     return (f"roller monolayer N={args.N} (phi=0.4, z=a+Exp(0.5a), gravity -1 z, torque +1 y, U0=1, b=0.1a), "
-            f"AB step dt={args.dt}, RFD delta={args.delta}, Lanczos tol={args.tol}, {args.precision} pairs{per}")
+            f"AB step dt={args.dt}, RFD delta={args.delta}, Lanczos tol={args.tol}, {args.precision} pairs{per}{pc}")
 
 
 def oracle_sample(N, seed, seconds, periodic=None):
@@ -223,6 +226,8 @@ def run_ours(args, rank, world, local_rank):
     if args.periodic:
         ctx.set_periodic(cell_side(N), cell_side(N))
         images = 9  # each source at its minimum image and the eight neighbour-cell shifts
+    if args.precondition:
+        ctx.set_preconditioner("block-diagonal")
     pos0 = inputs.monolayer(N, seed=seed)
     q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
     Up = torch.zeros_like(q)

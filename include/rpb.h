@@ -97,6 +97,20 @@ int rpb_set_stream(rpb_ctx *ctx, void *stream);
  * the cell (they are folded in for the computation, and returned unfolded). */
 int rpb_set_periodic(rpb_ctx *ctx, double Lx, double Ly);
 
+/* Preconditioner of the Lanczos square root (Sec. II.C reports trying a block-diagonal one; the
+ * paper's own runs use none, which is the default).  RPB_PRECOND_BLOCK_DIAGONAL: with D the diagonal
+ * of the particles' translation self blocks (each particle's mobility including its interaction
+ * with the wall, none between particles; the block is diagonal, and 0 for a sphere on or below the
+ * wall), rpb_lanczos_sqrt_apply and the Brownian part of rpb_ab_step / rpb_step run the iteration on
+ * P M P with P = D^{-1/2} (0 where D = 0) and return g = D^{1/2} y: a sample with covariance M, but
+ * not M^{1/2} W itself.  iters_out / lanczos_iters count the products with P M P, and the error
+ * estimate and the stopping test are taken on y.  Allocates 2 vectors of 3 max_N doubles on the first
+ * switch-on (RPB_ENOMEM if that fails; the setting is then unchanged); RPB_EINVAL for an unknown
+ * kind.  Batch contexts do not use it. */
+#define RPB_PRECOND_NONE 0
+#define RPB_PRECOND_BLOCK_DIAGONAL 1
+int rpb_set_preconditioner(rpb_ctx *ctx, int kind);
+
 /* U = M_tt F + M_tr T  (Sec. II.B Eq. mobilityDifferential and mobilityOverlap; Sec. III Eq.
  * mobilityDifferentialTR; regularisation M = B Mtilde B of Appendix A Eq. effMob, applied to
  * both blocks).  pos: 3N positions.  F, T: 3N forces and torques; either may be NULL (treated

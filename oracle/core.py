@@ -186,21 +186,19 @@ def self_diagonal(pos, a=1.0, eta=1.0, wall=True, periodic=None):
     """Diagonal of the self blocks M_ii of M_tt, particle-major, shape (N, 3).
 
     The block-diagonal preconditioner Sec. II.C mentions keeps each particle's self mobility,
-    including its interaction with the wall; the translation self block of the wall-corrected
-    (regularised) mobility is diagonal, so its diagonal is the block.  Taken from the oracle's own
-    self block (pair_blocks with same=True), or, in pseudo-periodic mode, by applying the periodic
-    mobility to a unit vector on one particle (its own images contribute to its self block)."""
+    including its interaction with the wall, and neglects its hydrodynamic interactions with other
+    particles; in pseudo-periodic mode a particle's periodic images count as other particles, so
+    the block is the same as without periods.  The translation self block of the wall-corrected
+    (regularised) mobility is diagonal, so its diagonal is the block: taken from the oracle's own
+    self block (pair_blocks with same=True), or mu0 I without the wall."""
     pos = _c3(pos)
     N = pos.shape[0]
     D = np.zeros((N, 3))
     for i in range(N):
-        if periodic is None and wall:
+        if wall:
             D[i] = np.diag(pair_blocks(pos[i], pos[i], same=True, a=a, eta=eta)[0])
         else:
-            for c in range(3):
-                e = np.zeros((N, 3))
-                e[i, c] = 1.0
-                D[i, c] = mobility_apply(pos, e, None, a, eta, rows=(i, i + 1), wall=wall, periodic=periodic)[0, c]
+            D[i] = np.diag(freespace_tt(pos[i], pos[i], a=a, eta=eta, same=True))
     return D
 
 
@@ -233,7 +231,7 @@ def lanczos_sqrt(pos, W, tol=1e-3, max_iter=100, exact_iters=None, a=1.0, eta=1.
         def matvec(v):
             return mobility_apply(pos, v.reshape(-1, 3), None, a, eta, wall=wall, periodic=periodic).ravel()
     if precondition:
-        D = self_diagonal(pos, a, eta, wall, periodic).ravel()
+        D = self_diagonal(pos, a, eta, wall).ravel()
         Pd = np.where(D > 0.0, 1.0 / np.sqrt(np.where(D > 0.0, D, 1.0)), 0.0)
         y, m, eps, conv = lanczos_sqrt(pos, W, tol, max_iter, exact_iters, matvec=lambda v: Pd * matvec(Pd * v))
         return (np.sqrt(D) * y.ravel()).reshape(-1, 3), m, eps, conv

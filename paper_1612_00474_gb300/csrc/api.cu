@@ -73,7 +73,7 @@ static void free_ws(Workspace &w)
 {
     void *dev[] = {w.src, w.partial, w.V, w.w, w.red, w.lz, w.pos_a, w.pos_b, w.pos_w, w.cells,
                    w.vec_a, w.vec_b, w.vec_c, w.vec_d, w.vec_e, w.vec_f, w.vec_g,
-                   w.sym_index, w.sym_tgt, w.sym_src, w.src2};
+                   w.sym_index, w.sym_tgt, w.sym_src, w.src2, w.pc, w.pcx};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (w.host_status) cudaFreeHost(w.host_status);
@@ -263,6 +263,33 @@ int rpb_set_periodic(rpb_ctx *ctx, double Lx, double Ly)
     return RPB_OK;
 }
 
+int rpb_set_preconditioner(rpb_ctx *ctx, int kind)
+{
+    g_err[0] = 0;
+    if (!ctx) {
+        set_error("null context");
+        return RPB_EINVAL;
+    }
+    if (kind != RPB_PRECOND_NONE && kind != RPB_PRECOND_BLOCK_DIAGONAL) {
+        set_error("unknown preconditioner %d", kind);
+        return RPB_EINVAL;
+    }
+    Workspace &w = ctx->ws;
+    if (kind != RPB_PRECOND_NONE && !w.pc) {
+        const size_t vb = (size_t)3 * ctx->max_N * sizeof(double);
+        if (cudaMalloc(&w.pc, vb) != cudaSuccess || cudaMalloc(&w.pcx, vb) != cudaSuccess) {
+            cudaGetLastError();
+            if (w.pc) cudaFree(w.pc);
+            if (w.pcx) cudaFree(w.pcx);
+            w.pc = w.pcx = nullptr;
+            set_error("cudaMalloc of the preconditioner vectors (2 x %zu bytes) failed", vb);
+            return RPB_ENOMEM;
+        }
+    }
+    ctx->precond = kind;
+    return RPB_OK;
+}
+
 int rpb_mobility_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T, double *U)
 {
     g_err[0] = 0;
@@ -385,15 +412,23 @@ int rpb_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step,
         if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 1u, 0u, Wt))) return rc;
         if (mobility_apply2_ok(ctx, N)) {
             // the deterministic velocity and the first Lanczos product M v_0 share one pair pass
+            // (with the preconditioner: M P v_0, scaled by P afterwards)
             bool zero = false;
-            if ((rc = lanczos_init(ctx, N, W, &zero))) return rc;
+            if ((rc = lanczos_precond_prepare(ctx, N, pos)) || (rc = lanczos_init(ctx, N, W, &zero))) return rc;
             if (zero) {
                 if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
                 if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "zero g")))
                     return rc;
                 conv = 1;
             } else {
-                if ((rc = mobility_apply2_impl(ctx, N, pos, F, T, w.V, Un, w.w))) return rc;
+                if (ctx->precond) {
+                    if ((rc = precond_scale(ctx, N, w.V, w.pcx, false)) ||
+                        (rc = mobility_apply2_impl(ctx, N, pos, F, T, w.pcx, Un, w.w)) ||
+                        (rc = precond_scale(ctx, N, w.w, w.w, false)))
+                        return rc;
+                } else if ((rc = mobility_apply2_impl(ctx, N, pos, F, T, w.V, Un, w.w))) {
+                    return rc;
+                }
                 lrc = lanczos_run(ctx, N, pos, g, tol, max_iter, true, &iters, &err, &conv);
             }
         } else {

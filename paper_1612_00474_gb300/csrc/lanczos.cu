@@ -18,6 +18,7 @@
 #include <cmath>
 
 #include "lanczos_math.cuh"
+#include "pair_math.cuh"
 
 namespace rpb {
 
@@ -164,6 +165,61 @@ __global__ void combine_kernel(const double *__restrict__ V, size_t ld, int64_t 
     }
 }
 
+// Block-diagonal preconditioner (Sec. II.C reports trying it: each particle's self mobility, with
+// its wall interaction, and no interactions between particles).  The translation self block of the
+// wall-corrected, regularised mobility is diagonal, s_i^2 / (8 pi eta) (mu_par, mu_par, mu_perp) at
+// the clamped height, so P = D^{-1/2} is a vector; P = 0 where D = 0 (spheres on or below the wall
+// have no mobility).  Free space: D = mu0.
+__global__ void precond_diag_kernel(const double *__restrict__ pos, int64_t N, PairConsts<double> c, double a,
+                                    double scale, int wall, double *__restrict__ P)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double z = pos[2 * N + i];
+        double ux = 0.0, uy = 0.0, uz = 0.0;
+        double k = scale;
+        if (wall) {
+            const double si = H0(z / a);
+            k *= si * si;
+            self_velocity<false, true>(fmax(z, a), 1.0, 1.0, 1.0, 0.0, 0.0, c, ux, uy, uz);
+        } else {
+            self_velocity<false, false>(z, 1.0, 1.0, 1.0, 0.0, 0.0, c, ux, uy, uz);
+        }
+        const double dx = k * ux, dz = k * uz;
+        P[i] = dx > 0.0 ? 1.0 / sqrt(dx) : 0.0;
+        P[N + i] = P[i];
+        P[2 * N + i] = dz > 0.0 ? 1.0 / sqrt(dz) : 0.0;
+    }
+}
+
+// out = x P (inverse: x / P, and 0 where P = 0), elementwise over 3N
+// (x and out may be the same vector: no __restrict__ on them)
+__global__ void precond_scale_kernel(const double *x, const double *__restrict__ P, int64_t n, int inverse,
+                                     double *out)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const double p = P[r];
+        out[r] = inverse ? (p > 0.0 ? x[r] / p : 0.0) : x[r] * p;
+    }
+}
+
+int lanczos_precond_prepare(rpb_ctx *ctx, int64_t N, const double *pos)
+{
+    if (!ctx->precond) return RPB_OK;
+    const double a = ctx->p.a;
+    precond_diag_kernel<<<blas_grid(N, ctx->num_sms), kBlasThreads, 0, ctx->stream>>>(
+        pos, N, make_consts<double>(a), a, 1.0 / (8.0 * kPi * ctx->p.eta), ctx->p.wall, ctx->ws.pc);
+    count_launches(1);
+    return cuda_fail(cudaGetLastError(), "preconditioner");
+}
+
+int precond_scale(rpb_ctx *ctx, int64_t N, const double *x, double *out, bool inverse)
+{
+    precond_scale_kernel<<<blas_grid(3 * N, ctx->num_sms), kBlasThreads, 0, ctx->stream>>>(x, ctx->ws.pc, 3 * N,
+                                                                                         inverse ? 1 : 0, out);
+    count_launches(1);
+    return cuda_fail(cudaGetLastError(), "preconditioner scale");
+}
+
 int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero)
 {
     cudaStream_t st = ctx->stream;
@@ -191,7 +247,7 @@ int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, do
 {
     bool zero = false;
     int rc;
-    if ((rc = lanczos_init(ctx, N, W, &zero))) return rc;
+    if ((rc = lanczos_precond_prepare(ctx, N, pos)) || (rc = lanczos_init(ctx, N, W, &zero))) return rc;
     if (zero) {
         if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "zero g"))) return rc;
         if (iters_out) *iters_out = 0;
@@ -223,7 +279,16 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
     double eps = -1.0;
     for (int k = 0; k < max_iter; ++k) {
         const double *vk = V + (size_t)k * ld;
-        if (!(k == 0 && first_done) && (rc = mobility_apply_impl(ctx, N, pos, vk, nullptr, w))) return rc;
+        if (!(k == 0 && first_done)) {
+            if (ctx->precond) {  // w = P M P v_k
+                if ((rc = precond_scale(ctx, N, vk, ctx->ws.pcx, false)) ||
+                    (rc = mobility_apply_impl(ctx, N, pos, ctx->ws.pcx, nullptr, w)) ||
+                    (rc = precond_scale(ctx, N, w, w, false)))
+                    return rc;
+            } else if ((rc = mobility_apply_impl(ctx, N, pos, vk, nullptr, w))) {
+                return rc;
+            }
+        }
         const int nv = k + 1;
         dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
         project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c1, nullptr);
@@ -248,6 +313,7 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
     }
     combine_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, m, lz + L.y, g);
     count_launches(1);
+    if (ctx->precond && (rc = precond_scale(ctx, N, g, g, true))) return rc;  // g = D^{1/2} y
     if ((rc = cuda_fail(cudaGetLastError(), "lanczos kernels"))) return rc;
     if (iters_out) *iters_out = m;
     if (err_out) *err_out = eps;

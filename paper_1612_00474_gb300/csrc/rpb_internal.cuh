@@ -152,6 +152,8 @@ struct Workspace {
     double *vec_f = nullptr;
     double *vec_g = nullptr;
     double *host_status = nullptr; // pinned host copy of the Lanczos status word
+    double *pc = nullptr;          // block-diagonal preconditioner D^{-1/2} (3 max_N), rpb_set_preconditioner
+    double *pcx = nullptr;         // a Krylov vector scaled by it
     // symmetric translation-translation pass (float32 contexts): schedule, row and column partials
     int *sym_index = nullptr;      // CTA table and segment table (4 ints each), row_seg, col_start
     size_t sym_index_ints = 0;
@@ -178,6 +180,7 @@ struct rpb_ctx {
     int sym_fused;     // products with torques also use the symmetric pass; env RPB_FP32_SYM_FUSED=0 off
     int sym_rhs2;      // a step's fused product and first Lanczos product share one pass; env RPB_FP32_SYM_RHS2=0 off
     double Lx = 0.0, Ly = 0.0;  // pseudo-periodic periods (0: unbounded in-plane), rpb_set_periodic
+    int precond = 0;            // Lanczos preconditioner (RPB_PRECOND_*), rpb_set_preconditioner
     int f32_slots[2] = {0, 0};  // resident CTAs of the float32 one-way pair kernels (tt, with torques)
     rpb::Workspace ws;
 };
@@ -232,8 +235,14 @@ int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t 
 int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol, int max_iter,
                  int *iters_out, double *err_out, int *converged_out);
 // The two halves of lanczos_impl: |W| and v_0 = W/|W| into ws.V (synchronises; *nw_zero when W = 0),
-// then the iterations; with first_done the first product M v_0 is already in ws.w.
+// then the iterations; with first_done the first product M v_0 is already in ws.w (with the
+// preconditioner on: P M P v_0, see lanczos_precond_prepare).
 int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero);
+// With ctx->precond set: P = D^{-1/2} at these positions into ws.pc (D: diagonal of the self blocks),
+// so that the iteration runs on P M P and returns g = D^{1/2} y.  precond_scale: out = x * P
+// elementwise (inverse: x / P, 0 where P = 0).
+int lanczos_precond_prepare(rpb_ctx *ctx, int64_t N, const double *pos);
+int precond_scale(rpb_ctx *ctx, int64_t N, const double *x, double *out, bool inverse);
 int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double tol, int max_iter, bool first_done,
                 int *iters_out, double *err_out, int *converged_out);
 int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift,

@@ -23,9 +23,10 @@ EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", 
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
            "rpb_launch_count", "rpb_mobility_apply_noalloc", "rpb_batch_create", "rpb_batch_destroy",
            "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step", "rpb_batch_run",
-           "rpb_set_periodic")
+           "rpb_set_periodic", "rpb_set_preconditioner")
 SCHEMES = {"AB": 0, "EM": 1}
 RFDS = {"centred": 0, "one-sided": 1}
+PRECONDITIONERS = {"none": 0, "block-diagonal": 1}
 NOALLOC_MAX_N = 16384
 
 
@@ -84,6 +85,7 @@ def load(build_if_missing=True):
     L.rpb_destroy.argtypes = [vp]
     L.rpb_set_stream.argtypes = [vp, vp]
     L.rpb_set_periodic.argtypes = [vp, d, d]
+    L.rpb_set_preconditioner.argtypes = [vp, i32]
     L.rpb_mobility_apply.argtypes = [vp, i64, vp, vp, vp, vp]
     L.rpb_lanczos_sqrt_apply.argtypes = [vp, i64, vp, vp, vp, d, i32, ctypes.POINTER(i32), ctypes.POINTER(d)]
     L.rpb_rfd_drift.argtypes = [vp, i64, vp, vp, d, vp]
@@ -203,6 +205,10 @@ class Context:
     def set_periodic(self, Lx, Ly):
         """Pseudo-periodic boundaries with periods (Lx, Ly); (0, 0) switches them off (rpb_set_periodic)."""
         _check(load().rpb_set_periodic(self._h, float(Lx), float(Ly)))
+
+    def set_preconditioner(self, kind):
+        """Lanczos preconditioner: "none" (default) or "block-diagonal" (rpb_set_preconditioner)."""
+        _check(load().rpb_set_preconditioner(self._h, PRECONDITIONERS[kind]))
 
     @staticmethod
     def _empty(n, like):
