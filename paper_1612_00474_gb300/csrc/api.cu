@@ -130,8 +130,6 @@ int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, 
     {
         const char *v = getenv("RPB_FP32_PAIR");
         c->fp32_variant = (v && strcmp(v, "scalar") == 0) ? 0 : 1;
-        const char *m = getenv("RPB_SYM_MINB");
-        c->sym_minb = m ? (strcmp(m, "5") == 0 ? 5 : 6) : 0;  // 0: each kernel form's own default
         const char *fu = getenv("RPB_FP32_SYM_FUSED");
         c->sym_fused = !(fu && strcmp(fu, "0") == 0);
     }

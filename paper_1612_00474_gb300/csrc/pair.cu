@@ -421,12 +421,24 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     float ks[NC], kc[NC];  // compensated per-tile sums of the target side
 #pragma unroll
     for (int q = 0; q < NC; ++q) ks[q] = kc[q] = 0.f;
+    // translation-translation forms: the next tile's sources are loaded into registers while the
+    // current tile is evaluated (the load latency is hidden behind the pair work)
+    constexpr bool PF = !TORQUE && !RHS2 && !PER;
+    float4 nsp = make_float4(1e18f, 0.f, 0.f, 0.f), nsf = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (PF && (seg.t0 - tb) * kTile + tid < Ni) {
+        const long long j0 = off + (seg.t0 - tb) * kTile + tid;
+        nsp = src[j0].p;
+        nsf = src[j0].f;
+    }
     for (int t = seg.t0; t < seg.t1; ++t) {
         const int lj = (t - tb) * kTile + tid;
         const long long j = off + lj;
         float4 sp_ = make_float4(1e18f, 0.f, 0.f, 0.f), sf_ = make_float4(1.f, 0.f, 0.f, 0.f);
         float4 st_ = make_float4(0.f, 0.f, 0.f, 0.f), sq_ = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lj < Ni) {
+        if (PF) {
+            sp_ = nsp;
+            sf_ = nsf;
+        } else if (lj < Ni) {
             sp_ = src[j].p;
             sf_ = src[j].f;
             if (TORQUE) st_ = src[j].t;
@@ -455,6 +467,14 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
             }
         }
         __syncthreads();
+        if (PF) {
+            nsp = make_float4(1e18f, 0.f, 0.f, 0.f);
+            nsf = make_float4(1.f, 0.f, 0.f, 0.f);
+            if (t + 1 < seg.t1 && lj + kTile < Ni) {
+                nsp = src[j + kTile].p;
+                nsf = src[j + kTile].f;
+            }
+        }
         // a batched suspension's last tile is ragged: the loops stop after its last live source (the
         // padding sources carry zero force, so what they would add is an exact zero; the column
         // partial slots of padding sources then hold stale values, which no output reads)
@@ -691,6 +711,8 @@ __global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_red
     }
 }
 
+constexpr int kTtMinBlocks = 4;     // resident CTAs per SM of the translation-translation form (up to 128 registers:
+                                    // four source pairs per step and the next tile's sources in flight)
 constexpr int kFusedMinBlocks = 4;  // resident CTAs per SM of the form with torques
 constexpr int kRhs2MinBlocks = 3;  // resident CTAs per SM of the two-right-hand-side form
 constexpr int kPerMinBlocks = 4;   // resident CTAs per SM of the pseudo-periodic forms
@@ -817,12 +839,8 @@ static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F,
         pair_f32x2_sym_kernel<kFusedMinBlocks, true><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs,
                                                                                       w.sym_tgt, w.sym_src);
     } else {
-        if (ctx->sym_minb == 6)
-            pair_f32x2_sym_kernel<6, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
-                                                                                 w.sym_src);
-        else
-            pair_f32x2_sym_kernel<5, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs, w.sym_tgt,
-                                                                                 w.sym_src);
+        pair_f32x2_sym_kernel<kTtMinBlocks, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs,
+                                                                                        w.sym_tgt, w.sym_src);
     }
     pair_sym_reduce_kernel<3><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
                                                              cs, N, pos, F, T, make_consts<double>(a), a,
@@ -997,7 +1015,7 @@ int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, 
         pair_f32x2_sym_kernel<kFusedMinBlocks, true, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
             src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
     else
-        pair_f32x2_sym_kernel<5, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
+        pair_f32x2_sym_kernel<kTtMinBlocks, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
             src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
     pair_sym_reduce_kernel<3, true><<<pl.ntiles, 3 * kTile, 0, st>>>(
         pl.tgt, pl.srcp, pl.index + pl.row_off, cs, n, pos, F, T, make_consts<double>(a), a, 1.0 / (8.0 * kPi * eta),

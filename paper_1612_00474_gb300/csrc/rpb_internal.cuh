@@ -176,7 +176,6 @@ struct rpb_ctx {
     int num_sms;
     int fp32_variant;  // float32 pair kernel: 1 = packed float32x2 (default), 0 = scalar; env RPB_FP32_PAIR
     int sym_enabled;   // float32 translation-translation products use the symmetric pass; env RPB_FP32_SYM=0 off
-    int sym_minb;      // symmetric tt form for 5 (default) or 6 resident CTAs per SM; env RPB_SYM_MINB=6
     int sym_fused;     // products with torques also use the symmetric pass; env RPB_FP32_SYM_FUSED=0 off
     int sym_rhs2;      // a step's fused product and first Lanczos product share one pass; env RPB_FP32_SYM_RHS2=0 off
     double Lx = 0.0, Ly = 0.0;  // pseudo-periodic periods (0: unbounded in-plane), rpb_set_periodic
