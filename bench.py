@@ -40,10 +40,10 @@ FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25  # dense FP64 rate of a GB300 (vector pipe)
 # DRAM bytes (read + write) of one launch of the symmetric translation-translation kernel at
 # N = 65536, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the
-# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command); 4.50 MB read (the
-# packed sources), 165.33 MB written (segment and source-column partials leaving L2).  Valid for
+# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command); 4.93 MB read (the
+# packed sources), 165.35 MB written (segment and source-column partials leaving L2).  Valid for
 # this kernel build only: reset to None when the kernel changes.
-SYM_TT_TRAFFIC_BYTES = {65536: 4.50e6 + 165.33e6}
+SYM_TT_TRAFFIC_BYTES = {65536: 4.93e6 + 165.35e6}
 SM_MAX_MHZ = 2070.0
 
 
