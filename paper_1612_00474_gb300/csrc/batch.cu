@@ -588,6 +588,13 @@ struct rpb_batch {
     cudaEvent_t join = nullptr;
     unsigned long long *d_unconv = nullptr;
     unsigned long long *h_unconv = nullptr;
+    // graph-replayed Lanczos: iterations after the first run inside conditional (IF) nodes of the
+    // graph, captured on `body`; d_iter_runs[k] counts how often iteration k ran (for the launch
+    // count), iter_launches[k] is the number of kernels of iteration k's body
+    cudaStream_t body = nullptr;
+    unsigned long long *d_iter_runs = nullptr;
+    unsigned long long *h_iter_runs = nullptr;
+    int iter_launches[kMaxIter] = {};
     // float32 products by the symmetric pass (both directions of a pair from one evaluation):
     // schedule and partial-sum scratch for the current batch sizes
     bool sym_enabled = false;
@@ -611,6 +618,9 @@ static void batch_free(rpb_batch *bt)
     for (void *p : host)
         if (p) cudaFreeHost(p);
     if (bt->d_unconv) cudaFree(bt->d_unconv);
+    if (bt->d_iter_runs) cudaFree(bt->d_iter_runs);
+    if (bt->h_iter_runs) cudaFreeHost(bt->h_iter_runs);
+    if (bt->body) cudaStreamDestroy(bt->body);
     batch_sym_free(bt->sym);
     if (bt->join) cudaEventDestroy(bt->join);
     if (bt->cap) cudaStreamDestroy(bt->cap);
@@ -737,15 +747,54 @@ static int batch_product(rpb_batch *bt, const double *pos, const double *F, cons
     return cuda_fail(cudaGetLastError(), "batch pair kernels");
 }
 
+// Inside a replayed graph: count this run of iteration k and, unless it is the last one, let the
+// conditional node of iteration k + 1 run only while some instance is still active.
+__global__ void batch_iter_kernel(cudaGraphConditionalHandle next, int has_next, const int *__restrict__ n_active,
+                                  unsigned long long *__restrict__ runs_k)
+{
+    *runs_k += 1ull;
+    if (has_next) cudaGraphSetConditional(next, *n_active > 0 ? 1u : 0u);
+}
+
+// Open a conditional (IF) node after the work captured so far on `st` and start capturing its body on
+// `body`; the node runs its body when `h` was set non-zero during this launch of the graph.
+static int begin_if_node(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle h)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t nd = 0;
+    int rc;
+    if ((rc = cuda_fail(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &nd), "capture info")))
+        return rc;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if ((rc = cuda_fail(cudaGraphAddNode(&node, g, deps, edges, nd, &p), "conditional node")) ||
+        (rc = cuda_fail(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+                        "capture dependencies")) ||
+        (rc = cuda_fail(cudaStreamBeginCaptureToGraph(body, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal),
+                        "body capture")))
+        return rc;
+    return RPB_OK;
+}
+
 // Lanczos for every instance at once; per-instance m, eps and convergence land in h_lz statuses.
 // graph == false: the host reads the number of still-active instances after every iteration and stops
 // when it reaches zero, then copies the per-instance statuses to h_lz.  graph == true (inside a CUDA
-// graph capture): exactly max_iter iterations are enqueued, with converged instances masked out of
-// every kernel, and nothing is read back.
+// graph capture): iteration 0 is captured as is and iterations 1 .. max_iter - 1 each inside a
+// conditional node that runs only while some instance is still active (the previous iteration's
+// last kernel sets its condition), so a replay does the iterations the step needs, at most max_iter;
+// converged instances are masked out of every kernel, and nothing is read back.
 static int batch_lanczos(rpb_batch *bt, const double *pos, const double *W, double *g, double tol, int max_iter,
                          bool graph = false)
 {
-    cudaStream_t st = bt->stream;
+    cudaStream_t main_st = bt->stream;
     const int B = bt->B;
     const int64_t total = bt->total;
     const size_t ld = (size_t)3 * bt->max_total;
@@ -753,46 +802,85 @@ static int batch_lanczos(rpb_batch *bt, const double *pos, const double *W, doub
     double *V = bt->V, *w = bt->vec[V_WORK];
     const int ge = grid_for(3 * total, bt->num_sms);
     int rc;
-    batch_dots_kernel<<<dim3(B, 1), kBThreads, 0, st>>>(W, 0, W, bt->d_inst, nullptr, total, B, bt->red);
-    batch_norm_init_kernel<<<(B + 127) / 128, 128, 0, st>>>(bt->red, B, bt->lz, bt->lz_stride, L.status, bt->d_active);
-    batch_scale_kernel<<<ge, 256, 0, st>>>(W, bt->d_inst, bt->d_inst_of, nullptr, total, bt->lz, bt->lz_stride, L.status,
-                                           ST_INV_NW, V);
+    cudaGraphConditionalHandle hnd[kMaxIter] = {};
+    if (graph) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        if ((rc = cuda_fail(cudaStreamGetCaptureInfo(main_st, &cs, nullptr, &cg, nullptr, nullptr, nullptr),
+                            "capture info")))
+            return rc;
+        for (int k = 1; k < max_iter; ++k)
+            if ((rc = cuda_fail(cudaGraphConditionalHandleCreate(&hnd[k], cg, 0u, cudaGraphCondAssignDefault),
+                                "conditional handle")))
+                return rc;
+    }
+    batch_dots_kernel<<<dim3(B, 1), kBThreads, 0, main_st>>>(W, 0, W, bt->d_inst, nullptr, total, B, bt->red);
+    batch_norm_init_kernel<<<(B + 127) / 128, 128, 0, main_st>>>(bt->red, B, bt->lz, bt->lz_stride, L.status,
+                                                                bt->d_active);
+    batch_scale_kernel<<<ge, 256, 0, main_st>>>(W, bt->d_inst, bt->d_inst_of, nullptr, total, bt->lz, bt->lz_stride,
+                                                L.status, ST_INV_NW, V);
     count_launches(3);
     for (int k = 0; k < max_iter; ++k) {
+        const bool cond = graph && k >= 1;
+        if (cond) {
+            if ((rc = begin_if_node(main_st, bt->body, hnd[k]))) return rc;
+            bt->stream = bt->body;
+        }
+        cudaStream_t st = bt->stream;
+        const uint64_t before = rpb_launch_count();
         const double *vk = V + (size_t)k * ld;
-        if ((rc = batch_product(bt, pos, vk, nullptr, w, bt->d_active))) return rc;
+        rc = batch_product(bt, pos, vk, nullptr, w, bt->d_active);
         const int nv = k + 1;
-        batch_dots_kernel<<<dim3(B, nv), kBThreads, 0, st>>>(V, ld, w, bt->d_inst, bt->d_active, total, B, bt->red);
-        batch_project_kernel<<<B, kBThreads, 0, st>>>(V, ld, w, bt->d_inst, bt->d_active, total, B, nv, bt->red, bt->lz,
-                                                      bt->lz_stride, L.c1, nullptr);
-        batch_dots_kernel<<<dim3(B, nv), kBThreads, 0, st>>>(V, ld, w, bt->d_inst, bt->d_active, total, B, bt->red);
-        batch_project_kernel<<<B, kBThreads, 0, st>>>(V, ld, w, bt->d_inst, bt->d_active, total, B, nv, bt->red, bt->lz,
-                                                      bt->lz_stride, L.c2, bt->norm2);
-        if ((rc = cuda_fail(cudaMemsetAsync(bt->d_nactive, 0, sizeof(int), st), "memset"))) return rc;
-        batch_tail_kernel<<<(B + 3) / 4, 128, 0, st>>>(bt->lz, bt->lz_stride, L, k, tol, bt->norm2, B, bt->d_active,
-                                                       bt->d_nactive);
-        count_launches(5);
-        if (!graph) {
-            if ((rc = cuda_fail(cudaMemcpyAsync(bt->h_nactive, bt->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st),
-                                "n_active copy")))
-                return rc;
-            if ((rc = cuda_fail(cudaStreamSynchronize(st), "batch lanczos iteration"))) return rc;
-            if (*bt->h_nactive == 0) break;
+        if (!rc) {
+            batch_dots_kernel<<<dim3(B, nv), kBThreads, 0, st>>>(V, ld, w, bt->d_inst, bt->d_active, total, B, bt->red);
+            batch_project_kernel<<<B, kBThreads, 0, st>>>(V, ld, w, bt->d_inst, bt->d_active, total, B, nv, bt->red,
+                                                          bt->lz, bt->lz_stride, L.c1, nullptr);
+            batch_dots_kernel<<<dim3(B, nv), kBThreads, 0, st>>>(V, ld, w, bt->d_inst, bt->d_active, total, B, bt->red);
+            batch_project_kernel<<<B, kBThreads, 0, st>>>(V, ld, w, bt->d_inst, bt->d_active, total, B, nv, bt->red,
+                                                          bt->lz, bt->lz_stride, L.c2, bt->norm2);
+            rc = cuda_fail(cudaMemsetAsync(bt->d_nactive, 0, sizeof(int), st), "memset");
         }
-        if (k + 1 < max_iter) {
-            batch_scale_kernel<<<ge, 256, 0, st>>>(w, bt->d_inst, bt->d_inst_of, bt->d_active, total, bt->lz,
-                                                   bt->lz_stride, L.status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
-            count_launches(1);
+        if (!rc) {
+            batch_tail_kernel<<<(B + 3) / 4, 128, 0, st>>>(bt->lz, bt->lz_stride, L, k, tol, bt->norm2, B,
+                                                           bt->d_active, bt->d_nactive);
+            count_launches(5);
+            if (graph) {
+                const bool has_next = k + 1 < max_iter;
+                batch_iter_kernel<<<1, 1, 0, st>>>(has_next ? hnd[k + 1] : 0ull, has_next ? 1 : 0, bt->d_nactive,
+                                                   bt->d_iter_runs + k);
+                count_launches(1);
+            } else {
+                if ((rc = cuda_fail(cudaMemcpyAsync(bt->h_nactive, bt->d_nactive, sizeof(int),
+                                                    cudaMemcpyDeviceToHost, st),
+                                    "n_active copy")))
+                    return rc;
+                if ((rc = cuda_fail(cudaStreamSynchronize(st), "batch lanczos iteration"))) return rc;
+                if (*bt->h_nactive == 0) break;
+            }
+            if (k + 1 < max_iter) {
+                batch_scale_kernel<<<ge, 256, 0, st>>>(w, bt->d_inst, bt->d_inst_of, bt->d_active, total, bt->lz,
+                                                       bt->lz_stride, L.status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
+                count_launches(1);
+            }
+            rc = cuda_fail(cudaGetLastError(), "batch lanczos kernels");
         }
+        if (cond) {
+            bt->iter_launches[k] = (int)(rpb_launch_count() - before);
+            cudaGraph_t body_graph = nullptr;
+            const int erc = cuda_fail(cudaStreamEndCapture(bt->body, &body_graph), "body capture end");
+            bt->stream = main_st;
+            if (!rc) rc = erc;
+        }
+        if (rc) return rc;
     }
-    batch_combine_kernel<<<ge, 256, 0, st>>>(V, ld, bt->d_inst_of, total, bt->lz, bt->lz_stride, L, g);
+    batch_combine_kernel<<<ge, 256, 0, main_st>>>(V, ld, bt->d_inst_of, total, bt->lz, bt->lz_stride, L, g);
     count_launches(1);
     if (graph) return cuda_fail(cudaGetLastError(), "batch lanczos kernels");
     if ((rc = cuda_fail(cudaMemcpyAsync(bt->h_lz, bt->lz, (size_t)B * bt->lz_stride * sizeof(double),
-                                        cudaMemcpyDeviceToHost, st),
+                                        cudaMemcpyDeviceToHost, main_st),
                         "status copy")))
         return rc;
-    return cuda_fail(cudaStreamSynchronize(st), "batch lanczos");
+    return cuda_fail(cudaStreamSynchronize(main_st), "batch lanczos");
 }
 
 // After a step replayed from a CUDA graph: advance every instance's step counter and count the
@@ -873,7 +961,11 @@ static int batch_run_impl(rpb_batch *bt, int B, const int64_t *N, double *const 
     cudaStream_t st = bt->stream;
     double **v = bt->vec;
     if ((rc = batch_gather(bt, 0, v[V_POS], 0)) || (rc = batch_gather(bt, 1, v[V_UP], 0))) return rc;
-    if ((rc = cuda_fail(cudaMemsetAsync(bt->d_unconv, 0, sizeof(unsigned long long), st), "memset"))) return rc;
+    if ((rc = cuda_fail(cudaMemsetAsync(bt->d_unconv, 0, sizeof(unsigned long long), st), "memset")) ||
+        (rc = cuda_fail(cudaMemsetAsync(bt->d_iter_runs, 0, kMaxIter * sizeof(unsigned long long), st), "memset")))
+        return rc;
+    for (int k = 0; k < kMaxIter; ++k) bt->iter_launches[k] = 0;
+    int per_step = 0;
     if (nsteps > 0) {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -881,8 +973,8 @@ static int batch_run_impl(rpb_batch *bt, int B, const int64_t *N, double *const 
         if ((rc = cuda_fail(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return rc;
         const int brc = batch_step_body(bt, dt, delta, tol, lanczos_iters, fp, true);
         const cudaError_t ec = cudaStreamEndCapture(st, &graph);
-        const int per_step = (int)(rpb_launch_count() - before);
-        count_launches(-per_step);  // captured, not executed
+        per_step = (int)(rpb_launch_count() - before);
+        count_launches(-per_step);  // captured, not executed (counted below from the runs)
         if (brc) {
             if (graph) cudaGraphDestroy(graph);
             return brc;
@@ -893,7 +985,6 @@ static int batch_run_impl(rpb_batch *bt, int B, const int64_t *N, double *const 
             return rc;
         }
         for (int s = 0; s < nsteps && !rc; ++s) rc = cuda_fail(cudaGraphLaunch(exec, st), "graph launch");
-        if (!rc) count_launches(per_step * nsteps);
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
         if (rc) return rc;
@@ -905,8 +996,19 @@ static int batch_run_impl(rpb_batch *bt, int B, const int64_t *N, double *const 
         (rc = cuda_fail(cudaMemcpyAsync(bt->h_unconv, bt->d_unconv, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                         st),
                         "count copy")) ||
+        (rc = cuda_fail(cudaMemcpyAsync(bt->h_iter_runs, bt->d_iter_runs, kMaxIter * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, st),
+                        "iteration count copy")) ||
         (rc = cuda_fail(cudaStreamSynchronize(st), "batch run")))
         return rc;
+    if (nsteps > 0) {  // kernels executed: the unconditional part every step, each iteration body per run
+        int64_t cond_part = 0, executed = 0;
+        for (int k = 1; k < kMaxIter; ++k) {
+            cond_part += bt->iter_launches[k];
+            executed += (int64_t)bt->iter_launches[k] * (int64_t)bt->h_iter_runs[k];
+        }
+        count_launches((int)((per_step - cond_part) * (int64_t)nsteps + executed));
+    }
     batch_read_stats(bt, tol, stats);
     if (unconverged) *unconverged = (int64_t)*bt->h_unconv;
     if (*bt->h_unconv && tol > 0.0) {
@@ -979,6 +1081,9 @@ int rpb_batch_create(rpb_batch **out, const rpb_params *p, int64_t max_total_N, 
               cudaMalloc(&bt->d_unconv, sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&bt->h_unconv, sizeof(unsigned long long)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&bt->body, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&bt->d_iter_runs, kMaxIter * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMallocHost(&bt->h_iter_runs, kMaxIter * sizeof(unsigned long long)) == cudaSuccess &&
               cudaEventCreateWithFlags(&bt->join, cudaEventDisableTiming) == cudaSuccess;
     for (double *&v : bt->vec) ok = ok && cudaMalloc(&v, vb) == cudaSuccess;
     if (!ok) {
