@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "pair_math.cuh"
+#include "sym_schedule.h"
 
 namespace rpb {
 
@@ -717,52 +718,6 @@ constexpr int kFusedMinBlocks = 4;  // resident CTAs per SM of the form with tor
 constexpr int kRhs2MinBlocks = 3;  // resident CTAs per SM of the two-right-hand-side form
 constexpr int kPerMinBlocks = 4;   // resident CTAs per SM of the pseudo-periodic forms
 
-// Upper-triangle schedule for N targets: the nb (nb + 1) / 2 units (b, t >= b) in row-major order
-// cut into ncta runs of equal length, each run split into segments at row ends.  ncta = 60 x SMs
-// (when there are that many units) fills whole waves at 4, 5 and 6 resident CTAs per SM, the
-// occupancies of the kernel's forms (two right-hand sides, with torques, translation only).
-// cta4: (s0, s1, 0, 0) per CTA; seg4: (b, t0, t1, 0) per segment, in unit order, so row b's segments
-// are [row_seg[b], row_seg[b + 1]); col_start[t]: first source-partial slot of column t.
-void sym_schedule(int64_t N, int num_sms, std::vector<int> &cta4, std::vector<int> &seg4, std::vector<int> &row_seg,
-                  std::vector<int> &col_start)
-{
-    const int nb = (int)((N + kTile - 1) / kTile);
-    const int64_t units = (int64_t)nb * (nb + 1) / 2;
-    int64_t ncta = std::min<int64_t>(units, 60 * (int64_t)num_sms);
-    const int64_t L = (units + ncta - 1) / ncta;
-    cta4.clear();
-    seg4.clear();
-    row_seg.assign(nb + 1, 0);
-    col_start.assign(nb, 0);
-    for (int t = 0; t < nb; ++t) col_start[t] = (int)((int64_t)t * (t - 1) / 2);
-    int b = 0, t = 0, nseg = 0;
-    int64_t left = units;
-    while (left > 0) {
-        int64_t k = std::min(L, left);
-        left -= k;
-        cta4.push_back(nseg);
-        while (k > 0) {
-            const int m = (int)std::min<int64_t>(k, nb - t);
-            if (t == b) row_seg[b] = nseg;
-            seg4.push_back(b);
-            seg4.push_back(t);
-            seg4.push_back(t + m);
-            seg4.push_back(0);
-            ++nseg;
-            t += m;
-            k -= m;
-            if (t == nb) {
-                ++b;
-                t = b;
-            }
-        }
-        cta4.push_back(nseg);
-        cta4.push_back(0);
-        cta4.push_back(0);
-    }
-    row_seg[nb] = nseg;
-}
-
 // Capacity of the schedule: at most kSymMaxCtaPerSm x SMs CTAs and that many plus nb segments.
 constexpr int kSymMaxCtaPerSm = 64;
 
@@ -793,7 +748,7 @@ static int sym_prepare(rpb_ctx *ctx, int N)
     if (w.sym_N == N) return RPB_OK;
     cudaStream_t st = ctx->stream;
     std::vector<int> cta4, seg4, row_seg, col_start;
-    sym_schedule(N, ctx->num_sms, cta4, seg4, row_seg, col_start);
+    sym_schedule(N, ctx->num_sms, kTile, cta4, seg4, row_seg, col_start);
     const size_t need = cta4.size() + seg4.size() + row_seg.size() + col_start.size();
     if (need > w.sym_index_ints || seg4.size() / 4 * 3 * kTile * sizeof(double) > w.sym_tgt_bytes) {
         set_error("internal: symmetric schedule larger than its scratch (N=%d)", N);
@@ -926,39 +881,17 @@ int batch_sym_plan(BatchSymPlan &pl, int B, const int64_t *N, cudaStream_t st, b
         return RPB_OK;
     }
     pl.valid = false;
+    BatchSchedule bs;
+    batch_sym_schedule(B, N, kTile, kBatchSegTiles, bs);
     std::vector<SymInst> si(B);
-    std::vector<int> seg4, row_seg, col_start, tile_inst;
-    int64_t off = 0, srows = 0;
-    int g = 0;
-    for (int k = 0; k < B; ++k) {
-        const int nb = (int)((N[k] + kTile - 1) / kTile);
-        si[k].off = off;
-        si[k].N = (int)N[k];
-        si[k].tile0 = g;
-        for (int r = 0; r < nb; ++r) {
-            row_seg.push_back((int)(seg4.size() / 4));
-            tile_inst.push_back(k);
-            for (int t0 = g + r; t0 < g + nb; t0 += kBatchSegTiles) {
-                seg4.push_back(g + r);
-                seg4.push_back(t0);
-                seg4.push_back(std::min(g + nb, t0 + kBatchSegTiles));
-                seg4.push_back(k);
-            }
-            col_start.push_back((int)(srows - g));  // slot of row b in column g + r: col_start + b
-            srows += r;
-        }
-        off += N[k];
-        g += nb;
-    }
+    for (int k = 0; k < B; ++k) si[k] = SymInst{(long long)bs.off[k], bs.n[k], bs.tile0[k]};
+    const std::vector<int> &seg4 = bs.seg4, &row_seg = bs.row_seg, &col_start = bs.col_start,
+                           &tile_inst = bs.tile_inst, &order = bs.cta_order;
     const int nseg = (int)(seg4.size() / 4);
-    row_seg.push_back(nseg);
-    const size_t src_bytes = (size_t)srows * 3 * kTile * sizeof(float);
+    const int g = bs.ntiles;
+    const size_t src_bytes = (size_t)bs.n_src_slots * 3 * kTile * sizeof(float);
     const size_t tgt_bytes = (size_t)nseg * 3 * kTile * sizeof(double);
     if (src_bytes + tgt_bytes > kBatchSymScratchLimit) return RPB_OK;  // one-way kernels instead
-    std::vector<int> order(nseg);
-    for (int q = 0; q < nseg; ++q) order[q] = q;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return seg4[4 * x + 2] - seg4[4 * x + 1] > seg4[4 * y + 2] - seg4[4 * y + 1]; });
     std::vector<int> host;
     host.reserve(4 * nseg + seg4.size() + row_seg.size() + col_start.size() + tile_inst.size());
     for (int q : order) {

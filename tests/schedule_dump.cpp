@@ -1,0 +1,49 @@
+// Prints the work lists of the symmetric pair pass (sym_schedule.h) as JSON for
+// tests/test_schedule_cpu.py.  usage: schedule_dump single N num_sms | schedule_dump batch N0 N1 ...
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "sym_schedule.h"
+
+static void dump(const char *name, const std::vector<int> &v, bool last = false)
+{
+    std::printf("\"%s\": [", name);
+    for (size_t i = 0; i < v.size(); ++i) std::printf(i ? ",%d" : "%d", v[i]);
+    std::printf("]%s", last ? "" : ", ");
+}
+
+int main(int argc, char **argv)
+{
+    const int tile = 128;
+    if (argc >= 4 && std::strcmp(argv[1], "single") == 0) {
+        std::vector<int> cta4, seg4, row_seg, col_start;
+        rpb::sym_schedule(std::atoll(argv[2]), std::atoi(argv[3]), tile, cta4, seg4, row_seg, col_start);
+        std::printf("{");
+        dump("cta4", cta4);
+        dump("seg4", seg4);
+        dump("row_seg", row_seg);
+        dump("col_start", col_start, true);
+        std::printf("}\n");
+        return 0;
+    }
+    if (argc >= 3 && std::strcmp(argv[1], "batch") == 0) {
+        std::vector<int64_t> N;
+        for (int i = 2; i < argc; ++i) N.push_back(std::atoll(argv[i]));
+        rpb::BatchSchedule s;
+        rpb::batch_sym_schedule((int)N.size(), N.data(), tile, 8, s);
+        std::printf("{\"tile0\": [");
+        for (size_t i = 0; i < s.tile0.size(); ++i) std::printf(i ? ",%d" : "%d", s.tile0[i]);
+        std::printf("], \"n_src_slots\": %lld, \"ntiles\": %d, ", (long long)s.n_src_slots, s.ntiles);
+        dump("seg4", s.seg4);
+        dump("row_seg", s.row_seg);
+        dump("col_start", s.col_start);
+        dump("tile_inst", s.tile_inst);
+        dump("cta_order", s.cta_order, true);
+        std::printf("}\n");
+        return 0;
+    }
+    std::fprintf(stderr, "usage: schedule_dump single N num_sms | schedule_dump batch N0 N1 ...\n");
+    return 2;
+}
