@@ -219,10 +219,11 @@ int rpb_batch_ab_step(rpb_batch *bt, int B, const int64_t *N, double *const *pos
 
 /* nsteps AB steps of every instance (as repeated rpb_batch_ab_step) with one gather and one scatter
  * of the state, the step captured once into a CUDA graph and replayed nsteps times with no host
- * synchronisation in between.  Inside the graph Lanczos runs exactly lanczos_iters iterations per
- * step with converged instances masked out (so lanczos_iters must cover the iteration count the
- * tolerance needs; *unconverged, if not NULL, receives the number of instance-steps that did not
- * reach tol, and RPB_ENOCONV is returned if it is nonzero with tol > 0).  steps: each instance's
+ * synchronisation in between.  Inside the graph each Lanczos iteration after the first is a
+ * conditional node that runs while some instance is still active (decided on the device), up to
+ * lanczos_iters iterations per step, with converged instances masked out (so lanczos_iters caps the
+ * iteration count the tolerance needs; *unconverged, if not NULL, receives the number of
+ * instance-steps that did not reach tol, and RPB_ENOCONV is returned if it is nonzero with tol > 0).  steps: each instance's
  * first step index (advanced on the device).  stats: the last step's statistics (B entries, or
  * NULL).  The work runs on a stream the batch context owns, ordered after the context's stream;
  * the call returns when it is complete. */
