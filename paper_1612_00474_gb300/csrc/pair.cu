@@ -291,11 +291,14 @@ __global__ void __launch_bounds__(kPairThreads, 6) pair_f32x2_kernel(const SrcF3
 // same amount of work; a run is split at row ends into segments (b, t0, t1).  Per segment the CTA
 // keeps the 128 targets of block b in registers; the diagonal tile (t = b) is done one-directionally
 // with the self pair excluded; every other tile gives both u_i (target side, registers) and v_j
-// (source side): each lane's v_j for four sources are combined across the warp by a reduce-scatter
-// (two exchange levels, then three butterfly levels), the four warps' sums are added at the end of
-// the tile, and the tile's source sums go to src_part[col_start[t] + b].  Each segment's target sums
-// go to tgt_part[segment].  The reduce kernel adds, for each sphere, its row's segment partials and
-// its column's source partials in a fixed order.
+// (source side): each lane evaluates four source pairs (eight sources) per step, and their v_j are
+// combined across the warp by a reduce-scatter (three exchange levels, then two butterfly levels;
+// the order in which a lane takes the pairs and a swapped copy of the tile make it select-free), the
+// four warps' sums are added at the end of the tile, and the tile's source sums go to
+// src_part[col_start[t] + b].  Each segment's target sums go to tgt_part[segment].  The reduce
+// kernel adds, for each sphere, its row's segment partials and its column's source partials in a
+// fixed order.  The translation-translation forms load the next tile's sources while a tile is
+// evaluated.  The work lists come from sym_schedule.h.
 struct SymCta {
     int s0, s1, pad0, pad1;  // segments [s0, s1)
 };
