@@ -29,21 +29,35 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "wall-RPY matvec Gpairs/s; BD steps/s at N=65536; p50/p99 solve latency"
-# Algorithmic flops of the pair block as the kernels evaluate its closed form (FMA = 2 flops, multiply
-# or add = 1; the two reciprocal square roots per pair are MUFU operations, not counted):
-FLOPS_TT = 106      # one direction, translation-translation: geometry 8 + coefficients 63 + application 35
-FLOPS_FUSED = 147   # one direction with the translation-rotation coupling (+ 41)
-FLOPS_SYM = 135     # per unordered pair, block evaluated once and applied both ways: geometry 8 +
-                    # coefficients with the |R| powers folded in 70 + target application 30 + source 27
-OPS_SYM = 88        # the same as FP32 operations (an FMA, a multiply or an add is one lane operation)
+
+
+def read_flops(path=os.path.join(ROOT, "FLOPS.md")):
+    """The fixed per-pair work of the pair block (FLOPS.md): {key: count} for its FLOPS_* / MUFU_* rows."""
+    out = {}
+    with open(path) as f:
+        for line in f:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 2 and (cells[0].startswith("FLOPS_") or cells[0].startswith("MUFU_")):
+                out[cells[0]] = int(cells[1])
+    return out
+
+
+_FLOPS = read_flops()
+FLOPS_TT = _FLOPS["FLOPS_TT"]          # one direction, translation-translation, per ordered pair
+FLOPS_FUSED = _FLOPS["FLOPS_FUSED"]    # one direction with the translation-rotation coupling
+FLOPS_SYM = _FLOPS["FLOPS_SYM"]        # per unordered pair, applied both ways (reciprocity)
+# FP32 lane operations (an FMA, a multiply or an add is one) that the symmetric translation-translation
+# kernel executes per unordered pair, counted from its source (pair_offsets_x2 6, pair_block_x2 34,
+# tt_apply_target 16, tt_apply_source 16); a property of the kernel, used only for the pipe-occupancy
+# view beside the flop roofline.
+OPS_SYM_KERNEL = 72
 FP32_LANES_PER_SM = 128
-FP64_NOMINAL_TFLOPS = 1.25  # dense FP64 rate of a GB300 (vector pipe)
+FP64_NOMINAL_TFLOPS = 1.25  # dense FP64 rate of a GB300 (vector pipe), for context
 # DRAM bytes (read + write) of one launch of the symmetric translation-translation kernel at
 # N = 65536, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the
-# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command); 4.93 MB read (the
-# packed sources), 165.35 MB written (segment and source-column partials leaving L2).  Valid for
-# this kernel build only: reset to None when the kernel changes.
-SYM_TT_TRAFFIC_BYTES = {65536: 4.93e6 + 165.35e6}
+# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command).  Valid for one
+# kernel build only: empty until the current build is captured.
+SYM_TT_TRAFFIC_BYTES = {}
 SM_MAX_MHZ = 2070.0
 
 
@@ -159,6 +173,20 @@ def clocks_stop(proc):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def measure_peaks(device_index):
+    """Measured fused-multiply-add rates of this GPU (rpb_fma_peak), with the clocks sampled meanwhile."""
+    from paper_1612_00474_gb300 import rpb
+
+    clk = clocks_start(device_index)
+    out = {}
+    for kind in ("ffma2", "ffma", "dfma"):
+        t, ms = rpb.fma_peak(kind)
+        out[kind + "_tflops"] = t
+        out[kind + "_ms"] = ms
+    out["clocks"] = clocks_stop(clk)
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -240,6 +268,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.ab_step(q, Up, step, seed, **kw)
         step += 1
     torch.cuda.synchronize()
+    peaks = measure_peaks(local_rank)
     if dist:
         dist.barrier()
 
@@ -326,12 +355,17 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0:
         sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        fp32_peak = max(peaks["ffma2_tflops"], peaks["ffma_tflops"])
         if args.precision == "fp32":
-            peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-            peak_basis = f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"
+            peak = fp32_peak
+            peak_basis = (f"measured on this GPU by rpb_fma_peak: FFMA2 {peaks['ffma2_tflops']:.1f}, FFMA "
+                          f"{peaks['ffma_tflops']:.1f} TFLOP/s (best of 3 launches on all SMs; nominal "
+                          f"{sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz = "
+                          f"{sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12:.1f})")
         else:
-            peak = FP64_NOMINAL_TFLOPS
-            peak_basis = "nominal GB300 FP64 rate (no measured FP64 figure)"
+            peak = peaks["dfma_tflops"]
+            peak_basis = (f"measured on this GPU by rpb_fma_peak: DFMA {peak:.3f} TFLOP/s (nominal "
+                          f"{FP64_NOMINAL_TFLOPS})")
         sym = args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256
         diag = float(N) * 128
         if args.periodic and sym:  # nine images of each unordered pair once, both ways
@@ -352,10 +386,11 @@ def run_ours(args, rank, world, local_rank):
             # the FP32 pipe's operation rate: one lane operation per lane per clock, whether an FMA, a
             # multiply or an add (a third of the pair's operations are multiplies and adds that cannot be
             # fused, so the flop fraction understates how busy the pipe is)
-            ops = (9.0 if args.periodic else 1.0) * OPS_SYM * (float(N) * N - diag) / 2
-            ops_peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-            ops_view = {"per_unordered_pair": OPS_SYM, "achieved": ops / t_tt / 1e12, "peak": ops_peak,
-                        "unit": "Top/s", "frac": ops / t_tt / 1e12 / ops_peak}
+            ops = (9.0 if args.periodic else 1.0) * OPS_SYM_KERNEL * (float(N) * N - diag) / 2
+            ops_peak = fp32_peak / 2  # one FMA is one lane operation
+            ops_view = {"per_unordered_pair": OPS_SYM_KERNEL, "basis": "the kernel's own operation count",
+                        "achieved": ops / t_tt / 1e12, "peak": ops_peak, "unit": "Top/s",
+                        "frac": ops / t_tt / 1e12 / ops_peak}
         value = pairs / total_s / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
@@ -380,6 +415,7 @@ def run_ours(args, rank, world, local_rank):
                          "traffic": SYM_TT_TRAFFIC_BYTES.get(N) if sym and not args.periodic else None,
                          "traffic_unit": "bytes per launch",
                          "fp32_ops": ops_view},
+            "peaks": peaks,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": "Gpairs/s", "h2d_bytes_per_step": 2 * 3 * N * 8,
                     "d2h_bytes_per_step": 2 * 3 * N * 8},

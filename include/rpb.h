@@ -231,6 +231,19 @@ int rpb_batch_run(rpb_batch *bt, int B, const int64_t *N, double *const *pos, do
                   const int64_t *steps, const uint64_t *seeds, int nsteps, double dt, double delta, double tol,
                   int lanczos_iters, const rpb_force_params *fp, rpb_step_stats *stats, int64_t *unconverged);
 
+/* Measured arithmetic peak of the current device (a measurement aid: the paper has none).  Runs
+ * independent chains of fused multiply-adds on every SM -- packed float32x2 (RPB_PEAK_FFMA2, the
+ * instruction the float32 pair kernels use), scalar float32 (RPB_PEAK_FFMA) or float64
+ * (RPB_PEAK_DFMA) -- for about 40 ms per launch, one warm-up launch and three timed ones with CUDA
+ * events on stream (a cudaStream_t, NULL = legacy default stream), and returns the best rate in
+ * *tflops (an FMA counts 2 flops) and that launch's duration in *ms (may be NULL).  It runs at
+ * whatever clocks the GPU is at (it changes no setting).  Synchronises the stream.  RPB_EINVAL for
+ * an unknown kind or a null tflops, RPB_ECUDA for CUDA failures. */
+#define RPB_PEAK_FFMA2 0
+#define RPB_PEAK_FFMA 1
+#define RPB_PEAK_DFMA 2
+int rpb_fma_peak(int kind, void *stream, double *tflops, double *ms);
+
 /* Largest N accepted by rpb_mobility_apply_noalloc. */
 #define RPB_NOALLOC_MAX_N 16384
 
@@ -247,7 +260,11 @@ int rpb_batch_run(rpb_batch *bt, int B, const int64_t *N, double *const *pos, do
  *   - p: a, eta and precision are used (kT is ignored).  stream: a cudaStream_t (NULL = legacy
  *     default stream), on the current device.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *     with that device current, and the call looks it up again whenever the device's CUDA
+ *     context has changed since (after cudaDeviceReset, or a primary context released and created
+ *     anew, the array may have moved).  Make that first call, and the first call after such a
+ *     change, outside any stream capture: made while the stream is being captured, it returns
+ *     RPB_EINVAL with a message saying so.
  *   - Every call on a device shares the one array and leaves its contents behind; each call
  *     overwrites all of the scratch it reads, so nothing has to be cleared in between.  Calls
  *     whose kernels may overlap on the GPU (different streams, or different host threads) race on

@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "grid_plan.h"
 #include "pair_math.cuh"
 #include "sym_schedule.h"
 
@@ -368,7 +369,8 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     constexpr int SW = G == 4 ? P + 4 : P + 2;
     __shared__ float4 sA[SW + P], sB[SW + P], sC[SW + P], sD[SW + P];
     __shared__ float4 sE[TORQUE ? SW + P : 1];
-    __shared__ float2 sG[TORQUE ? SW + P : 1];
+    __shared__ float4 sG[TORQUE ? SW + P : 1];  // (T_z, T_z', 6 z_j, 6 z_j')
+    __shared__ float4 sZ[SW + P];                // (-2 z_j, -2 z_j', -4 z_j^2, -4 z_j'^2)
     __shared__ float4 sP[RHS2 ? SW + P : 1];
     __shared__ float2 sQ[RHS2 ? SW + P : 1];
     __shared__ float sv[4][NC][kTile];
@@ -391,6 +393,7 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     float *fD = reinterpret_cast<float *>(sD);
     float *fE = reinterpret_cast<float *>(sE);
     float *fG = reinterpret_cast<float *>(sG);
+    float *fZ = reinterpret_cast<float *>(sZ);
     float *fP = reinterpret_cast<float *>(sP);
     float *fQ = reinterpret_cast<float *>(sQ);
     for (int sg = cd.s0; sg < cd.s1; ++sg) {
@@ -422,6 +425,7 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
     const float2 Gx = make_float2(tf.y, tf.y), Gy = make_float2(tf.z, tf.z), Gz = make_float2(tf.w, tf.w);
     const float2 Hx = make_float2(th.x, th.x), Hy = make_float2(th.y, th.y), Hz = make_float2(th.z, th.z);
     const float2 Qx = make_float2(tq.x, tq.x), Qy = make_float2(tq.y, tq.y), Qz = make_float2(tq.z, tq.z);
+    const float2 six_zi = make_float2(6.f * tf.x, 6.f * tf.x);
     float ks[NC], kc[NC];  // compensated per-tile sums of the target side
 #pragma unroll
     for (int q = 0; q < NC; ++q) ks[q] = kc[q] = 0.f;
@@ -459,10 +463,13 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
             fC[o4 + 2] = sf_.y;
             fD[o4] = sf_.z;
             fD[o4 + 2] = sf_.w;
+            fZ[o4] = -2.f * sf_.x;
+            fZ[o4 + 2] = -4.f * (sf_.x * sf_.x);
             if (TORQUE) {
                 fE[o4] = st_.x;
                 fE[o4 + 2] = st_.y;
-                fG[o2] = st_.z;
+                fG[o4] = st_.z;
+                fG[o4 + 2] = 6.f * sf_.x;
             }
             if (RHS2) {
                 fP[o4] = sq_.x;
@@ -491,7 +498,7 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
             for (int k = 0; k < kend; ++k) {
                 const float4 a = sA[k], b = sB[k], cc = sC[k], d = sD[k];
                 const float4 e = TORQUE ? sE[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float2 g = TORQUE ? sG[k] : zero2;
+                const float2 g = TORQUE ? make_float2(sG[k].x, sG[k].y) : zero2;
                 float2 rx0 = add2(sub2(txh, make_float2(a.x, a.y)), sub2(txl, make_float2(b.x, b.y)));
                 float2 ry0 = add2(sub2(tyh, make_float2(a.z, a.w)), sub2(tyl, make_float2(b.z, b.w)));
                 if (PER) {
@@ -536,7 +543,10 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                     const int kh = G == 2 ? k + (h ? k1 : k0) : k + (h ^ pk) + swz;
                     const float4 a = sA[kh], cc = sC[kh], d = sD[kh];
                     const float4 e = TORQUE ? sE[kh] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float2 g = TORQUE ? sG[kh] : zero2;
+                    const float4 g4 = TORQUE ? sG[kh] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float2 g = make_float2(g4.x, g4.y), six_zj = make_float2(g4.z, g4.w);
+                    const float4 zf = sZ[kh];
+                    const float2 m2zj = make_float2(zf.x, zf.y), m4zj2 = make_float2(zf.z, zf.w);
                     const float4 pv = RHS2 ? sP[kh] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float2 pz = RHS2 ? sQ[kh] : zero2;
                     const float2 zj = make_float2(cc.x, cc.y);
@@ -544,7 +554,8 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                         float2 rx, ry, rz, rho2, r2;
                         const bool close =
                             pair_offsets_x2(txh, tyh, txl, tyl, tz2, zj, a, &sB[kh], c, rx, ry, rz, rho2, r2);
-                        pair_sym_x2<TORQUE, RHS2>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
+                        pair_sym_x2<TORQUE, RHS2>(rx, ry, rz, rho2, r2, close, tz2, zj, m2zj, m4zj2, six_zi, six_zj,
+                                                  make_float2(cc.z, cc.w),
                                                   make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
                                                   make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c,
                                                   u[0], u[1], u[2], v[h][0], v[h][1], v[h][2],
@@ -567,7 +578,8 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
                             const float2 r2 = fma2(rz, rz, rho2);
                             const bool close = __any_sync(0xffffffffu, r2.x < c.four_a2 || r2.y < c.four_a2);
                             float2 vx, vy, vz;
-                            pair_sym_x2<TORQUE>(rx, ry, rz, rho2, r2, close, tz2, zj, make_float2(cc.z, cc.w),
+                            pair_sym_x2<TORQUE>(rx, ry, rz, rho2, r2, close, tz2, zj, m2zj, m4zj2, six_zi, six_zj,
+                                                make_float2(cc.z, cc.w),
                                                 make_float2(d.x, d.y), make_float2(d.z, d.w), Gx, Gy, Gz,
                                                 make_float2(e.x, e.y), make_float2(e.z, e.w), g, Hx, Hy, Hz, c,
                                                 u[0], u[1], u[2], vx, vy, vz);
@@ -1212,55 +1224,9 @@ __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, 
     U[2 * N + i] = k * uz;
 }
 
-static int target_blocks(int num_sms)
-{
-    return num_sms * 8;
-}
-
-constexpr int64_t kMaxSplitsF32 = 16;  // source chunks of a float32 one-way product
-
 void pair_grid(int64_t N, int num_sms, int precision, int slots, int *splits, int64_t *chunk)
 {
-    const int64_t tiles = (N + kTile - 1) / kTile;
-    int64_t S = (target_blocks(num_sms) + tiles - 1) / tiles;
-    if (precision == RPB_FP64) {
-        // Float64 runs at a small fraction of the float32 rate on this part, so even a small product
-        // is spread over every SM: source chunks may be shorter than a tile (multiples of 4 sources;
-        // the float64 kernel finds its own sphere by index, not by tile alignment).
-        if (S > (N + 3) / 4) S = (N + 3) / 4;
-        if (S < 1) S = 1;
-        int64_t ch = ((N + S - 1) / S + 3) / 4 * 4;
-        *chunk = ch;
-        *splits = (int)((N + ch - 1) / ch);
-        return;
-    }
-    // float32 kernels evaluate whole 128-source tiles and rely on tile-aligned chunks
-    auto chunk_of = [&](int64_t s) { return std::max<int64_t>(kTile, ((N + s - 1) / s + kTile - 1) / kTile * kTile); };
-    if (slots > 0) {
-        // The grid's CTAs do nearly equal work, so they run in waves of `slots` (the resident CTAs of
-        // the whole GPU) and the kernel takes about (number of waves) x (one CTA's time, which is
-        // proportional to its chunk).  Take the split count minimising that product; a larger one
-        // only if it saves over 1%.
-        auto cost = [&](int64_t s) {
-            const int64_t ch = chunk_of(s), sp = (N + ch - 1) / ch;
-            return (double)((tiles * sp + slots - 1) / slots) * (double)ch;
-        };
-        const int64_t smax = std::min<int64_t>(kMaxSplitsF32, tiles);
-        S = 1;
-        double best = cost(1);
-        for (int64_t s2 = 2; s2 <= smax; ++s2) {
-            const double l = cost(s2);
-            if (l < 0.99 * best) {
-                best = l;
-                S = s2;
-            }
-        }
-    } else {
-        if (S > tiles) S = tiles;
-        if (S < 1) S = 1;
-    }
-    *chunk = chunk_of(S);
-    *splits = (int)((N + *chunk - 1) / *chunk);
+    pair_grid_plan(N, num_sms, precision == RPB_FP64, slots, kTile, splits, chunk);
 }
 
 // Resident CTAs over the whole GPU of the float32 one-way kernels (translation only, with torques).
@@ -1714,6 +1680,8 @@ int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_para
 // scratch (packed sources, then the per-chunk partial sums) in a fixed array of the library's device
 // image instead of a context's cudaMalloc'd workspace.  The array is created with the module on
 // every device that loads the library and lives until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 namespace rpb {
@@ -1727,11 +1695,58 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
-static void *g_noalloc_ptr[kNoAllocMaxDevices];
-static int g_noalloc_sms[kNoAllocMaxDevices];
+// Per device: the context the address was looked up in (its process-unique id), the address, the SM
+// count.  A context destroyed and created again (cudaDeviceReset, or a primary context released and
+// retained anew) loads the module again, and the array may then live elsewhere: the id tells.
+struct NoAllocSlot {
+    unsigned long long ctx_id;
+    void *ptr;
+    int sms;
+};
+static NoAllocSlot g_noalloc[kNoAllocMaxDevices];
 
-// Device address of the scratch array on the current device (looked up once per device).
-static int noalloc_setup(void **ptr, int *sms)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Process-unique id of the calling thread's current CUDA context (driver entry points through the
+// runtime, so the library needs no link against the driver library).
+static int current_ctx_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    int rc;
+    if (!get_current || !get_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0 = cudaDriverEntryPointSymbolNotFound, q1 = q0;
+        if ((rc = cuda_fail(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0),
+                            "cudaGetDriverEntryPointByVersion(cuCtxGetCurrent)")))
+            return rc;
+        if ((rc = cuda_fail(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1),
+                            "cudaGetDriverEntryPointByVersion(cuCtxGetId)")))
+            return rc;
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1) {
+            set_error("the CUDA driver offers no cuCtxGetCurrent / cuCtxGetId");
+            return RPB_ECUDA;
+        }
+        get_current = (CtxGetCurrentFn)f0;
+        get_id = (CtxGetIdFn)f1;
+    }
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) {
+        set_error("no current CUDA context");
+        return RPB_ECUDA;
+    }
+    if (get_id(c, id) != CUDA_SUCCESS) {
+        set_error("cuCtxGetId failed");
+        return RPB_ECUDA;
+    }
+    return RPB_OK;
+}
+
+// Device address of the scratch array in the current context (looked up once per device and
+// context).  The lookup is refused while `st` is being captured into a graph: it runs host-side
+// runtime calls that have no place in a capture.
+static int noalloc_setup(cudaStream_t st, void **ptr, int *sms)
 {
     int dev = 0;
     int rc;
@@ -1740,17 +1755,29 @@ static int noalloc_setup(void **ptr, int *sms)
         set_error("device ordinal %d outside [0, %d)", dev, kNoAllocMaxDevices);
         return RPB_EINVAL;
     }
+    // (a runtime call on the stream: it also makes the device's context current if nothing has yet)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((rc = cuda_fail(cudaStreamIsCapturing(st, &cs), "cudaStreamIsCapturing"))) return rc;
+    unsigned long long id = 0;
+    if ((rc = current_ctx_id(&id))) return rc;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocSlot &sl = g_noalloc[dev];
+    if (!sl.ptr || sl.ctx_id != id) {
+        if (cs != cudaStreamCaptureStatusNone) {
+            set_error("rpb_mobility_apply_noalloc: the first call on a device (or after its context was "
+                      "recreated) must not be made while the stream is being captured");
+            return RPB_EINVAL;
+        }
         void *p = nullptr;
         if ((rc = cuda_fail(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)"))) return rc;
         int n = 0;
         if ((rc = cuda_fail(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev), "SM count"))) return rc;
-        g_noalloc_sms[dev] = n;
-        g_noalloc_ptr[dev] = p;
+        sl.ctx_id = id;
+        sl.ptr = p;
+        sl.sms = n;
     }
-    *ptr = g_noalloc_ptr[dev];
-    *sms = g_noalloc_sms[dev];
+    *ptr = sl.ptr;
+    *sms = sl.sms;
     return RPB_OK;
 }
 
@@ -1790,15 +1817,10 @@ extern "C" int rpb_mobility_apply_noalloc(int64_t N64, const double *pos, const 
     void *base = nullptr;
     int sms = 0;
     int rc;
-    if ((rc = noalloc_setup(&base, &sms))) return rc;
+    if ((rc = noalloc_setup(st, &base, &sms))) return rc;
     int splits;
     int64_t chunk;
-    pair_grid(N64, sms, p->precision, 0, &splits, &chunk);
-    const int64_t max_splits = kNoAllocPartialElems / (3 * N64);
-    if (splits > max_splits) {
-        chunk = ((N64 + max_splits - 1) / max_splits + kTile - 1) / kTile * kTile;
-        splits = (int)((N64 + chunk - 1) / chunk);
-    }
+    noalloc_grid_plan(N64, sms, p->precision == RPB_FP64, kTile, kNoAllocPartialElems, &splits, &chunk);
     double *part = (double *)((unsigned char *)base + kNoAllocSrcBytes);
     const int pb = 256;
     const dim3 grid((unsigned)((N + kPairThreads - 1) / kPairThreads), (unsigned)splits);

@@ -225,47 +225,67 @@ __device__ __forceinline__ void pair_velocity_f32(float rx, float ry, float zi, 
 }
 
 // ---- two pairs per lane with packed float32x2 arithmetic (FFMA2/FMUL2/FADD2 on sm_100+)
-// The same formulation as pair_velocity_f32, evaluated for two sources at once: every quantity is a
-// float2 whose halves belong to two independent pairs, so one packed instruction does the work of
-// two scalar ones.  Constants are passed as float2 pairs in the kernel parameters.
+// Every quantity is a float2 whose halves belong to two independent pairs, so one packed instruction
+// does the work of two scalar ones.  Constants are passed as float2 pairs in the kernel parameters.
+//
+// Coefficient form.  With u = 1/|R|, s = u^2, Z = R_z^2 and the closed form of pair_velocity, the wall
+// coefficients are polynomials in s whose coefficients depend on the heights only:
+//   A = -1 + s X_A,           X_A = p + s (q - (10/3) a^4 s Z),   p = -2 z_i z_j - 2a^2/3,  q = 2a^2 Z + 2a^4/3
+//   B = -1 + s X_B,           2 X_B = -6 p + s (-20 a^2 Z - (20/3) a^4 + (140/3) a^4 s Z)
+//   C = u (2 z_j + R_z s X_C), X_C = -2 X_B + (20/3) a^4 s
+//   D = u (2 z_j - (20/3) a^4 R_z s^2)
+//   E = s Ehat,               Ehat = -4 z_j^2 + s (-4 a^2 Z - (8/3) a^4 + 20 a^4 s Z)
+// so the coefficients of the application (free-space c1, c2 included) are
+//   c_F = c1 + A u = (c1 - u) + u^3 X_A,    B3 = B u^3 = u^5 X_B - u^3,
+//   C3 = C u^2 = 2 u^3 z_j - u^5 R_z (2 X_B) + (20/3) a^4 u^7 R_z,   D3 = D u^2 = 2 u^3 z_j - (20/3) a^4 u^7 R_z,
+//   E3 = E u = u^3 Ehat,  and the block is  M F = c_F F + c2 (r.F) r + (B3 w + C3 F_z) R + (D3 w + E3 F_z) z_hat,
+// w = R.F (R and r share their in-plane part).  c_F + E3 multiplies F_z in the z component, so it is
+// formed once (c_FE).  Per source, -2 z_j and -4 z_j^2 (and 6 z_j for the rotation coupling) come
+// precomputed with the source.
+//   Translation-rotation, with c_t the free-space rotlet coefficient (|r|^-3, or the overlap form) and
+// dcp = c_t - u^3:  u += T_y m2 - dcp T_z r_y - kappa tz3 r_x,  u_y += -T_x m2 + dcp T_z r_x - kappa tz3 r_y,
+// u_z += tz3 (dcp - 2a^2 u^5 - kappa R_z), where tz3 = T_x r_y - T_y r_x, m2 = dcp r_z + 2a^2 u^5 R_z and
+// kappa = u^5 (6 z_i - 10 a^2 s R_z).  The reversed pair (source velocity from the target's torque) has
+// r -> -r and z_i <-> z_j in m2 and kappa.
 struct X2Consts {
-    float2 one, two_3_a2, m_two_a2, a2;
+    float2 two_3_a2, m_two_a2, two_a2;    // 2a^2/3, -2a^2, 2a^2
+    float2 m2_3_a2, two_3_a4;             // -2a^2/3, 2a^4/3
+    float2 m10_3_a4, c140_3_a4, m20_a2;   // -(10/3) a^4, (140/3) a^4, -20 a^2
+    float2 m20_3_a4, c20_3_a4, m6;        // -(20/3) a^4, (20/3) a^4, -6
+    float2 m4_a2, m8_3_a4, c20_a4;        // -4 a^2, -(8/3) a^4, 20 a^4
+    float2 half, m10_a2;                  // 1/2, -10 a^2
     float lo_r2;  // squared distance below which the low parts of the positions are added (float32 kernels)
-    float2 m10_3, c2_3, two, m2_3, m1, c70_3, m10, m6, m140_3, c40_3, c20, m4, c12, m20_3, m8_3, c6;
     float four_a2, near_c1, near_r, near_c2, near_tr, near_tr_r;
 };
 
 inline X2Consts make_x2_consts(double a)
 {
     auto p = [](double v) { return make_float2((float)v, (float)v); };
+    const double a2 = a * a, a4 = a2 * a2;
     X2Consts c;
-    c.one = p(1.0);
-    c.two_3_a2 = p(2.0 * a * a / 3.0);
-    c.m_two_a2 = p(-2.0 * a * a);
-    c.a2 = p(a * a);
-    c.m10_3 = p(-10.0 / 3.0);
-    c.c2_3 = p(2.0 / 3.0);
-    c.two = p(2.0);
-    c.m2_3 = p(-2.0 / 3.0);
-    c.m1 = p(-1.0);
-    c.c70_3 = p(70.0 / 3.0);
-    c.m10 = p(-10.0);
+    c.two_3_a2 = p(2.0 * a2 / 3.0);
+    c.m_two_a2 = p(-2.0 * a2);
+    c.two_a2 = p(2.0 * a2);
+    c.m2_3_a2 = p(-2.0 * a2 / 3.0);
+    c.two_3_a4 = p(2.0 * a4 / 3.0);
+    c.m10_3_a4 = p(-10.0 * a4 / 3.0);
+    c.c140_3_a4 = p(140.0 * a4 / 3.0);
+    c.m20_a2 = p(-20.0 * a2);
+    c.m20_3_a4 = p(-20.0 * a4 / 3.0);
+    c.c20_3_a4 = p(20.0 * a4 / 3.0);
     c.m6 = p(-6.0);
-    c.m140_3 = p(-140.0 / 3.0);
-    c.c40_3 = p(40.0 / 3.0);
-    c.c20 = p(20.0);
-    c.m4 = p(-4.0);
-    c.c12 = p(12.0);
-    c.m20_3 = p(-20.0 / 3.0);
-    c.m8_3 = p(-8.0 / 3.0);
-    c.c6 = p(6.0);
-    c.four_a2 = (float)(4.0 * a * a);
+    c.m4_a2 = p(-4.0 * a2);
+    c.m8_3_a4 = p(-8.0 * a4 / 3.0);
+    c.c20_a4 = p(20.0 * a4);
+    c.half = p(0.5);
+    c.m10_a2 = p(-10.0 * a2);
+    c.four_a2 = (float)(4.0 * a2);
     c.near_c1 = (float)(4.0 / (3.0 * a));
     c.near_r = (float)(9.0 / (32.0 * a));
-    c.near_c2 = (float)(1.0 / (8.0 * a * a));
-    c.near_tr = (float)(1.0 / (2.0 * a * a * a));
+    c.near_c2 = (float)(1.0 / (8.0 * a2));
+    c.near_tr = (float)(1.0 / (2.0 * a2 * a));
     c.near_tr_r = (float)(3.0 / (8.0 * a));
-    c.lo_r2 = (float)(100.0 * a * a);
+    c.lo_r2 = (float)(100.0 * a2);
     return c;
 }
 
@@ -290,11 +310,15 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
     return __fadd2_rn(a, neg2(b));
 }
 
-__device__ __forceinline__ void near_fix(float r2, float inv_r, const X2Consts &c, float &c1, float &c2, float &ct)
+// Overlap branch (r < 2a) of the free-space coefficients for one pair: c1 - u (u = 1/|R| of the
+// image), c2 and the rotlet coefficient c_t.  r^2 below the smallest normal float is a coincident
+// pair (the self form).
+__device__ __forceinline__ void near_fix(float r2, float inv_r, float u, const X2Consts &c, float &c1mu, float &c2,
+                                         float &ct)
 {
     const float r = r2 >= kMinNormal ? r2 * inv_r : 0.f;
     const float ir = r2 >= kMinNormal ? inv_r : 0.f;
-    c1 = c.near_c1 * fmaf(-c.near_r, r, 1.f);
+    c1mu = fmaf(c.near_c1, fmaf(-c.near_r, r, 1.f), -u);
     c2 = c.near_c2 * ir;
     ct = c.near_tr * fmaf(-c.near_tr_r, r, 1.f);
 }
@@ -324,12 +348,145 @@ __device__ __forceinline__ bool pair_offsets_x2(float2 txh, float2 tyh, float2 t
     return close;
 }
 
-// pair_velocity_x2 from the geometry of pair_offsets_x2 (close: some lane may overlap).
+// Coefficients of a translation-translation pair block (packed pairs): M F = c_F F + c2 (r.F) r +
+// (B3 w + C3 F_z) R + (D3 w + E3 F_z) z_hat with w = R.F, c_FE = c_F + E3.
+struct TTBlock {
+    float2 rx, ry, rz, Rz, c2, cF, cFE, B3, C3, D3;
+};
+// Direction-independent factors of the translation-rotation coupling: dcp = c_t - u^3; m2, kappa and
+// the z factor (dcp - 2a^2 u^5 - kappa R_z) for the pair (t) and the reversed pair (s).
+struct TRBlock {
+    float2 dcp, m2t, m2s, kt, ks, zt, zs;
+};
+
+// The block of two pairs from their geometry: in-plane offset (rx, ry), rz = zi - zj, rho2 = rx^2 +
+// ry^2, r2 = rho2 + rz^2; `close` true (warp-uniformly) when some lane may hold an overlapping pair
+// (r < 2a), the overlap branch then being taken per pair.  m2zj = -2 z_j, m4zj2 = -4 z_j^2; six_zi,
+// six_zj = 6 z_i, 6 z_j (read only with TORQUE; six_zj only for the reversed pair's factors).
+template <bool TORQUE>
+__device__ __forceinline__ void pair_block_x2(float2 rx, float2 ry, float2 rz, float2 rho2, float2 r2, bool close,
+                                              float2 zi, float2 zj, float2 m2zj, float2 m4zj2, float2 six_zi,
+                                              float2 six_zj, const X2Consts &c, TTBlock &m, TRBlock &tb)
+{
+    const float2 ir = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+    const float2 Rz = add2(zi, zj);
+    const float2 Z = mul2(Rz, Rz);
+    const float2 R2 = add2(rho2, Z);
+    const float2 u = make_float2(rsqrt_ftz(R2.x), rsqrt_ftz(R2.y));
+    const float2 ir2 = mul2(ir, ir);
+    const float2 ir3 = mul2(ir, ir2);
+    float2 c1mu = fma2(c.two_3_a2, ir3, sub2(ir, u));  // (1 + 2a^2/(3 r^2)) / r - u
+    float2 c2 = fma2(c.m_two_a2, mul2(ir3, ir2), ir3);  // (1 - 2a^2/r^2) / r^3
+    float2 ct = ir3;
+    if (close) {
+        if (r2.x < c.four_a2) near_fix(r2.x, ir.x, u.x, c, c1mu.x, c2.x, ct.x);
+        if (r2.y < c.four_a2) near_fix(r2.y, ir.y, u.y, c, c1mu.y, c2.y, ct.y);
+    }
+    const float2 s = mul2(u, u);
+    const float2 u3 = mul2(s, u);
+    const float2 u5 = mul2(u3, s);
+    const float2 sZ = mul2(s, Z);
+    const float2 p = fma2(m2zj, zi, c.m2_3_a2);
+    const float2 q = fma2(c.two_a2, Z, c.two_3_a4);
+    const float2 XA = fma2(s, fma2(sZ, c.m10_3_a4, q), p);
+    const float2 XB2 = fma2(s, fma2(sZ, c.c140_3_a4, fma2(c.m20_a2, Z, c.m20_3_a4)), mul2(c.m6, p));
+    const float2 Eh = fma2(s, fma2(sZ, c.c20_a4, fma2(c.m4_a2, Z, c.m8_3_a4)), m4zj2);
+    const float2 b2 = mul2(u5, XB2);
+    const float2 T2 = neg2(mul2(u3, m2zj));  // 2 u^3 z_j
+    const float2 u5Rz = mul2(u5, Rz);
+    const float2 u7Rz = mul2(u5Rz, s);
+    const float2 cF = fma2(u3, XA, c1mu);
+    m.rx = rx;
+    m.ry = ry;
+    m.rz = rz;
+    m.Rz = Rz;
+    m.c2 = c2;
+    m.cF = cF;
+    m.cFE = fma2(u3, Eh, cF);
+    m.B3 = fma2(b2, c.half, neg2(u3));
+    m.C3 = fma2(neg2(Rz), b2, fma2(u7Rz, c.c20_3_a4, T2));
+    m.D3 = fma2(u7Rz, c.m20_3_a4, T2);
+    if (TORQUE) {
+        const float2 dcp = sub2(ct, u3);
+        const float2 dcprz = mul2(dcp, rz);
+        const float2 w10 = mul2(c.m10_a2, u7Rz);
+        const float2 d2 = fma2(c.m_two_a2, u5, dcp);
+        tb.dcp = dcp;
+        tb.m2t = fma2(u5Rz, c.two_a2, dcprz);
+        tb.m2s = fma2(u5Rz, c.two_a2, neg2(dcprz));
+        tb.kt = fma2(six_zi, u5, w10);
+        tb.ks = fma2(six_zj, u5, w10);
+        tb.zt = fma2(neg2(Rz), tb.kt, d2);
+        tb.zs = fma2(neg2(Rz), tb.ks, d2);
+    }
+}
+
+// target side: u += M_ij F_j
+__device__ __forceinline__ void tt_apply_target(const TTBlock &m, float2 Fx, float2 Fy, float2 Fz, float2 &ux,
+                                                float2 &uy, float2 &uz)
+{
+    const float2 pF = fma2(m.rx, Fx, mul2(m.ry, Fy));
+    const float2 w = fma2(m.Rz, Fz, pF);
+    const float2 k2 = mul2(m.c2, fma2(m.rz, Fz, pF));
+    const float2 ke = fma2(m.B3, w, mul2(m.C3, Fz));
+    const float2 kk = add2(k2, ke);
+    ux = fma2(m.cF, Fx, fma2(kk, m.rx, ux));
+    uy = fma2(m.cF, Fy, fma2(kk, m.ry, uy));
+    uz = fma2(m.cFE, Fz, fma2(k2, m.rz, fma2(ke, m.Rz, fma2(m.D3, w, uz))));
+}
+// source side: v = M_ij^T G_i (C3 and D3 exchanged)
+__device__ __forceinline__ void tt_apply_source(const TTBlock &m, float2 Gx, float2 Gy, float2 Gz, float2 &vx,
+                                                float2 &vy, float2 &vz)
+{
+    const float2 pF = fma2(m.rx, Gx, mul2(m.ry, Gy));
+    const float2 w = fma2(m.Rz, Gz, pF);
+    const float2 k2 = mul2(m.c2, fma2(m.rz, Gz, pF));
+    const float2 ke = fma2(m.B3, w, mul2(m.D3, Gz));
+    const float2 kk = add2(k2, ke);
+    vx = fma2(m.cF, Gx, mul2(kk, m.rx));
+    vy = fma2(m.cF, Gy, mul2(kk, m.ry));
+    vz = fma2(m.cFE, Gz, fma2(k2, m.rz, fma2(ke, m.Rz, mul2(m.C3, w))));
+}
+// target side of the translation-rotation coupling: u += M_tr(i, j) T_j
+__device__ __forceinline__ void tr_apply_target(const TTBlock &m, const TRBlock &tb, float2 Tx, float2 Ty, float2 Tz,
+                                                float2 &ux, float2 &uy, float2 &uz)
+{
+    const float2 tz3 = fma2(Tx, m.ry, neg2(mul2(Ty, m.rx)));
+    const float2 dTz = mul2(tb.dcp, Tz);
+    const float2 kt = mul2(tb.kt, tz3);
+    ux = fma2(Ty, tb.m2t, fma2(neg2(dTz), m.ry, fma2(neg2(kt), m.rx, ux)));
+    uy = fma2(neg2(Tx), tb.m2t, fma2(dTz, m.rx, fma2(neg2(kt), m.ry, uy)));
+    uz = fma2(tz3, tb.zt, uz);
+}
+// source side: v += M_tr(j, i) H_i (the reversed pair: r -> -r, z_i <-> z_j)
+__device__ __forceinline__ void tr_apply_source(const TTBlock &m, const TRBlock &tb, float2 Hx, float2 Hy, float2 Hz,
+                                                float2 &vx, float2 &vy, float2 &vz)
+{
+    const float2 tau = fma2(Hx, m.ry, neg2(mul2(Hy, m.rx)));
+    const float2 dHz = mul2(tb.dcp, Hz);
+    const float2 ks = mul2(tb.ks, tau);
+    vx = fma2(Hy, tb.m2s, fma2(dHz, m.ry, fma2(neg2(ks), m.rx, vx)));
+    vy = fma2(neg2(Hx), tb.m2s, fma2(neg2(dHz), m.rx, fma2(neg2(ks), m.ry, vy)));
+    vz = fma2(neg2(tau), tb.zs, vz);
+}
+
+// Target velocity of two sources (one-way), from the geometry of pair_offsets_x2 (close: some lane
+// may overlap); the per-source factors are formed here.  In units of 1/(8 pi eta); F, T with s_j.
 template <bool TORQUE>
 __device__ __forceinline__ void pair_velocity_x2_geo(float2 rx, float2 ry, float2 rz, float2 rho2, float2 r2,
                                                      bool close, float2 zi, float2 zj, float2 Fx, float2 Fy,
                                                      float2 Fz, float2 Tx, float2 Ty, float2 Tz, const X2Consts &c,
-                                                     float2 &ux, float2 &uy, float2 &uz);
+                                                     float2 &ux, float2 &uy, float2 &uz)
+{
+    const float2 zj2 = add2(zj, zj);
+    const float2 six = make_float2(6.f, 6.f);
+    TTBlock m;
+    TRBlock tb;
+    pair_block_x2<TORQUE>(rx, ry, rz, rho2, r2, close, zi, zj, neg2(zj2), neg2(mul2(zj2, zj2)), mul2(six, zi),
+                          make_float2(0.f, 0.f), c, m, tb);
+    tt_apply_target(m, Fx, Fy, Fz, ux, uy, uz);
+    if (TORQUE) tr_apply_target(m, tb, Tx, Ty, Tz, ux, uy, uz);
+}
 
 template <bool TORQUE>
 __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi, float2 zj, float2 Fx, float2 Fy,
@@ -343,152 +500,28 @@ __device__ __forceinline__ void pair_velocity_x2(float2 rx, float2 ry, float2 zi
     pair_velocity_x2_geo<TORQUE>(rx, ry, rz, rho2, r2, close, zi, zj, Fx, Fy, Fz, Tx, Ty, Tz, c, ux, uy, uz);
 }
 
-template <bool TORQUE>
-__device__ __forceinline__ void pair_velocity_x2_geo(float2 rx, float2 ry, float2 rz, float2 rho2, float2 r2,
-                                                     bool close, float2 zi, float2 zj, float2 Fx, float2 Fy,
-                                                     float2 Fz, float2 Tx, float2 Ty, float2 Tz, const X2Consts &c,
-                                                     float2 &ux, float2 &uy, float2 &uz)
-{
-    const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-    const float2 inv_r2 = mul2(inv_r, inv_r);
-    const float2 ir3 = mul2(inv_r, inv_r2);
-    float2 c1 = fma2(c.two_3_a2, ir3, inv_r);  // (1 + 2a^2/(3 r^2)) / r
-    float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
-    float2 ct = ir3;
-    if (close) {
-        if (r2.x < c.four_a2) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
-        if (r2.y < c.four_a2) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
-    }
-    const float2 Rz = add2(zi, zj);
-    const float2 R2 = fma2(Rz, Rz, rho2);
-    const float2 invR = make_float2(rsqrt_ftz(R2.x), rsqrt_ftz(R2.y));
-    const float2 invR2 = mul2(invR, invR);
-    const float2 ez = mul2(Rz, invR);
-    const float2 t = mul2(zj, invR);
-    const float2 s = mul2(c.a2, invR2);
-    const float2 ez2 = mul2(ez, ez), t2 = mul2(t, t), et = mul2(ez, t), s2 = mul2(s, s);
-    const float2 d = sub2(t2, et);
-    const float2 A = fma2(s2, fma2(c.m10_3, ez2, c.c2_3), fma2(s, fma2(c.two, ez2, c.m2_3), fma2(c.two, d, c.m1)));
-    const float2 B = fma2(s2, fma2(c.c70_3, ez2, c.m10_3), fma2(s, fma2(c.m10, ez2, c.two), fma2(c.m6, d, c.m1)));
-    const float2 C = fma2(ez, fma2(s2, fma2(c.m140_3, ez2, c.c40_3), mul2(s, fma2(c.c20, ez2, c.m4))),
-                          mul2(t, fma2(c.c12, sub2(et, ez2), c.two)));
-    const float2 D = fma2(c.m20_3, mul2(s2, ez), add2(t, t));
-    const float2 E = fma2(s2, fma2(c.c20, ez2, c.m8_3), mul2(c.m4, fma2(s, ez2, t2)));
-    const float2 pF = fma2(rx, Fx, mul2(ry, Fy));
-    const float2 q = mul2(fma2(Rz, Fz, pF), invR);
-    const float2 k2 = mul2(c2, fma2(rz, Fz, pF));
-    const float2 ke = mul2(fma2(B, q, mul2(C, Fz)), invR2);
-    const float2 kz = mul2(fma2(D, q, mul2(E, Fz)), invR);
-    const float2 cF = fma2(A, invR, c1);
-    const float2 kk = add2(k2, ke);
-    ux = fma2(cF, Fx, fma2(kk, rx, ux));
-    uy = fma2(cF, Fy, fma2(kk, ry, uy));
-    uz = fma2(cF, Fz, fma2(k2, rz, fma2(ke, Rz, add2(uz, kz))));
-    if (TORQUE) {
-        const float2 p = mul2(invR2, invR);
-        const float2 dcp = sub2(ct, p);
-        const float2 m1 = fma2(ct, rz, neg2(mul2(p, Rz)));
-        const float2 tz3 = fma2(Tx, ry, neg2(mul2(Ty, rx)));
-        const float2 se = mul2(s, ez);
-        const float2 m2 = fma2(add2(t, se), add2(invR2, invR2), m1);
-        const float2 ce = fma2(c.m10, se, mul2(c.c6, sub2(ez, t)));
-        const float2 w = mul2(neg2(tz3), invR);
-        const float2 cw = mul2(mul2(ce, w), p);
-        const float2 dTz = mul2(dcp, Tz);
-        ux = fma2(Ty, m2, fma2(neg2(dTz), ry, fma2(cw, rx, ux)));
-        uy = fma2(neg2(Tx), m2, fma2(dTz, rx, fma2(cw, ry, uy)));
-        uz = fma2(dcp, tz3, fma2(cw, Rz, fma2(mul2(add2(s, s), invR2), w, uz)));
-    }
-}
-
 // Both directions of a pair block, two pairs per lane (packed float32x2).  Reciprocity of the
 // mobility (M_ji = M_ij^T) lets one evaluation of the pair geometry serve the target
-// (u_i += M_ij F_j, accumulated) and the source (v_j = M_ji F_i, returned): the free-space
-// translation block is symmetric, and the transposed wall block swaps the roles of C and D.
+// (u_i += M_ij F_j, accumulated) and the source (v_j = M_ji G_i, returned): the free-space
+// translation block is symmetric, and the transposed wall block swaps the roles of C3 and D3.
 // TORQUE adds the translation-rotation coupling both ways: u_i += M_tr(i,j) T_j and
-// v_j += M_tr(j,i) H_i.  For the reversed pair the in-plane offset and the height difference change
-// sign, the image height z_i + z_j, |R|, s, e_z and the rotlet coefficient are unchanged, and
-// t' = z~_i / |R| replaces t = z~_j / |R|.
-// Coefficients of a translation-translation pair block (packed pairs) and its two applications.
-// With w = R.F = R_z F_z + r_x F_x + r_y F_y (R and r share their in-plane part) the wall terms are
-// (B w / |R|^3 + C F_z / |R|^2) R and (D w / |R|^2 + E F_z / |R|) z_hat, so the inverse powers of |R|
-// are folded into the coefficients once per pair: B3 = B/|R|^3, C2 = C/|R|^2, D2 = D/|R|^2, E1 = E/|R|.
-struct TTBlock {
-    float2 rx, ry, rz, Rz, c2, cF, B3, C2, D2, E1;
-};
-// target side: u += M_ij F_j
-__device__ __forceinline__ void tt_apply_target(const TTBlock &m, float2 Fx, float2 Fy, float2 Fz, float2 &ux,
-                                                float2 &uy, float2 &uz)
-{
-    const float2 pF = fma2(m.rx, Fx, mul2(m.ry, Fy));
-    const float2 w = fma2(m.Rz, Fz, pF);
-    const float2 k2 = mul2(m.c2, fma2(m.rz, Fz, pF));
-    const float2 ke = fma2(m.B3, w, mul2(m.C2, Fz));
-    const float2 kz = fma2(m.D2, w, mul2(m.E1, Fz));
-    const float2 kk = add2(k2, ke);
-    ux = fma2(m.cF, Fx, fma2(kk, m.rx, ux));
-    uy = fma2(m.cF, Fy, fma2(kk, m.ry, uy));
-    uz = fma2(m.cF, Fz, fma2(k2, m.rz, fma2(ke, m.Rz, add2(uz, kz))));
-}
-// source side: v = M_ij^T G_i (C and D exchanged)
-__device__ __forceinline__ void tt_apply_source(const TTBlock &m, float2 Gx, float2 Gy, float2 Gz, float2 &vx,
-                                                float2 &vy, float2 &vz)
-{
-    const float2 pF = fma2(m.rx, Gx, mul2(m.ry, Gy));
-    const float2 w = fma2(m.Rz, Gz, pF);
-    const float2 k2 = mul2(m.c2, fma2(m.rz, Gz, pF));
-    const float2 ke = fma2(m.B3, w, mul2(m.D2, Gz));
-    const float2 kz = fma2(m.C2, w, mul2(m.E1, Gz));
-    const float2 kk = add2(k2, ke);
-    vx = fma2(m.cF, Gx, mul2(kk, m.rx));
-    vy = fma2(m.cF, Gy, mul2(kk, m.ry));
-    vz = fma2(m.cF, Gz, fma2(k2, m.rz, fma2(ke, m.Rz, kz)));
-}
-
-// F: source loads, G: target loads; T: source torques, H: target torques.
-// The caller gives the pair geometry: in-plane offset (rx, ry), rz = zi - zj, rho2 = rx^2 + ry^2,
-// r2 = rho2 + rz^2, and `close`, true (warp-uniformly) when some lane of the warp may hold an
-// overlapping pair (r < 2a); the overlap branch is then taken per lane.
+// v_j += M_tr(j,i) H_i.  F, T: source loads; G, H: target loads.  Per-source factors m2zj = -2 z_j,
+// m4zj2 = -4 z_j^2, six_zj = 6 z_j and the target's six_zi = 6 z_i come precomputed.
 // RHS2: a second translation-translation right-hand side applied with the same block, P (sources)
 // and Q (targets) -> u2 (target side, accumulated) and v2 (source side, returned).
 template <bool TORQUE, bool RHS2 = false>
 __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, float2 rho2, float2 r2, bool close,
-                                            float2 zi, float2 zj, float2 Fx, float2 Fy, float2 Fz, float2 Gx,
+                                            float2 zi, float2 zj, float2 m2zj, float2 m4zj2, float2 six_zi,
+                                            float2 six_zj, float2 Fx, float2 Fy, float2 Fz, float2 Gx,
                                             float2 Gy, float2 Gz, float2 Tx, float2 Ty, float2 Tz, float2 Hx,
                                             float2 Hy, float2 Hz, const X2Consts &c, float2 &ux, float2 &uy,
                                             float2 &uz, float2 &vx, float2 &vy, float2 &vz, float2 Px = {},
                                             float2 Py = {}, float2 Pz = {}, float2 Qx = {}, float2 Qy = {},
                                             float2 Qz = {}, float2 *u2 = nullptr, float2 *v2 = nullptr)
 {
-    const float2 inv_r = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-    const float2 inv_r2 = mul2(inv_r, inv_r);
-    const float2 ir3 = mul2(inv_r, inv_r2);
-    float2 c1 = fma2(c.two_3_a2, ir3, inv_r);  // (1 + 2a^2/(3 r^2)) / r
-    float2 c2 = mul2(ir3, fma2(c.m_two_a2, inv_r2, c.one));
-    float2 ct = ir3;
-    if (close) {
-        if (r2.x < c.four_a2) near_fix(r2.x, inv_r.x, c, c1.x, c2.x, ct.x);
-        if (r2.y < c.four_a2) near_fix(r2.y, inv_r.y, c, c1.y, c2.y, ct.y);
-    }
-    const float2 Rz = add2(zi, zj);
-    const float2 R2 = fma2(Rz, Rz, rho2);
-    const float2 invR = make_float2(rsqrt_ftz(R2.x), rsqrt_ftz(R2.y));
-    const float2 invR2 = mul2(invR, invR);
-    const float2 ez = mul2(Rz, invR);
-    const float2 t = mul2(zj, invR);
-    const float2 s = mul2(c.a2, invR2);
-    const float2 ez2 = mul2(ez, ez), t2 = mul2(t, t), et = mul2(ez, t), s2 = mul2(s, s);
-    const float2 d = sub2(t2, et);
-    const float2 A = fma2(s2, fma2(c.m10_3, ez2, c.c2_3), fma2(s, fma2(c.two, ez2, c.m2_3), fma2(c.two, d, c.m1)));
-    const float2 B = fma2(s2, fma2(c.c70_3, ez2, c.m10_3), fma2(s, fma2(c.m10, ez2, c.two), fma2(c.m6, d, c.m1)));
-    const float2 C = fma2(ez, fma2(s2, fma2(c.m140_3, ez2, c.c40_3), mul2(s, fma2(c.c20, ez2, c.m4))),
-                          mul2(t, fma2(c.c12, sub2(et, ez2), c.two)));
-    const float2 D = fma2(c.m20_3, mul2(s2, ez), add2(t, t));
-    const float2 E = fma2(s2, fma2(c.c20, ez2, c.m8_3), mul2(c.m4, fma2(s, ez2, t2)));
-    const float2 cF = fma2(A, invR, c1);
-    const float2 invR3 = mul2(invR2, invR);
-    const float2 C2 = mul2(C, invR2);
-    const TTBlock m{rx, ry, rz, Rz, c2, cF, mul2(B, invR3), C2, mul2(D, invR2), mul2(E, invR)};
+    TTBlock m;
+    TRBlock tb;
+    pair_block_x2<TORQUE>(rx, ry, rz, rho2, r2, close, zi, zj, m2zj, m4zj2, six_zi, six_zj, c, m, tb);
     tt_apply_target(m, Fx, Fy, Fz, ux, uy, uz);
     tt_apply_source(m, Gx, Gy, Gz, vx, vy, vz);
     if (RHS2) {
@@ -496,40 +529,8 @@ __device__ __forceinline__ void pair_sym_x2(float2 rx, float2 ry, float2 rz, flo
         tt_apply_source(m, Qx, Qy, Qz, v2[0], v2[1], v2[2]);
     }
     if (TORQUE) {
-        // the rotation coupling of pair_velocity_x2 (c_t T x r - p T x R + |R|^-2 [...]), with the
-        // factors that do not depend on the direction computed once
-        const float2 p = invR3;
-        const float2 dcp = sub2(ct, p);
-        const float2 ctrz = mul2(ct, rz), pRz = mul2(p, Rz);
-        const float2 se = mul2(s, ez);
-        const float2 i2 = add2(invR2, invR2);
-        const float2 s2i = mul2(add2(s, s), invR2);
-        const float2 ce0 = fma2(c.m10, se, mul2(c.c6, ez));  // c_e = ce0 - 6 t
-        {  // target side, source torque T_j
-            const float2 m1 = sub2(ctrz, pRz);
-            const float2 tz3 = fma2(Tx, ry, neg2(mul2(Ty, rx)));
-            const float2 m2 = fma2(add2(t, se), i2, m1);
-            const float2 ce = fma2(c.m6, t, ce0);
-            const float2 w = mul2(neg2(tz3), invR);
-            const float2 cw = mul2(mul2(ce, w), p);
-            const float2 dTz = mul2(dcp, Tz);
-            ux = fma2(Ty, m2, fma2(neg2(dTz), ry, fma2(cw, rx, ux)));
-            uy = fma2(neg2(Tx), m2, fma2(dTz, rx, fma2(cw, ry, uy)));
-            uz = fma2(dcp, tz3, fma2(cw, Rz, fma2(s2i, w, uz)));
-        }
-        {  // source side, target torque H_i, reversed pair
-            const float2 tr = mul2(zi, invR);
-            const float2 m1 = neg2(add2(ctrz, pRz));
-            const float2 tz3 = fma2(Hy, rx, neg2(mul2(Hx, ry)));
-            const float2 m2 = fma2(add2(tr, se), i2, m1);
-            const float2 ce = fma2(c.m6, tr, ce0);
-            const float2 w = mul2(neg2(tz3), invR);
-            const float2 cw = mul2(mul2(ce, w), p);
-            const float2 dTz = mul2(dcp, Hz);
-            vx = fma2(Hy, m2, fma2(dTz, ry, fma2(neg2(cw), rx, vx)));
-            vy = fma2(neg2(Hx), m2, fma2(neg2(dTz), rx, fma2(neg2(cw), ry, vy)));
-            vz = fma2(dcp, tz3, fma2(cw, Rz, fma2(s2i, w, vz)));
-        }
+        tr_apply_target(m, tb, Tx, Ty, Tz, ux, uy, uz);
+        tr_apply_source(m, tb, Hx, Hy, Hz, vx, vy, vz);
     }
 }
 

@@ -23,7 +23,7 @@ EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", 
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
            "rpb_launch_count", "rpb_mobility_apply_noalloc", "rpb_batch_create", "rpb_batch_destroy",
            "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step", "rpb_batch_run",
-           "rpb_set_periodic", "rpb_set_preconditioner")
+           "rpb_set_periodic", "rpb_set_preconditioner", "rpb_fma_peak")
 SCHEMES = {"AB": 0, "EM": 1}
 RFDS = {"centred": 0, "one-sided": 1}
 PRECONDITIONERS = {"none": 0, "block-diagonal": 1}
@@ -100,6 +100,7 @@ def load(build_if_missing=True):
     L.rpb_launch_count.argtypes = []
     L.rpb_launch_count.restype = ctypes.c_uint64
     L.rpb_mobility_apply_noalloc.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp]
+    L.rpb_fma_peak.argtypes = [i32, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
     pi64 = ctypes.POINTER(i64)
     L.rpb_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), i64, i32, i32, vp]
     L.rpb_batch_destroy.argtypes = [vp]
@@ -123,6 +124,16 @@ def last_error():
 def launch_count():
     """Kernel launches the library has enqueued so far (rpb_launch_count)."""
     return int(load().rpb_launch_count())
+
+
+PEAK_KINDS = {"ffma2": 0, "ffma": 1, "dfma": 2}
+
+
+def fma_peak(kind="ffma2"):
+    """Measured fused-multiply-add rate of the current device (rpb_fma_peak): (TFLOP/s, ms per launch)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().rpb_fma_peak(PEAK_KINDS[kind], _stream(), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 def mobility_apply_noalloc(pos, F=None, T=None, a=1.0, eta=1.0, precision="fp64", out=None):

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <vector>
 
+#include "grid_plan.h"
 #include "sym_schedule.h"
 
 static void dump(const char *name, const std::vector<int> &v, bool last = false)
@@ -17,6 +18,26 @@ static void dump(const char *name, const std::vector<int> &v, bool last = false)
 int main(int argc, char **argv)
 {
     const int tile = 128;
+    if (argc >= 6 && std::strcmp(argv[1], "noalloc") == 0) {
+        // noalloc max_N max_sms max_partial_elems fp64: every (N, SM count) plan, one line each when it
+        // breaks a bound ("N sms splits chunk"), then "ok" or "bad"
+        const long long maxN = std::atoll(argv[2]);
+        const int maxs = std::atoi(argv[3]);
+        const long long cap = std::atoll(argv[4]);
+        const bool fp64 = std::atoi(argv[5]) != 0;
+        long long bad = 0;
+        for (long long N = 1; N <= maxN; ++N)
+            for (int sms = 1; sms <= maxs; sms += (sms < 160 ? 1 : 37)) {
+                int splits = 0;
+                int64_t chunk = 0;
+                rpb::noalloc_grid_plan(N, sms, fp64, tile, cap, &splits, &chunk);
+                const bool ok = splits >= 1 && (long long)splits * 3 * N <= cap && chunk % (fp64 ? 4 : tile) == 0 &&
+                                (long long)splits * chunk >= N && (long long)(splits - 1) * chunk < N;
+                if (!ok && bad++ < 20) std::printf("%lld %d %d %lld\n", N, sms, splits, (long long)chunk);
+            }
+        std::printf(bad ? "bad\n" : "ok\n");
+        return 0;
+    }
     if (argc >= 4 && std::strcmp(argv[1], "single") == 0) {
         std::vector<int> cta4, seg4, row_seg, col_start;
         rpb::sym_schedule(std::atoll(argv[2]), std::atoi(argv[3]), tile, cta4, seg4, row_seg, col_start);

@@ -111,3 +111,21 @@ def test_batch_schedule_independent_of_companions(dump):
     for t in range(1, nb):
         for b in range(t):
             assert mixed["col_start"][g + t] + (g + b) - base == alone["col_start"][t] + b
+
+
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_noalloc_partials_fit(fp64, tmp_path):
+    """The allocation-free product's chunk plan keeps its partial sums (splits x 3N doubles) inside its
+    fixed array for every N up to its limit and any SM count up to 1024, in chunks that cover the N
+    sources exactly once (whole tiles in float32, multiples of 4 sources in float64)."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    exe = str(tmp_path / "schedule_dump")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-I", CSRC, os.path.join(HERE, "schedule_dump.cpp"), "-o", exe],
+                   check=True)
+    max_n = 16384                 # RPB_NOALLOC_MAX_N
+    cap = 16 * 3 * max_n          # kNoAllocPartialElems
+    out = subprocess.run([exe, "noalloc", str(max_n), "1024", str(cap), str(fp64)], check=True, capture_output=True,
+                         text=True).stdout.split()
+    assert out[-1] == "ok", out[:40]

@@ -68,3 +68,25 @@ def test_noalloc_largest_size_and_limit(gpu_lib):
     assert rc == gpu_lib.RPB_EINVAL
     assert str(N) in gpu_lib.last_error()
     assert np.isfinite(out.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_noalloc_against_oracle_and_null_loads(gpu_lib, precision, tol):
+    """Its own error against the FP64 oracle (rather than against another GPU product) at a small N
+    that spans tiles and a ragged tail, with forces and torques, torques only, and neither (zeros)."""
+    import oracle as O
+
+    N = 300
+    pos = inputs.monolayer(N, seed=7)
+    F = inputs.vectors(N, 7)
+    T = inputs.vectors(N, 57)
+    for f, t in ((F, T), (None, T)):
+        got = gpu_lib.mobility_apply_noalloc(_dev(pos), None if f is None else _dev(f), _dev(t), precision=precision)
+        torch.cuda.synchronize()
+        ref = O.mobility_apply(pos, f, t)
+        err = float(np.max(np.abs(inputs.from_soa(got.cpu().numpy(), N) - ref)) / np.max(np.abs(ref)))
+        assert err <= tol, (precision, f is None, err)
+    out = torch.full((3 * N,), float("nan"), dtype=torch.float64, device="cuda")
+    gpu_lib.mobility_apply_noalloc(_dev(pos), None, None, precision=precision, out=out)
+    torch.cuda.synchronize()
+    assert bool((out == 0).all())
