@@ -55,9 +55,10 @@ FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25  # dense FP64 rate of a GB300 (vector pipe), for context
 # DRAM bytes (read + write) of one launch of the symmetric translation-translation kernel at
 # N = 65536, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the
-# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command).  Valid for one
-# kernel build only: empty until the current build is captured.
-SYM_TT_TRAFFIC_BYTES = {}
+# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command): 4.92 MB read (the
+# packed sources), 165.19 MB written (segment and source-column partials leaving L2).  Valid for this
+# kernel build only: reset to {} when the kernel changes.
+SYM_TT_TRAFFIC_BYTES = {65536: 4.916e6 + 165.190e6}
 SM_MAX_MHZ = 2070.0
 
 
@@ -759,10 +760,10 @@ def oracle_timing(threads, seconds, step_4096=True):
 
 def run_small(args, rank, world, local_rank):
     """The 256-sphere configuration (seed 0, FP64 pairs, dt = 0.01, delta = 1e-6, tol = 1e-3):
-    microseconds per AB step on the GPU through rpb_ab_step (the host reads the Lanczos status back
-    after every iteration) and through a graph-replayed rpb_batch_run of the one suspension, beside the
-    FP64 oracle's full step on all host cores and on one core (plus, on both, one 4096-sphere step and
-    a row sample of the 65536-sphere fused product)."""
+    microseconds per AB step on the GPU through rpb_run (the step replayed from a CUDA graph, the
+    Lanczos stop decided on the device) and through rpb_ab_step (the host reads the Lanczos status back
+    after every iteration), beside the FP64 oracle's full step on all host cores and on one core (plus,
+    on both, one 4096-sphere step and a row sample of the 65536-sphere fused product)."""
     import torch
 
     from paper_1612_00474_gb300 import inputs, rpb
@@ -794,30 +795,34 @@ def run_small(args, rank, world, local_rank):
         us.append(e0.elapsed_time(e1) * 1e3)
         ms_m.append(st["m"])
         step += 1
-    launches = rpb.launch_count() - launches0
+    launches_host = rpb.launch_count() - launches0
+    # the same suspension, steps replayed from a CUDA graph (one capture per call, amortised over the
+    # call's steps: the timed call makes K = max(steps, 50) of them)
+    ctx.run(q, U, step, seed, max(1, args.warmup), max_iter=64, **kw)
+    step += max(1, args.warmup)
+    K = max(args.steps, 50)
+    torch.cuda.synchronize()
+    launches0 = rpb.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st_run, unconv = ctx.run(q, U, step, seed, K, max_iter=64, **kw)
+    e1.record(stream)
+    e1.synchronize()
+    launches_run = rpb.launch_count() - launches0
+    graph_us = e0.elapsed_time(e1) * 1e3 / K
     ctx.close()
-    # the same suspension as a one-instance graph-replayed run
-    bt = rpb.BatchContext(max_total_N=N, max_B=1, precision="fp64", max_iter=64)
-    qb = [torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")]
-    Ub = [torch.zeros_like(qb[0])]
-    bt.run(qb, Ub, [0], [seed], nsteps=max(1, args.warmup), lanczos_iters=args.lanczos_iters, **kw)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, unconv = bt.run(qb, Ub, [max(1, args.warmup)], [seed], nsteps=args.steps, lanczos_iters=args.lanczos_iters,
-                       **kw)
-    torch.cuda.synchronize()
-    graph_us = (time.perf_counter() - t0) * 1e6 / args.steps
-    bt.close()
     clocks = clocks_stop(clk)
     gpu_us = statistics.median(us)
-    line = _base_line(args, 1, gpu_us, "us/step", gpu_us / 1e3, "f64",
+    line = _base_line(args, 1, graph_us, "us/step", graph_us / 1e3, "f64",
                       {"workload": f"small: N={N} monolayer (seed {seed}), AB step dt=0.01, delta=1e-6, tol=1e-3, "
                                    f"fp64 pairs", "N": N})
     line["higher_is_better"] = False
-    line.update({"us_per_step": {"rpb_ab_step_median": gpu_us, "rpb_ab_step_mean": statistics.mean(us),
-                                 "graph_run": graph_us},
-                 "graph_run": {"lanczos_iters_per_step": args.lanczos_iters, "unconverged_instance_steps": unconv},
-                 "lanczos_m": ms_m, "gpu_launches": int(launches), "clocks": clocks})
+    line.update({"us_per_step": {"rpb_run": graph_us, "rpb_ab_step_median": gpu_us,
+                                 "rpb_ab_step_mean": statistics.mean(us)},
+                 "graph_run": {"steps": K, "last_m": st_run["m"], "unconverged_steps": unconv,
+                               "launches_per_step": launches_run / K},
+                 "lanczos_m": ms_m, "gpu_launches": int(launches_run),
+                 "host_driven_launches_per_step": launches_host / max(1, args.steps), "clocks": clocks})
     if not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         allc = oracle_timing(cores, 5.0)

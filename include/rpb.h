@@ -119,6 +119,15 @@ int rpb_set_preconditioner(rpb_ctx *ctx, int kind);
 int rpb_mobility_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
                        double *U);
 
+/* Two products at the same positions: U = M_tt F + M_tr T and U2 = M_tt P (the blocks as for
+ * rpb_mobility_apply).  A time step needs both at once: the deterministic velocity and the first
+ * Lanczos product M v_0 of Sec. II.C.  Where the context can (float32 pairs, wall on, no periodic
+ * images, N >= 256, T given), one symmetric pass evaluates each pair's block once and applies it to
+ * both right-hand sides -- the pass rpb_ab_step uses; otherwise two products.  F, P: 3N, non-null; T
+ * may be NULL.  U, U2: 3N outputs, distinct, aliasing no input. */
+int rpb_mobility_apply2(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
+                        const double *P, double *U, double *U2);
+
 /* g ~ M_tt^{1/2} W by the Lanczos method (Sec. II.C; error estimate eps_m = |g_m - g_{m-1}| /
  * |g_{m-1}|).  Full reorthogonalisation (classical Gram-Schmidt twice) and the tridiagonal
  * square root are float64 in both precisions.  Stops at the first m >= 2 with eps_m <= tol; if
@@ -179,6 +188,26 @@ typedef struct {
 int rpb_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed, double dt,
              double delta, double tol, int max_iter, const rpb_force_params *fp, const rpb_step_options *opts,
              rpb_step_stats *stats);
+
+/* nsteps time steps of one suspension, as nsteps calls of rpb_step with step indices step, step + 1,
+ * ... (Eq. AB or Eq. EM; Sec. II.A-C for the drift and the Lanczos square root), with the same results
+ * bit for bit: the step is captured once into a CUDA graph and replayed nsteps times with no host
+ * synchronisation in between.  Each Lanczos iteration after the first is a conditional node that
+ * runs only while the stopping test of Sec. II.C (eps_m <= tol, or an invariant Krylov space) has not
+ * been met, decided on the device by the previous iteration, so a replay runs the iterations a
+ * host-driven step would, up to max_iter.  The step index keying the noise and the first-step flag
+ * (step == 0 starts with an Euler-Maruyama step) advance on the device.
+ *   - The work runs on a stream the context creates on first use (with a few hundred bytes of
+ *     device state), ordered after the context's stream; the context's stream is ordered after the
+ *     run, and the call returns when the run is complete.  Must not be called while the context's
+ *     stream is being captured.
+ *   - stats (may be NULL): the last step's Lanczos dimension m, eps_m and convergence.
+ *     *unconverged (may be NULL): steps whose Lanczos stopped at max_iter without meeting tol.
+ *   - Errors: as rpb_step; RPB_EINVAL also for nsteps < 0 or step + nsteps >= 2^32; RPB_ENOCONV if
+ *     some step did not converge with tol > 0 (all steps are still taken).  nsteps = 0 does nothing. */
+int rpb_run(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step, uint64_t seed, int nsteps, double dt,
+            double delta, double tol, int max_iter, const rpb_force_params *fp, const rpb_step_options *opts,
+            rpb_step_stats *stats, int64_t *unconverged);
 
 /* Message for the calling thread's most recent failed call ("" if none). */
 const char *rpb_last_error(void);

@@ -80,6 +80,109 @@ static void free_ws(Workspace &w)
     w = Workspace();
 }
 
+int check_step_args(rpb_ctx *ctx, int64_t N, const double *pos, const double *U_prev, int64_t step, double dt,
+                    double delta, int max_iter, const rpb_force_params *fp, const rpb_step_options *opts)
+{
+    int rc;
+    const int scheme = opts ? opts->scheme : RPB_SCHEME_AB;
+    const int rfd = opts ? opts->rfd : RPB_RFD_CENTRED;
+    if ((scheme != RPB_SCHEME_AB && scheme != RPB_SCHEME_EM) || (rfd != RPB_RFD_CENTRED && rfd != RPB_RFD_ONE_SIDED)) {
+        set_error("bad step options (scheme=%d rfd=%d)", scheme, rfd);
+        return RPB_EINVAL;
+    }
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(U_prev, "U_prev", false)))
+        return rc;
+    if (!fp || !(fp->b > 0.0) || !(dt > 0.0) || !(delta > 0.0) || step < 0 || step > 0xffffffffLL) {
+        set_error("bad step arguments (dt=%g delta=%g step=%lld)", dt, delta, (long long)step);
+        return RPB_EINVAL;
+    }
+    if (max_iter < 1 || max_iter > ctx->max_iter) {
+        set_error("max_iter=%d outside [1, %d]", max_iter, ctx->max_iter);
+        return RPB_EINVAL;
+    }
+    if (U_prev == pos) {
+        set_error("U_prev aliases pos");
+        return RPB_EINVAL;
+    }
+    return RPB_OK;
+}
+
+// One time step (Eq. AB, or Eq. EM with scheme = RPB_SCHEME_EM), enqueued on ctx->stream.  gr == null:
+// the Lanczos stop is read back per iteration and stats are written.  gr != null: the step is being
+// captured into a graph (rpb_run): the step index and the first-step flag come from gr->state on the
+// device, Lanczos iterations after the first are conditional nodes, and nothing is read back.
+int step_impl(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, uint32_t step, uint64_t seed, double dt,
+              double delta, double tol, int max_iter, const rpb_force_params *fp, int scheme, int rfd,
+              rpb_step_stats *stats, LzGraph *gr)
+{
+    int rc;
+    Workspace &w = ctx->ws;
+    const unsigned int *d_step = gr ? &gr->state->step : nullptr;
+    double *F = w.vec_a, *T = w.vec_b, *Un = w.vec_c, *W = w.vec_d, *Wt = w.vec_e, *g = w.vec_f, *drift = w.vec_g;
+    if ((rc = forces_impl(ctx, N, pos, fp, F))) return rc;
+    if ((rc = fill_torque(ctx, N, fp->torque, T))) return rc;
+    int iters = 0, conv = 0;
+    double err = -1.0;
+    int lrc = RPB_OK;
+    if (ctx->p.kT > 0.0) {
+        if ((rc = philox_impl(ctx, N, seed, step, 0u, 0u, W, d_step))) return rc;
+        if ((rc = philox_impl(ctx, N, seed, step, 1u, 0u, Wt, d_step))) return rc;
+        if (mobility_apply2_ok(ctx, N)) {
+            // the deterministic velocity and the first Lanczos product M v_0 share one pair pass
+            // (with the preconditioner: M P v_0, scaled by P afterwards)
+            bool zero = false;
+            if ((rc = lanczos_precond_prepare(ctx, N, pos)) || (rc = lanczos_init(ctx, N, W, &zero, gr != nullptr)))
+                return rc;
+            if (zero) {
+                if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
+                if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "zero g")))
+                    return rc;
+                conv = 1;
+            } else {
+                if (ctx->precond) {
+                    if ((rc = precond_scale(ctx, N, w.V, w.pcx, false)) ||
+                        (rc = mobility_apply2_impl(ctx, N, pos, F, T, w.pcx, Un, w.w)) ||
+                        (rc = precond_scale(ctx, N, w.w, w.w, false)))
+                        return rc;
+                } else if ((rc = mobility_apply2_impl(ctx, N, pos, F, T, w.V, Un, w.w))) {
+                    return rc;
+                }
+                lrc = lanczos_run(ctx, N, pos, g, tol, max_iter, true, &iters, &err, &conv, gr);
+            }
+        } else {
+            if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
+            lrc = lanczos_impl(ctx, N, pos, W, g, tol, max_iter, &iters, &err, &conv, gr);
+        }
+        if (lrc != RPB_OK && lrc != RPB_ENOCONV) return lrc;
+        if ((rc = rfd_impl(ctx, N, pos, Wt, delta, drift, rfd == RPB_RFD_ONE_SIDED))) return rc;
+    } else {
+        if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
+        // kT = 0: no Brownian increment and no drift (both carry a factor kT); the deterministic
+        // scheme needs neither the noise nor M^{1/2}
+        if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "clear g")) ||
+            (rc = cuda_fail(cudaMemsetAsync(drift, 0, 3 * N * sizeof(double), ctx->stream), "clear drift")))
+            return rc;
+        err = 0.0;
+        conv = 1;
+    }
+    const double noise = sqrt(2.0 * ctx->p.kT * dt);
+    // Euler-Maruyama is the update with U^{n-1} := U^n (Eq. EM); AB uses that only on the first step
+    const int em = scheme == RPB_SCHEME_EM || (!gr && step == 0);
+    if ((rc = ab_update_impl(ctx, N, pos, U_prev, Un, g, drift, dt, noise, em, gr ? &gr->state->first : nullptr)))
+        return rc;
+    if (gr) return RPB_OK;
+    if (stats) {
+        stats->lanczos_iters = iters;
+        stats->lanczos_err = err;
+        stats->converged = conv;
+    }
+    if (lrc == RPB_ENOCONV) {
+        set_error("lanczos: no convergence in %d iterations (eps=%g, tol=%g)", iters, err, tol);
+        return RPB_ENOCONV;
+    }
+    return RPB_OK;
+}
+
 }  // namespace rpb
 
 using namespace rpb;
@@ -229,6 +332,7 @@ int rpb_destroy(rpb_ctx *ctx)
     if (!ctx) return RPB_OK;
     g_err[0] = 0;
     int rc = cuda_fail(cudaStreamSynchronize(ctx->stream), "rpb_destroy sync");
+    run_free(ctx);
     free_ws(ctx->ws);
     delete ctx;
     return rc;
@@ -301,6 +405,30 @@ int rpb_mobility_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double 
     }
     if (!F && !T) return cuda_fail(cudaMemsetAsync(U, 0, 3 * N * sizeof(double), ctx->stream), "memset U");
     return mobility_apply_impl(ctx, N, pos, F, T, U);
+}
+
+int rpb_mobility_apply2(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
+                        const double *P, double *U, double *U2)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(F, "F", false)) ||
+        (rc = check_vec(T, "T", true)) || (rc = check_vec(P, "P", false)) || (rc = check_vec(U, "U", false)) ||
+        (rc = check_vec(U2, "U2", false)))
+        return rc;
+    const double *outs[] = {U, U2};
+    for (const double *o : outs)
+        if (o == pos || o == F || o == T || o == P) {
+            set_error("an output aliases an input");
+            return RPB_EINVAL;
+        }
+    if (U == U2) {
+        set_error("U and U2 are the same buffer");
+        return RPB_EINVAL;
+    }
+    if (T && mobility_apply2_ok(ctx, N)) return mobility_apply2_impl(ctx, N, pos, F, T, P, U, U2);
+    if ((rc = mobility_apply_impl(ctx, N, pos, F, T, U))) return rc;
+    return mobility_apply_impl(ctx, N, pos, P, nullptr, U2);
 }
 
 int rpb_lanczos_sqrt_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol,
@@ -378,87 +506,9 @@ int rpb_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step,
 {
     g_err[0] = 0;
     int rc;
-    const int scheme = opts ? opts->scheme : RPB_SCHEME_AB;
-    const int rfd = opts ? opts->rfd : RPB_RFD_CENTRED;
-    if ((scheme != RPB_SCHEME_AB && scheme != RPB_SCHEME_EM) || (rfd != RPB_RFD_CENTRED && rfd != RPB_RFD_ONE_SIDED)) {
-        set_error("bad step options (scheme=%d rfd=%d)", scheme, rfd);
-        return RPB_EINVAL;
-    }
-    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(U_prev, "U_prev", false)))
-        return rc;
-    if (!fp || !(fp->b > 0.0) || !(dt > 0.0) || !(delta > 0.0) || step < 0 || step > 0xffffffffLL) {
-        set_error("bad step arguments (dt=%g delta=%g step=%lld)", dt, delta, (long long)step);
-        return RPB_EINVAL;
-    }
-    if (max_iter < 1 || max_iter > ctx->max_iter) {
-        set_error("max_iter=%d outside [1, %d]", max_iter, ctx->max_iter);
-        return RPB_EINVAL;
-    }
-    if (U_prev == pos) {
-        set_error("U_prev aliases pos");
-        return RPB_EINVAL;
-    }
-    Workspace &w = ctx->ws;
-    double *F = w.vec_a, *T = w.vec_b, *Un = w.vec_c, *W = w.vec_d, *Wt = w.vec_e, *g = w.vec_f, *drift = w.vec_g;
-    if ((rc = forces_impl(ctx, N, pos, fp, F))) return rc;
-    if ((rc = fill_torque(ctx, N, fp->torque, T))) return rc;
-    int iters = 0, conv = 0;
-    double err = -1.0;
-    int lrc = RPB_OK;
-    if (ctx->p.kT > 0.0) {
-        if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 0u, 0u, W))) return rc;
-        if ((rc = philox_impl(ctx, N, seed, (uint32_t)step, 1u, 0u, Wt))) return rc;
-        if (mobility_apply2_ok(ctx, N)) {
-            // the deterministic velocity and the first Lanczos product M v_0 share one pair pass
-            // (with the preconditioner: M P v_0, scaled by P afterwards)
-            bool zero = false;
-            if ((rc = lanczos_precond_prepare(ctx, N, pos)) || (rc = lanczos_init(ctx, N, W, &zero))) return rc;
-            if (zero) {
-                if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
-                if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "zero g")))
-                    return rc;
-                conv = 1;
-            } else {
-                if (ctx->precond) {
-                    if ((rc = precond_scale(ctx, N, w.V, w.pcx, false)) ||
-                        (rc = mobility_apply2_impl(ctx, N, pos, F, T, w.pcx, Un, w.w)) ||
-                        (rc = precond_scale(ctx, N, w.w, w.w, false)))
-                        return rc;
-                } else if ((rc = mobility_apply2_impl(ctx, N, pos, F, T, w.V, Un, w.w))) {
-                    return rc;
-                }
-                lrc = lanczos_run(ctx, N, pos, g, tol, max_iter, true, &iters, &err, &conv);
-            }
-        } else {
-            if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
-            lrc = lanczos_impl(ctx, N, pos, W, g, tol, max_iter, &iters, &err, &conv);
-        }
-        if (lrc != RPB_OK && lrc != RPB_ENOCONV) return lrc;
-        if ((rc = rfd_impl(ctx, N, pos, Wt, delta, drift, rfd == RPB_RFD_ONE_SIDED))) return rc;
-    } else {
-        if ((rc = mobility_apply_impl(ctx, N, pos, F, T, Un))) return rc;
-        // kT = 0: no Brownian increment and no drift (both carry a factor kT); the deterministic
-        // scheme needs neither the noise nor M^{1/2}
-        if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "clear g")) ||
-            (rc = cuda_fail(cudaMemsetAsync(drift, 0, 3 * N * sizeof(double), ctx->stream), "clear drift")))
-            return rc;
-        err = 0.0;
-        conv = 1;
-    }
-    const double noise = sqrt(2.0 * ctx->p.kT * dt);
-    // Euler-Maruyama is the update with U^{n-1} := U^n (Eq. EM); AB uses that only on the first step
-    const int em = scheme == RPB_SCHEME_EM || step == 0;
-    if ((rc = ab_update_impl(ctx, N, pos, U_prev, Un, g, drift, dt, noise, em))) return rc;
-    if (stats) {
-        stats->lanczos_iters = iters;
-        stats->lanczos_err = err;
-        stats->converged = conv;
-    }
-    if (lrc == RPB_ENOCONV) {
-        set_error("lanczos: no convergence in %d iterations (eps=%g, tol=%g)", iters, err, tol);
-        return RPB_ENOCONV;
-    }
-    return RPB_OK;
+    if ((rc = check_step_args(ctx, N, pos, U_prev, step, dt, delta, max_iter, fp, opts))) return rc;
+    return step_impl(ctx, N, pos, U_prev, (uint32_t)step, seed, dt, delta, tol, max_iter, fp,
+                     opts ? opts->scheme : RPB_SCHEME_AB, opts ? opts->rfd : RPB_RFD_CENTRED, stats, nullptr);
 }
 
 }  // extern "C"

@@ -756,34 +756,6 @@ __global__ void batch_iter_kernel(cudaGraphConditionalHandle next, int has_next,
     if (has_next) cudaGraphSetConditional(next, *n_active > 0 ? 1u : 0u);
 }
 
-// Open a conditional (IF) node after the work captured so far on `st` and start capturing its body on
-// `body`; the node runs its body when `h` was set non-zero during this launch of the graph.
-static int begin_if_node(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle h)
-{
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g = nullptr;
-    const cudaGraphNode_t *deps = nullptr;
-    const cudaGraphEdgeData *edges = nullptr;
-    size_t nd = 0;
-    int rc;
-    if ((rc = cuda_fail(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &nd), "capture info")))
-        return rc;
-    cudaGraphNodeParams p = {};
-    p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeIf;
-    p.conditional.size = 1;
-    cudaGraphNode_t node = nullptr;
-    if ((rc = cuda_fail(cudaGraphAddNode(&node, g, deps, edges, nd, &p), "conditional node")) ||
-        (rc = cuda_fail(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
-                        "capture dependencies")) ||
-        (rc = cuda_fail(cudaStreamBeginCaptureToGraph(body, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                                      cudaStreamCaptureModeThreadLocal),
-                        "body capture")))
-        return rc;
-    return RPB_OK;
-}
-
 // Lanczos for every instance at once; per-instance m, eps and convergence land in h_lz statuses.
 // graph == false: the host reads the number of still-active instances after every iteration and stops
 // when it reaches zero, then copies the per-instance statuses to h_lz.  graph == true (inside a CUDA
@@ -823,7 +795,7 @@ static int batch_lanczos(rpb_batch *bt, const double *pos, const double *W, doub
     for (int k = 0; k < max_iter; ++k) {
         const bool cond = graph && k >= 1;
         if (cond) {
-            if ((rc = begin_if_node(main_st, bt->body, hnd[k]))) return rc;
+            if ((rc = graph_begin_if(main_st, bt->body, hnd[k]))) return rc;
             bt->stream = bt->body;
         }
         cudaStream_t st = bt->stream;

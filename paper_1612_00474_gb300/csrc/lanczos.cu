@@ -13,7 +13,8 @@
 // three-term recurrence is a subset of the reorthogonalisation.
 // Reductions are two-level (per-block partials, then a fixed-order sum): results do not depend on
 // scheduling.  The stopping decision is read back once per iteration (one small device-to-host
-// copy and a stream synchronisation).
+// copy and a stream synchronisation), or, inside a graph-replayed run, taken on the device: each
+// iteration after the first is a conditional node that the previous iteration enables.
 #include <cfloat>
 #include <cmath>
 
@@ -151,11 +152,12 @@ __global__ void __launch_bounds__(32) lanczos_tail_kernel(double *__restrict__ l
     lanczos_tail_warp(lz, L, k, tol, lz[L.c1 + k] + lz[L.c2 + k], sqrt(bn), q0, sl, red);
 }
 
-// g[r] = sum_{k < m} y[k] V[k][r]   (y already carries |W|)
+// g[r] = sum_{k < m} y[k] V[k][r]   (y already carries |W|); d_m (optional): read m from the device
 __global__ void combine_kernel(const double *__restrict__ V, size_t ld, int64_t n, int m, const double *__restrict__ y,
-                               double *__restrict__ g)
+                               double *__restrict__ g, const int *__restrict__ d_m)
 {
     __shared__ double ys[kMaxIter];
+    if (d_m) m = *d_m;
     for (int k = threadIdx.x; k < m; k += blockDim.x) ys[k] = y[k];
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
@@ -220,7 +222,17 @@ int precond_scale(rpb_ctx *ctx, int64_t N, const double *x, double *out, bool in
     return cuda_fail(cudaGetLastError(), "preconditioner scale");
 }
 
-int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero)
+// Inside a replayed graph, after iteration k - 1 (m = k products so far): count this run, record m, and
+// let iteration k run only if the iteration has not stopped.
+__global__ void lz_iter_kernel(cudaGraphConditionalHandle next, int has_next, const double *__restrict__ status, int m,
+                               unsigned long long *__restrict__ runs, int *__restrict__ m_out)
+{
+    *runs += 1ull;
+    *m_out = m;
+    if (has_next) cudaGraphSetConditional(next, status[ST_STOP] == 0.0 ? 1u : 0u);
+}
+
+int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero, bool graph)
 {
     cudaStream_t st = ctx->stream;
     const int64_t n = 3 * N;
@@ -235,6 +247,10 @@ int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero)
     norm_init_kernel<<<1, 32, 0, st>>>(red, G, status);
     scale_kernel<<<G, kBlasThreads, 0, st>>>(W, n, status, ST_INV_NW, ctx->ws.V);
     count_launches(3);
+    if (graph) {
+        *nw_zero = false;
+        return cuda_fail(cudaGetLastError(), "lanczos init");
+    }
     if ((rc = cuda_fail(cudaMemcpyAsync(hs, status, 8 * sizeof(double), cudaMemcpyDeviceToHost, st), "status copy")))
         return rc;
     if ((rc = cuda_fail(cudaStreamSynchronize(st), "lanczos init"))) return rc;
@@ -243,11 +259,11 @@ int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero)
 }
 
 int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol, int max_iter,
-                 int *iters_out, double *err_out, int *converged_out)
+                 int *iters_out, double *err_out, int *converged_out, LzGraph *gr)
 {
     bool zero = false;
     int rc;
-    if ((rc = lanczos_precond_prepare(ctx, N, pos)) || (rc = lanczos_init(ctx, N, W, &zero))) return rc;
+    if ((rc = lanczos_precond_prepare(ctx, N, pos)) || (rc = lanczos_init(ctx, N, W, &zero, gr != nullptr))) return rc;
     if (zero) {
         if ((rc = cuda_fail(cudaMemsetAsync(g, 0, 3 * N * sizeof(double), ctx->stream), "zero g"))) return rc;
         if (iters_out) *iters_out = 0;
@@ -255,13 +271,13 @@ int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, do
         if (converged_out) *converged_out = 1;
         return RPB_OK;
     }
-    return lanczos_run(ctx, N, pos, g, tol, max_iter, false, iters_out, err_out, converged_out);
+    return lanczos_run(ctx, N, pos, g, tol, max_iter, false, iters_out, err_out, converged_out, gr);
 }
 
 int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double tol, int max_iter, bool first_done,
-                int *iters_out, double *err_out, int *converged_out)
+                int *iters_out, double *err_out, int *converged_out, LzGraph *gr)
 {
-    cudaStream_t st = ctx->stream;
+    const cudaStream_t main_st = ctx->stream;
     const int64_t n = 3 * N;
     const size_t ld = (size_t)3 * ctx->max_N;
     const LzLayout L(ctx->max_iter);
@@ -277,44 +293,86 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
     int m = 0;
     bool stopped = false;
     double eps = -1.0;
-    for (int k = 0; k < max_iter; ++k) {
-        const double *vk = V + (size_t)k * ld;
-        if (!(k == 0 && first_done)) {
-            if (ctx->precond) {  // w = P M P v_k
-                if ((rc = precond_scale(ctx, N, vk, ctx->ws.pcx, false)) ||
-                    (rc = mobility_apply_impl(ctx, N, pos, ctx->ws.pcx, nullptr, w)) ||
-                    (rc = precond_scale(ctx, N, w, w, false)))
-                    return rc;
-            } else if ((rc = mobility_apply_impl(ctx, N, pos, vk, nullptr, w))) {
-                return rc;
-            }
-        }
-        const int nv = k + 1;
-        dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
-        project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c1, nullptr);
-        dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
-        project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c2, red_norm);
-        lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G);
-        count_launches(5);
-        if ((rc = cuda_fail(cudaMemcpyAsync(hs, status, 8 * sizeof(double), cudaMemcpyDeviceToHost, st),
-                            "status copy")))
+    if (gr) {  // one conditional handle per iteration after the first, on the graph being captured
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        if ((rc = cuda_fail(cudaStreamGetCaptureInfo(main_st, &cs, nullptr, &cg, nullptr, nullptr, nullptr),
+                            "capture info")))
             return rc;
-        if ((rc = cuda_fail(cudaStreamSynchronize(st), "lanczos iteration"))) return rc;
-        m = k + 1;
-        eps = hs[ST_EPS];
-        if (hs[ST_STOP] != 0.0) {
-            stopped = true;
-            break;
-        }
-        if (k + 1 < max_iter) {
-            scale_kernel<<<G, kBlasThreads, 0, st>>>(w, n, status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
-            count_launches(1);
+        for (int k = 1; k < max_iter; ++k) {
+            gr->iter_launches[k] = 0;
+            if ((rc = cuda_fail(cudaGraphConditionalHandleCreate(&gr->hnd[k], cg, 0u, cudaGraphCondAssignDefault),
+                                "conditional handle")))
+                return rc;
         }
     }
-    combine_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, m, lz + L.y, g);
+    for (int k = 0; k < max_iter; ++k) {
+        const bool cond = gr && k >= 1;
+        if (cond) {
+            if ((rc = graph_begin_if(main_st, gr->body, gr->hnd[k]))) return rc;
+            ctx->stream = gr->body;
+        }
+        cudaStream_t st = ctx->stream;
+        const uint64_t before = rpb_launch_count();
+        const double *vk = V + (size_t)k * ld;
+        rc = RPB_OK;
+        if (!(k == 0 && first_done)) {
+            if (ctx->precond) {  // w = P M P v_k
+                if (!(rc = precond_scale(ctx, N, vk, ctx->ws.pcx, false)) &&
+                    !(rc = mobility_apply_impl(ctx, N, pos, ctx->ws.pcx, nullptr, w)))
+                    rc = precond_scale(ctx, N, w, w, false);
+            } else {
+                rc = mobility_apply_impl(ctx, N, pos, vk, nullptr, w);
+            }
+        }
+        if (!rc) {
+            const int nv = k + 1;
+            dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
+            project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c1, nullptr);
+            dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
+            project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c2, red_norm);
+            lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G);
+            count_launches(5);
+            if (gr) {
+                const bool has_next = k + 1 < max_iter;
+                lz_iter_kernel<<<1, 1, 0, st>>>(has_next ? gr->hnd[k + 1] : 0ull, has_next ? 1 : 0, status, k + 1,
+                                                gr->state->iter_runs + k, &gr->state->m);
+                count_launches(1);
+                if (has_next) {  // v_{k+1} (unused when this iteration stopped)
+                    scale_kernel<<<G, kBlasThreads, 0, st>>>(w, n, status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
+                    count_launches(1);
+                }
+                rc = cuda_fail(cudaGetLastError(), "lanczos kernels");
+            } else {
+                if (!(rc = cuda_fail(cudaMemcpyAsync(hs, status, 8 * sizeof(double), cudaMemcpyDeviceToHost, st),
+                                     "status copy")))
+                    rc = cuda_fail(cudaStreamSynchronize(st), "lanczos iteration");
+                if (!rc) {
+                    m = k + 1;
+                    eps = hs[ST_EPS];
+                    if (hs[ST_STOP] != 0.0) stopped = true;
+                    if (!stopped && k + 1 < max_iter) {
+                        scale_kernel<<<G, kBlasThreads, 0, st>>>(w, n, status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
+                        count_launches(1);
+                    }
+                }
+            }
+        }
+        if (cond) {
+            gr->iter_launches[k] = (int)(rpb_launch_count() - before);
+            cudaGraph_t body_graph = nullptr;
+            const int erc = cuda_fail(cudaStreamEndCapture(gr->body, &body_graph), "body capture end");
+            ctx->stream = main_st;
+            if (!rc) rc = erc;
+        }
+        if (rc) return rc;
+        if (stopped) break;
+    }
+    combine_kernel<<<G, kBlasThreads, 0, main_st>>>(V, ld, n, m, lz + L.y, g, gr ? &gr->state->m : nullptr);
     count_launches(1);
     if (ctx->precond && (rc = precond_scale(ctx, N, g, g, true))) return rc;  // g = D^{1/2} y
     if ((rc = cuda_fail(cudaGetLastError(), "lanczos kernels"))) return rc;
+    if (gr) return RPB_OK;
     if (iters_out) *iters_out = m;
     if (err_out) *err_out = eps;
     const bool converged = stopped;

@@ -789,6 +789,12 @@ static int sym_prepare(rpb_ctx *ctx, int N)
     return RPB_OK;
 }
 
+int pair_prepare(rpb_ctx *ctx, int64_t N)
+{
+    if (ctx->sym_enabled && N >= 2 * kTile && N <= ctx->max_N) return sym_prepare(ctx, (int)N);
+    return RPB_OK;
+}
+
 // Symmetric product (float32 pairs), translation-translation or, with T, the fused product;
 // requires ctx->ws.sym_* scratch.
 static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F, const double *T, double *U)

@@ -165,6 +165,31 @@ struct Workspace {
     int sym_N = -1, sym_ncta = 0, sym_nseg = 0, sym_seg_off = 0, sym_row_off = 0, sym_col_off = 0;
 };
 
+constexpr int kRunMaxIter = 64;  // = kMaxIter of the Lanczos state
+
+// Device state of a graph-replayed run (rpb_run): the step index the noise is drawn with, whether the
+// coming step is a first (Euler-Maruyama) step, the Lanczos dimension m of the latest step, and counters
+// of the instance-steps that did not converge and of the runs of each Lanczos iteration.
+struct RunState {
+    unsigned int step;
+    int first;
+    int m;
+    int pad;
+    unsigned long long unconv;
+    unsigned long long iter_runs[kRunMaxIter];
+};
+struct RunCtx;  // run.cu
+
+// Capture of the Lanczos iterations into a CUDA graph (rpb_run): iteration k >= 1 is the body of a
+// conditional node hnd[k], captured on `body`; the last kernel of iteration k - 1 sets its condition on
+// the device from the stopping test, and records m in state.
+struct LzGraph {
+    cudaStream_t body = nullptr;
+    RunState *state = nullptr;
+    cudaGraphConditionalHandle hnd[kRunMaxIter] = {};
+    int iter_launches[kRunMaxIter] = {};  // kernels captured into iteration k's body
+};
+
 }  // namespace rpb
 
 struct rpb_ctx {
@@ -182,6 +207,7 @@ struct rpb_ctx {
     int precond = 0;            // Lanczos preconditioner (RPB_PRECOND_*), rpb_set_preconditioner
     int f32_slots[2] = {0, 0};  // resident CTAs of the float32 one-way pair kernels (tt, with torques)
     rpb::Workspace ws;
+    rpb::RunCtx *run = nullptr; // streams and device state of graph-replayed runs (rpb_run), made on first use
 };
 
 namespace rpb {
@@ -229,25 +255,45 @@ void batch_sym_free(BatchSymPlan &pl);
 // masks suspensions (null: all).
 int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, int64_t total, const double *pos,
                     const double *F, const double *T, double *U, const int *active, double a, double eta);
+// d_step (optional): a device word to read the step index from instead of `step` (graph replays).
 int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t stream_id, uint32_t instance,
-                double *out);
+                double *out, const unsigned int *d_step = nullptr);
+// Open a conditional (IF) node after the work captured so far on `st` and start capturing its body on
+// `body`; the node runs its body when `h` was set non-zero during this launch of the graph.
+int graph_begin_if(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle h);
+// Host-side preparation a product at this N needs (the symmetric pass's schedule), done before a
+// stream capture so that the captured products find it in place.
+int pair_prepare(rpb_ctx *ctx, int64_t N);
 int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g, double tol, int max_iter,
-                 int *iters_out, double *err_out, int *converged_out);
+                 int *iters_out, double *err_out, int *converged_out, LzGraph *gr = nullptr);
 // The two halves of lanczos_impl: |W| and v_0 = W/|W| into ws.V (synchronises; *nw_zero when W = 0),
 // then the iterations; with first_done the first product M v_0 is already in ws.w (with the
 // preconditioner on: P M P v_0, see lanczos_precond_prepare).
-int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero);
+// graph: inside a stream capture; nothing is read back (*nw_zero false: the noise W of a step is never 0).
+int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero, bool graph = false);
 // With ctx->precond set: P = D^{-1/2} at these positions into ws.pc (D: diagonal of the self blocks),
 // so that the iteration runs on P M P and returns g = D^{1/2} y.  precond_scale: out = x * P
 // elementwise (inverse: x / P, 0 where P = 0).
 int lanczos_precond_prepare(rpb_ctx *ctx, int64_t N, const double *pos);
 int precond_scale(rpb_ctx *ctx, int64_t N, const double *x, double *out, bool inverse);
+// gr: inside a stream capture, the iterations after the first in conditional nodes (see LzGraph); the
+// host outputs are then not written.
 int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double tol, int max_iter, bool first_done,
-                int *iters_out, double *err_out, int *converged_out);
+                int *iters_out, double *err_out, int *converged_out, LzGraph *gr = nullptr);
 int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, double delta, double *drift,
              int one_sided = 0);
+// d_first (optional): a device word that, when non-zero, makes the update a first step (graph replays).
 int ab_update_impl(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, const double *Un, const double *g,
-                   const double *drift, double dt, double noise_scale, int first);
+                   const double *drift, double dt, double noise_scale, int first, const int *d_first = nullptr);
+
+// Arguments of a time step (rpb_step, rpb_run), and the step itself (api.cu; see there).
+int check_step_args(rpb_ctx *ctx, int64_t N, const double *pos, const double *U_prev, int64_t step, double dt,
+                    double delta, int max_iter, const rpb_force_params *fp, const rpb_step_options *opts);
+int step_impl(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, uint32_t step, uint64_t seed, double dt,
+              double delta, double tol, int max_iter, const rpb_force_params *fp, int scheme, int rfd,
+              rpb_step_stats *stats, LzGraph *gr);
+// Streams and device state of graph-replayed runs (run.cu), released by rpb_destroy.
+void run_free(rpb_ctx *ctx);
 
 // Sizes of the Lanczos small-state block (doubles) for max_iter.
 size_t lanczos_state_elems(int max_iter);

@@ -28,8 +28,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // Normals k = 2p and 2p + 1 of the particle-major index k = 3 i + c, stored SoA out[c N + i].
 __global__ void philox_normal_kernel(int N, uint32_t k0, uint32_t k1, uint32_t step, uint32_t sid, uint32_t inst,
-                                     double *__restrict__ out)
+                                     double *__restrict__ out, const unsigned int *__restrict__ d_step)
 {
+    if (d_step) step = *d_step;
     const int64_t n = 3 * (int64_t)N;
     const int64_t npairs = (n + 1) / 2;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * blockDim.x) {
@@ -47,13 +48,13 @@ __global__ void philox_normal_kernel(int N, uint32_t k0, uint32_t k1, uint32_t s
 }
 
 int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t stream_id, uint32_t instance,
-                double *out)
+                double *out, const unsigned int *d_step)
 {
     const int64_t npairs = (3 * N + 1) / 2;
     int grid = (int)((npairs + 255) / 256);
     if (grid > 8 * ctx->num_sms) grid = 8 * ctx->num_sms;
     philox_normal_kernel<<<grid, 256, 0, ctx->stream>>>((int)N, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
-                                                        step, stream_id, instance, out);
+                                                        step, stream_id, instance, out, d_step);
     count_launches(1);
     return cuda_fail(cudaGetLastError(), "philox kernel");
 }
@@ -102,8 +103,9 @@ int rfd_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, doubl
 // ------------------------------------------------------------------ AB update (Eq. AB)
 __global__ void ab_update_kernel(double *__restrict__ pos, double *__restrict__ U_prev, const double *__restrict__ Un,
                                  const double *__restrict__ g, const double *__restrict__ drift, int64_t n, double dt,
-                                 double noise_scale, int first)
+                                 double noise_scale, int first, const int *__restrict__ d_first)
 {
+    if (d_first && *d_first) first = 1;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const double un = Un[r];
         const double up = first ? un : U_prev[r];
@@ -120,11 +122,11 @@ __global__ void fill3_kernel(double *__restrict__ v, int N, double x, double y, 
 }
 
 int ab_update_impl(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, const double *Un, const double *g,
-                   const double *drift, double dt, double noise_scale, int first)
+                   const double *drift, double dt, double noise_scale, int first, const int *d_first)
 {
     const int64_t n = 3 * N;
     ab_update_kernel<<<elem_grid(n, ctx->num_sms), 256, 0, ctx->stream>>>(pos, U_prev, Un, g, drift, n, dt,
-                                                                            noise_scale, first);
+                                                                            noise_scale, first, d_first);
     count_launches(1);
     return cuda_fail(cudaGetLastError(), "ab update");
 }

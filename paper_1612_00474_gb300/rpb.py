@@ -23,7 +23,7 @@ EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", 
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
            "rpb_launch_count", "rpb_mobility_apply_noalloc", "rpb_batch_create", "rpb_batch_destroy",
            "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step", "rpb_batch_run",
-           "rpb_set_periodic", "rpb_set_preconditioner", "rpb_fma_peak")
+           "rpb_set_periodic", "rpb_set_preconditioner", "rpb_fma_peak", "rpb_run", "rpb_mobility_apply2")
 SCHEMES = {"AB": 0, "EM": 1}
 RFDS = {"centred": 0, "one-sided": 1}
 PRECONDITIONERS = {"none": 0, "block-diagonal": 1}
@@ -101,6 +101,9 @@ def load(build_if_missing=True):
     L.rpb_launch_count.restype = ctypes.c_uint64
     L.rpb_mobility_apply_noalloc.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp]
     L.rpb_fma_peak.argtypes = [i32, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+    L.rpb_mobility_apply2.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+    L.rpb_run.argtypes = [vp, i64, vp, vp, i64, u64, i32, d, d, d, i32, ctypes.POINTER(ForceParams),
+                          ctypes.POINTER(StepOptions), ctypes.POINTER(StepStats), ctypes.POINTER(i64)]
     pi64 = ctypes.POINTER(i64)
     L.rpb_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), i64, i32, i32, vp]
     L.rpb_batch_destroy.argtypes = [vp]
@@ -236,6 +239,17 @@ class Context:
                                          _ptr(out, n, "U")))
         return out
 
+    def mobility_apply2(self, pos, F, T, P, out=None, out2=None):
+        """(M_tt F + M_tr T, M_tt P) at the same positions, in one pass where the context can
+        (rpb_mobility_apply2)."""
+        n = pos.numel()
+        out = self._empty(n, pos) if out is None else out
+        out2 = self._empty(n, pos) if out2 is None else out2
+        self._bind_stream()
+        _check(load().rpb_mobility_apply2(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(F, n, "F"), _ptr(T, n, "T"),
+                                          _ptr(P, n, "P"), _ptr(out, n, "U"), _ptr(out2, n, "U2")))
+        return out, out2
+
     def lanczos_sqrt_apply(self, pos, W, tol=1e-3, max_iter=None, out=None, raise_on_noconv=True):
         """g ~ M^{1/2} W (rpb_lanczos_sqrt_apply); returns (g, iterations, eps, converged)."""
         n = pos.numel()
@@ -305,6 +319,25 @@ class Context:
         if not (rc == RPB_ENOCONV and not raise_on_noconv):
             _check(rc)
         return dict(m=stats.lanczos_iters, eps=stats.lanczos_err, converged=bool(stats.converged))
+
+    def run(self, pos, U_prev, step, seed, nsteps, scheme="AB", rfd="centred", dt=0.01, delta=1e-6, tol=1e-3,
+            max_iter=None, weight=1.0, U0=1.0, b=0.1, torque=(0.0, 1.0, 0.0), raise_on_noconv=True):
+        """nsteps time steps in place, replayed from a CUDA graph with the Lanczos stop decided on the
+        device (rpb_run); the same results as nsteps calls of step().  Returns (last step's statistics,
+        number of steps whose Lanczos did not converge)."""
+        n = pos.numel()
+        fp = _force_params(weight, U0, b, torque)
+        opts = StepOptions(SCHEMES[scheme], RFDS[rfd])
+        stats = StepStats()
+        unconv = ctypes.c_int64(0)
+        self._bind_stream()
+        rc = load().rpb_run(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(U_prev, n, "U_prev"), int(step), int(seed),
+                            int(nsteps), float(dt), float(delta), float(tol), int(max_iter or self.max_iter),
+                            ctypes.byref(fp), ctypes.byref(opts), ctypes.byref(stats), ctypes.byref(unconv))
+        if not (rc == RPB_ENOCONV and not raise_on_noconv):
+            _check(rc)
+        return (dict(m=stats.lanczos_iters, eps=stats.lanczos_err, converged=bool(stats.converged)),
+                int(unconv.value))
 
 
 class BatchContext:
