@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--periodic", action="store_true",
                     help="monolayer: pseudo-periodic boundaries with the monolayer's square as the unit cell")
+    ap.add_argument("--split", choices=["replicas", "rows"], default="replicas",
+                    help="monolayer under torchrun: independent replicas (weak scaling) or one suspension whose "
+                         "products are shared by target rows among the ranks (strong scaling)")
     ap.add_argument("--precondition", action="store_true",
                     help="monolayer: block-diagonal Lanczos preconditioner (an option; the paper's runs use none)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -249,8 +252,15 @@ def run_ours(args, rank, world, local_rank):
     dist = init_dist(world)
 
     N = args.N
-    seed = args.seed + rank  # independent replicas, one suspension per rank
-    ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=64)
+    rows = args.split == "rows" and world > 1
+    if rows:  # one suspension, its products shared by target rows (same seed and state on every rank)
+        from paper_1612_00474_gb300.split import SplitContext
+
+        seed = args.seed
+        ctx = SplitContext(N, precision=args.precision, max_iter=64)
+    else:
+        seed = args.seed + rank  # independent replicas, one suspension per rank
+        ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=64)
     images = 1
     if args.periodic:
         ctx.set_periodic(cell_side(N), cell_side(N))
@@ -342,7 +352,10 @@ def run_ours(args, rank, world, local_rank):
     t_fused = time_product(W, Tq)
 
     # max of the times and sum of the work over ranks
+    # max of the times over ranks; the work summed over ranks for replicas, once for a shared suspension
     (total_s, e2e_s), (pairs, e2e_pairs) = aggregate(dist, [total_s, e2e_s], [pairs, e2e_pairs], device="cuda")
+    if rows:
+        pairs, e2e_pairs = pairs / world, e2e_pairs / world
     if dist:
         dist.barrier()
 
@@ -367,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
             peak = peaks["dfma_tflops"]
             peak_basis = (f"measured on this GPU by rpb_fma_peak: DFMA {peak:.3f} TFLOP/s (nominal "
                           f"{FP64_NOMINAL_TFLOPS})")
-        sym = args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256
+        sym = args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256 and not rows
         diag = float(N) * 128
         if args.periodic and sym:  # nine images of each unordered pair once, both ways
             flops_tt = 9.0 * (FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag)
@@ -378,6 +391,11 @@ def run_ours(args, rank, world, local_rank):
         elif sym:  # each unordered pair once (135 flop) except inside the 128-wide diagonal tiles (106 flop each way)
             flops_tt = FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag
             kernel = "pair_f32x2_sym_kernel (translation-translation, reciprocity)"
+        elif rows:  # this rank's rows against all sources, timed with the all-gather of the other rows
+            a_, b_ = ctx.split(N).mine
+            flops_tt = float(b_ - a_) * N * FLOPS_TT
+            kernel = (f"pair_f{'32x2' if args.precision == 'fp32' else '64'}_kernel<false> over rank 0's rows "
+                      f"[{a_}, {b_}) of {N}, timed with the all-gather of the row blocks")
         else:
             flops_tt = float(N) * N * FLOPS_TT
             kernel = f"pair_f{args.precision[2:]}_kernel<false> (translation-translation)"
@@ -396,10 +414,11 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "scaling": "strong" if rows else "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(args), "N": N, "precision": args.precision,
-                       "pair_arith": args.precision, "lanczos_arith": "f64", "parallelism": f"replicas x{world}",
+                       "pair_arith": args.precision, "lanczos_arith": "f64", "parallelism": f"rows x{world}" if rows else f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps",
                        "periodic": [cell_side(N)] * 2 if args.periodic else None,
                        "pair_evaluations_per_product": images * N * N},
@@ -454,6 +473,7 @@ def run_batched(args, rank, world, local_rank):
     U = [torch.zeros_like(t) for t in q]
     kw = dict(dt=args.dt, delta=args.delta, tol=args.tol, max_iter=64)
     stream = torch.cuda.current_stream()
+    tuned = bt.tune(q, reps=3)  # the tile schedule of this size mix, kept by the context
     step = 0
     for _ in range(args.warmup):
         bt.ab_step(q, U, [step] * B, seeds, **kw)
@@ -512,6 +532,8 @@ def run_batched(args, rank, world, local_rank):
                      "graph_run": {"steps": args.steps, "lanczos_iters_per_step": args.lanczos_iters,
                                    "unconverged_instance_steps": unconv, "host_driven_step_ms": ms_call,
                                    "max_m": m_used},
+                     "tiles": {"tuned": tuned["best"],
+                               "candidates_ms": [[c, round(t, 4)] for c, t in tuned["candidates"]]},
                      "step_ms": [round(x, 3) for x in ms], "gpu_launches": int(launches), "clocks": clocks})
         print(json.dumps(line), flush=True)
     if dist:

@@ -119,6 +119,31 @@ int rpb_set_preconditioner(rpb_ctx *ctx, int kind);
 int rpb_mobility_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
                        double *U);
 
+/* Rows row0 .. row1 - 1 of U = M_tt F + M_tr T (the blocks as for rpb_mobility_apply; all N spheres
+ * are sources): the direct summation of Sec. II.B restricted to a range of targets, so that
+ * processes (one per GPU) can each compute a share of the rows of one suspension's product and
+ * exchange them (rpb_set_product_hook).  row0 must be a multiple of 128, 0 <= row0 < row1 <= N.
+ * U_rows: 3 (row1 - row0) doubles, SoA over the rows ([x_row0 .. x_row1-1 | y .. | z ..]); must not
+ * alias an input.  F or T may be NULL (both NULL gives 0).  Not offered with pseudo-periodic
+ * boundaries (RPB_EINVAL), nor for float32 contexts without the wall. */
+int rpb_mobility_apply_rows(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
+                            int64_t row0, int64_t row1, double *U_rows);
+
+/* A product computed by the caller: must write all 3N entries of U = M_tt F + M_tr T (F or T may be
+ * NULL) on the context's stream and return RPB_OK, or an error code that the library passes on. */
+typedef int (*rpb_product_hook)(void *user, int64_t N, const double *pos, const double *F, const double *T,
+                                double *U);
+
+/* Delegate every product of this context to hook (NULL restores the library's own): rpb_mobility_apply,
+ * the products inside rpb_lanczos_sqrt_apply, rpb_rfd_drift, rpb_ab_step and rpb_step.  It lets a
+ * suspension be shared among processes by target rows (each computes its rows with
+ * rpb_mobility_apply_rows and the rows are gathered, Sec. II.B), while everything else of the step --
+ * forces, noise, the Lanczos recurrence and its float64 Gram-Schmidt and tridiagonal square root, the
+ * drift and the update -- runs unchanged in every process on the gathered vectors.  Inside the hook,
+ * products on this context are the library's own (no recursion).  With a hook, the two-right-hand-side
+ * pass is not used, and rpb_run refuses to run (RPB_EINVAL). */
+int rpb_set_product_hook(rpb_ctx *ctx, rpb_product_hook hook, void *user);
+
 /* Two products at the same positions: U = M_tt F + M_tr T and U2 = M_tt P (the blocks as for
  * rpb_mobility_apply).  A time step needs both at once: the deterministic velocity and the first
  * Lanczos product M v_0 of Sec. II.C.  Where the context can (float32 pairs, wall on, no periodic
@@ -272,6 +297,41 @@ int rpb_batch_run(rpb_batch *bt, int B, const int64_t *N, double *const *pos, do
 #define RPB_PEAK_FFMA 1
 #define RPB_PEAK_DFMA 2
 int rpb_fma_peak(int kind, void *stream, double *tflops, double *ms);
+
+/* Tile schedule of a batch context's float32 products -- what its autotuner chooses (the batched
+ * products are the direct summation of Sec. II.B over each suspension, the same method whatever the
+ * schedule):
+ *   seg_tiles   length, in 128-sphere tiles, of the runs into which the symmetric pass cuts every
+ *               suspension's rows of tiles (one CTA per run), 1 .. 64.  The cut depends only on each
+ *               suspension's own size, so for a given seg_tiles a suspension's result is the same bit
+ *               for bit alone and in any mix; between values it differs in rounding only.
+ *   ctas_per_sm resident CTAs per SM of the symmetric translation-translation kernel, 4 or 5 (no
+ *               effect on the results).
+ *   symmetric   1: the symmetric pass (both directions of a pair from one evaluation); 0: the
+ *               one-way kernel (float64 contexts always use it).
+ * The default is {8, 5, 1} (the environment variable RPB_FP32_BATCH_SYM=0 at creation makes it
+ * one-way). */
+typedef struct {
+    int seg_tiles;
+    int ctas_per_sm;
+    int symmetric;
+} rpb_batch_tiles;
+
+/* Set (t; NULL = the default) or read the tile schedule.  RPB_EINVAL for values outside the ranges
+ * above.  Takes effect from the next call. */
+int rpb_batch_set_tiles(rpb_batch *bt, const rpb_batch_tiles *t);
+int rpb_batch_get_tiles(rpb_batch *bt, rpb_batch_tiles *t);
+
+/* Autotuner: for the batch of B suspensions of sizes N at positions pos (host array of B device
+ * pointers), time every candidate schedule -- the symmetric pass with seg_tiles in {4, 8, 16, 32} at
+ * 4 and 5 CTAs per SM, and the one-way kernel -- by reps products of each kind (unit loads; one
+ * warm-up round first) with CUDA events on the context's stream, weighing ten translation-translation
+ * products per fused one (a step's mix); make the fastest the context's schedule (kept until set
+ * again) and return it in *best (may be NULL).  cand, cand_ms (may be NULL): the first max_cand
+ * candidates and their weighted times in ms; *ncand (may be NULL): the number of candidates.  Float64
+ * contexts have one candidate.  Synchronises the stream; allocates the symmetric plan's scratch. */
+int rpb_batch_tune(rpb_batch *bt, int B, const int64_t *N, const double *const *pos, int reps, rpb_batch_tiles *best,
+                   int max_cand, rpb_batch_tiles *cand, double *cand_ms, int *ncand);
 
 /* Largest N accepted by rpb_mobility_apply_noalloc. */
 #define RPB_NOALLOC_MAX_N 16384

@@ -407,6 +407,44 @@ int rpb_mobility_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double 
     return mobility_apply_impl(ctx, N, pos, F, T, U);
 }
 
+int rpb_mobility_apply_rows(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
+                            int64_t row0, int64_t row1, double *U_rows)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(F, "F", true)) ||
+        (rc = check_vec(T, "T", true)) || (rc = check_vec(U_rows, "U_rows", false)))
+        return rc;
+    if (row0 < 0 || row1 <= row0 || row1 > N || row0 % kTile != 0) {
+        set_error("rows [%lld, %lld) not within [0, N=%lld) with the first a multiple of %d", (long long)row0,
+                  (long long)row1, (long long)N, kTile);
+        return RPB_EINVAL;
+    }
+    if (ctx->Lx > 0.0 || (ctx->p.precision == RPB_FP32 && !ctx->p.wall)) {
+        set_error("row products are not offered with pseudo-periodic boundaries or float32 without the wall");
+        return RPB_EINVAL;
+    }
+    if (U_rows == pos || U_rows == F || U_rows == T) {
+        set_error("U_rows aliases an input");
+        return RPB_EINVAL;
+    }
+    if (!F && !T)
+        return cuda_fail(cudaMemsetAsync(U_rows, 0, 3 * (row1 - row0) * sizeof(double), ctx->stream), "memset U");
+    return mobility_rows_impl(ctx, N, pos, F, T, row0, row1, U_rows);
+}
+
+int rpb_set_product_hook(rpb_ctx *ctx, rpb_product_hook hook, void *user)
+{
+    g_err[0] = 0;
+    if (!ctx) {
+        set_error("null context");
+        return RPB_EINVAL;
+    }
+    ctx->hook = hook;
+    ctx->hook_user = hook ? user : nullptr;
+    return RPB_OK;
+}
+
 int rpb_mobility_apply2(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
                         const double *P, double *U, double *U2)
 {

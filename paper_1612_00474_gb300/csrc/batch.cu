@@ -600,6 +600,8 @@ struct rpb_batch {
     bool sym_enabled = false;
     bool sym_ok = false;
     BatchSymPlan sym;
+    int seg_tiles = 8;  // run length of the symmetric pass's row cut (rpb_batch_set_tiles / rpb_batch_tune)
+    int sym_env = 1;    // RPB_FP32_BATCH_SYM (the symmetric pass unless "0")
 };
 
 namespace rpb {
@@ -695,7 +697,7 @@ static int batch_setup(rpb_batch *bt, int B, const int64_t *N, const int64_t *st
     count_launches(1);
     if ((rc = cuda_fail(cudaGetLastError(), "inst_of"))) return rc;
     bt->sym_ok = false;
-    if (bt->sym_enabled && (rc = batch_sym_plan(bt->sym, B, N, bt->stream, &bt->sym_ok))) return rc;
+    if (bt->sym_enabled && (rc = batch_sym_plan(bt->sym, B, N, bt->stream, &bt->sym_ok, bt->seg_tiles))) return rc;
     return RPB_OK;
 }
 
@@ -1024,7 +1026,8 @@ int rpb_batch_create(rpb_batch **out, const rpb_params *p, int64_t max_total_N, 
     {
         // RPB_FP32_BATCH_SYM=0: float32 products by the one-way kernel instead of the symmetric pass
         const char *v = getenv("RPB_FP32_BATCH_SYM");
-        bt->sym_enabled = p->precision == RPB_FP32 && !(v && strcmp(v, "0") == 0);
+        bt->sym_env = !(v && strcmp(v, "0") == 0);
+        bt->sym_enabled = p->precision == RPB_FP32 && bt->sym_env;
     }
     int dev = 0;
     if (cuda_fail(cudaGetDevice(&dev), "cudaGetDevice") ||
@@ -1091,6 +1094,113 @@ int rpb_batch_set_stream(rpb_batch *bt, void *stream)
     }
     bt->stream = (cudaStream_t)stream;
     return RPB_OK;
+}
+
+int rpb_batch_set_tiles(rpb_batch *bt, const rpb_batch_tiles *t)
+{
+    if (!bt) {
+        set_error("null batch context");
+        return RPB_EINVAL;
+    }
+    rpb_batch_tiles d = {8, 5, bt->sym_env};
+    if (!t) t = &d;
+    if (t->seg_tiles < 1 || t->seg_tiles > 64 || (t->ctas_per_sm != 4 && t->ctas_per_sm != 5) ||
+        (t->symmetric != 0 && t->symmetric != 1)) {
+        set_error("bad tile schedule (seg_tiles=%d ctas_per_sm=%d symmetric=%d)", t->seg_tiles, t->ctas_per_sm,
+                  t->symmetric);
+        return RPB_EINVAL;
+    }
+    bt->seg_tiles = t->seg_tiles;
+    bt->sym.tt_minb = t->ctas_per_sm;
+    bt->sym_enabled = bt->p.precision == RPB_FP32 && t->symmetric;
+    bt->sym_ok = false;  // planned again by the next call
+    return RPB_OK;
+}
+
+int rpb_batch_get_tiles(rpb_batch *bt, rpb_batch_tiles *t)
+{
+    if (!bt || !t) {
+        set_error("null argument to rpb_batch_get_tiles");
+        return RPB_EINVAL;
+    }
+    t->seg_tiles = bt->seg_tiles;
+    t->ctas_per_sm = bt->sym.tt_minb;
+    t->symmetric = bt->sym_enabled ? 1 : 0;
+    return RPB_OK;
+}
+
+int rpb_batch_tune(rpb_batch *bt, int B, const int64_t *N, const double *const *pos, int reps, rpb_batch_tiles *best,
+                   int max_cand, rpb_batch_tiles *cand, double *cand_ms, int *ncand)
+{
+    if (!bt || !N || !pos || reps < 1) {
+        set_error("bad argument to rpb_batch_tune");
+        return RPB_EINVAL;
+    }
+    for (int b = 0; b < B && b < bt->max_B; ++b)
+        if (!pos[b]) {
+            set_error("instance %d: null pos", b);
+            return RPB_EINVAL;
+        }
+    int rc;
+    // candidates: the symmetric pass at every run length and occupancy, and the one-way kernel
+    std::vector<rpb_batch_tiles> cs;
+    if (bt->p.precision == RPB_FP32) {
+        for (int seg : {4, 8, 16, 32})
+            for (int minb : {4, 5}) cs.push_back(rpb_batch_tiles{seg, minb, 1});
+        cs.push_back(rpb_batch_tiles{8, 5, 0});
+    } else {
+        cs.push_back(rpb_batch_tiles{8, 5, 0});  // float64: the one-way kernel only
+    }
+    if ((rc = rpb_batch_set_tiles(bt, &cs[0])) ||
+        (rc = batch_setup(bt, B, N, nullptr, nullptr, const_cast<double *const *>(pos), nullptr, nullptr, nullptr)))
+        return rc;
+    cudaStream_t st = bt->stream;
+    double **v = bt->vec;
+    const int ge = grid_for(3 * bt->total, bt->num_sms);
+    if ((rc = batch_gather(bt, 0, v[V_POS], 0))) return rc;
+    batch_fill3_kernel<<<ge, 256, 0, st>>>(v[V_F], bt->total, 0.0, 0.0, -1.0);
+    batch_fill3_kernel<<<ge, 256, 0, st>>>(v[V_T], bt->total, 0.0, 1.0, 0.0);
+    count_launches(2);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((rc = cuda_fail(cudaEventCreate(&e0), "event")) || (rc = cuda_fail(cudaEventCreate(&e1), "event"))) {
+        if (e0) cudaEventDestroy(e0);
+        return rc;
+    }
+    double best_cost = -1.0;
+    size_t best_k = 0;
+    for (size_t k = 0; k < cs.size() && !rc; ++k) {
+        if ((rc = rpb_batch_set_tiles(bt, &cs[k]))) break;
+        if (bt->sym_enabled && (rc = batch_sym_plan(bt->sym, B, N, st, &bt->sym_ok, bt->seg_tiles))) break;
+        // a step makes about ten translation-translation products per fused one
+        float t_tt = 0.f, t_fu = 0.f;
+        for (int pass = 0; pass < 2 && !rc; ++pass) {  // pass 0 warms up
+            for (int which = 0; which < 2 && !rc; ++which) {
+                const double *T = which ? v[V_T] : nullptr;
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < reps && !rc; ++r) rc = batch_product(bt, v[V_POS], v[V_F], T, v[V_UN], nullptr);
+                cudaEventRecord(e1, st);
+                if (!rc) rc = cuda_fail(cudaEventSynchronize(e1), "tune timing");
+                float ms = 0.f;
+                if (!rc) rc = cuda_fail(cudaEventElapsedTime(&ms, e0, e1), "tune timing");
+                if (pass == 1) (which ? t_fu : t_tt) = ms / reps;
+            }
+        }
+        const double cost = 10.0 * t_tt + t_fu;
+        if (cand && cand_ms && (int)k < max_cand) {
+            cand[k] = cs[k];
+            cand_ms[k] = cost;
+        }
+        if (!rc && (best_cost < 0.0 || cost < best_cost)) {
+            best_cost = cost;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (ncand) *ncand = (int)cs.size();
+    if (best) *best = cs[best_k];
+    return rpb_batch_set_tiles(bt, &cs[best_k]);
 }
 
 int rpb_batch_mobility_apply(rpb_batch *bt, int B, const int64_t *N, const double *const *pos, const double *const *F,

@@ -59,6 +59,20 @@ inline void pair_grid_plan(int64_t N, int num_sms, bool fp64, int slots, int64_t
     *splits = (int)((N + *chunk - 1) / *chunk);
 }
 
+// Split of a product restricted to nt target rows (all N sources): about target_blocks CTAs in all,
+// source chunks of whole tiles (float32) or multiples of 4 sources (float64).
+inline void rows_grid_plan(int64_t nt, int64_t N, int num_sms, bool fp64, int64_t tile, int *splits, int64_t *chunk)
+{
+    const int64_t tblocks = (nt + tile - 1) / tile;
+    const int64_t q = fp64 ? 4 : tile;
+    int64_t S = (target_blocks(num_sms) + tblocks - 1) / tblocks;
+    const int64_t smax = (N + q - 1) / q;
+    if (S > smax) S = smax;
+    if (S < 1) S = 1;
+    *chunk = ((N + S - 1) / S + q - 1) / q * q;
+    *splits = (int)((N + *chunk - 1) / *chunk);
+}
+
 // The split of the allocation-free product: pair_grid_plan without occupancy slots, then at most
 // max_partial_elems / (3N) chunks (its partial sums live in a fixed array of max_partial_elems
 // doubles); chunks stay whole tiles.

@@ -166,21 +166,26 @@ __global__ void __launch_bounds__(kPairThreads) pair_f32_kernel(const SrcF32 *__
 // y_hi[2p], y_hi[2p+1]), (x_lo.., y_lo..), (z~.., Fx..), (Fy.., Fz..), and for torques (Tx.., Ty..)
 // and (Tz[2p], Tz[2p+1]).  Slots past the chunk's end hold a distant source with zero load, whose
 // contribution is exactly zero, so every tile is a full 64 iterations.
+// Targets t0 .. t0 + nt - 1 (t0 a multiple of kTile; nt < 0: all N), partials indexed by i - t0.
 template <bool TORQUE>
 __global__ void __launch_bounds__(kPairThreads, 6) pair_f32x2_kernel(const SrcF32 *__restrict__ src, int N, int chunk,
-                                                                   X2Consts c, double *__restrict__ part)
+                                                                   X2Consts c, double *__restrict__ part, int t0 = 0,
+                                                                   int nt = -1)
 {
     constexpr int P = kTile / 2;
     __shared__ float4 sA[P], sB[P], sC[P], sD[P];
     __shared__ float4 sE[TORQUE ? P : 1];
     __shared__ float2 sG[TORQUE ? P : 1];
+    if (nt < 0) nt = N;
     const int tid = threadIdx.x;
-    const int i = blockIdx.x * kPairThreads + tid;
+    const int li = blockIdx.x * kPairThreads + tid;
+    const int i = t0 + li;
+    const bool live = li < nt && i < N;
     const int j0 = blockIdx.y * chunk;
     const int j1 = min(N, j0 + chunk);
     float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
     float tz = 1.f;
-    if (i < N) {
+    if (live) {
         tp = src[i].p;
         tz = src[i].f.x;
     }
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(kPairThreads, 6) pair_f32x2_kernel(const SrcF3
     const float2 tz2 = make_float2(tz, tz);
     const float2 zero2 = make_float2(0.f, 0.f);
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-    const int diag = blockIdx.x * kTile;
+    const int diag = t0 + blockIdx.x * kTile;
     const int pp = tid >> 1, hh = tid & 1;
     float *fA = reinterpret_cast<float *>(sA);
     float *fB = reinterpret_cast<float *>(sB);
@@ -277,11 +282,11 @@ __global__ void __launch_bounds__(kPairThreads, 6) pair_f32x2_kernel(const SrcF3
         }
         __syncthreads();
     }
-    if (i < N) {
-        const size_t o = (size_t)blockIdx.y * 3 * N;
-        part[o + i] = (double)sx - (double)cx;
-        part[o + N + i] = (double)sy - (double)cy;
-        part[o + 2 * N + i] = (double)sz - (double)cz;
+    if (live) {
+        const size_t o = (size_t)blockIdx.y * 3 * nt;
+        part[o + li] = (double)sx - (double)cx;
+        part[o + nt + li] = (double)sy - (double)cy;
+        part[o + 2 * nt + li] = (double)sz - (double)cz;
     }
 }
 
@@ -727,8 +732,9 @@ __global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_red
     }
 }
 
-constexpr int kTtMinBlocks = 4;     // resident CTAs per SM of the translation-translation form (up to 128 registers:
-                                    // four source pairs per step and the next tile's sources in flight)
+constexpr int kTtMinBlocks = 5;     // resident CTAs per SM of the translation-translation form (up to 102 registers:
+                                    // four source pairs per step and the next tile's sources in flight fit in 96
+                                    // with the polynomial coefficient form; 4 CTAs measured 2.6% slower)
 constexpr int kFusedMinBlocks = 4;  // resident CTAs per SM of the form with torques
 constexpr int kRhs2MinBlocks = 3;  // resident CTAs per SM of the two-right-hand-side form
 constexpr int kPerMinBlocks = 4;   // resident CTAs per SM of the pseudo-periodic forms
@@ -893,17 +899,18 @@ static int grow(void **ptr, size_t *cap, size_t need, const char *what)
     return RPB_OK;
 }
 
-int batch_sym_plan(BatchSymPlan &pl, int B, const int64_t *N, cudaStream_t st, bool *ok)
+int batch_sym_plan(BatchSymPlan &pl, int B, const int64_t *N, cudaStream_t st, bool *ok, int seg_tiles)
 {
     *ok = false;
+    if (seg_tiles < 1) seg_tiles = kBatchSegTiles;
     std::vector<int64_t> sizes(N, N + B);
-    if (pl.valid && sizes == pl.sizes) {
+    if (pl.valid && sizes == pl.sizes && seg_tiles == pl.seg_tiles) {
         *ok = true;
         return RPB_OK;
     }
     pl.valid = false;
     BatchSchedule bs;
-    batch_sym_schedule(B, N, kTile, kBatchSegTiles, bs);
+    batch_sym_schedule(B, N, kTile, seg_tiles, bs);
     std::vector<SymInst> si(B);
     for (int k = 0; k < B; ++k) si[k] = SymInst{(long long)bs.off[k], bs.n[k], bs.tile0[k]};
     const std::vector<int> &seg4 = bs.seg4, &row_seg = bs.row_seg, &col_start = bs.col_start,
@@ -952,6 +959,7 @@ int batch_sym_plan(BatchSymPlan &pl, int B, const int64_t *N, cudaStream_t st, b
     pl.col_off = col_off;
     pl.inst_off = inst_off;
     pl.sizes = sizes;
+    pl.seg_tiles = seg_tiles;
     pl.valid = true;
     *ok = true;
     return RPB_OK;
@@ -968,8 +976,11 @@ int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, 
     if (T)
         pair_f32x2_sym_kernel<kFusedMinBlocks, true, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
             src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
+    else if (pl.tt_minb == 4)
+        pair_f32x2_sym_kernel<4, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
+            src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
     else
-        pair_f32x2_sym_kernel<kTtMinBlocks, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
+        pair_f32x2_sym_kernel<5, false, false, false, true><<<pl.ncta, kPairThreads, 0, st>>>(
             src, n, ctas, segs, c, cs, pl.tgt, pl.srcp, nullptr, PerLen{}, pl.sinst, active);
     pair_sym_reduce_kernel<3, true><<<pl.ntiles, 3 * kTile, 0, st>>>(
         pl.tgt, pl.srcp, pl.index + pl.row_off, cs, n, pos, F, T, make_consts<double>(a), a, 1.0 / (8.0 * kPi * eta),
@@ -980,7 +991,7 @@ int batch_sym_apply(const BatchSymPlan &pl, cudaStream_t st, const SrcF32 *src, 
 
 bool mobility_apply2_ok(const rpb_ctx *ctx, int64_t N)
 {
-    return ctx->sym_rhs2 && ctx->sym_enabled && ctx->p.wall && !(ctx->Lx > 0.0) && N >= 2 * kTile;
+    return !ctx->hook && ctx->sym_rhs2 && ctx->sym_enabled && ctx->p.wall && !(ctx->Lx > 0.0) && N >= 2 * kTile;
 }
 
 int mobility_apply2_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T,
@@ -1016,20 +1027,24 @@ int mobility_apply2_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const dou
 
 template <bool TORQUE, bool WALL = true>
 __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__restrict__ src, int N, int chunk,
-                                                                 PairConsts<double> c, double *__restrict__ part)
+                                                                 PairConsts<double> c, double *__restrict__ part,
+                                                                 int t0 = 0, int nt = -1)
 {
     __shared__ double2 sp[kTile];
     __shared__ double2 sq[kTile];
     __shared__ double2 sr[kTile];
     __shared__ double2 ss[TORQUE ? kTile : 1];
     __shared__ double2 su[TORQUE ? kTile : 1];
+    if (nt < 0) nt = N;
     const int tid = threadIdx.x;
-    const int i = blockIdx.x * kPairThreads + tid;
+    const int li = blockIdx.x * kPairThreads + tid;
+    const int i = t0 + li;
+    const bool live = li < nt && i < N;
     const int j0 = blockIdx.y * chunk;
     const int j1 = min(N, j0 + chunk);
     double2 tp = make_double2(0.0, 0.0);
     double tz = 1.0;
-    if (i < N) {
+    if (live) {
         tp = src[i].p;
         tz = src[i].q.x;
     }
@@ -1074,11 +1089,11 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
         }
         __syncthreads();
     }
-    if (i < N) {
-        const size_t o = (size_t)blockIdx.y * 3 * N;
-        part[o + i] = ux;
-        part[o + N + i] = uy;
-        part[o + 2 * N + i] = uz;
+    if (live) {
+        const size_t o = (size_t)blockIdx.y * 3 * nt;
+        part[o + li] = ux;
+        part[o + nt + li] = uy;
+        part[o + 2 * nt + li] = uz;
     }
 }
 
@@ -1201,19 +1216,23 @@ __global__ void __launch_bounds__(kPairThreads) pair_periodic_f32_kernel(const S
     }
 }
 
-// Sum the chunk partials in order, add the float64 self term, apply s_i / (8 pi eta).
+// Sum the chunk partials in order, add the float64 self term, apply s_i / (8 pi eta).  Targets t0 ..
+// t0 + nt - 1 (nt < 0: all N); U and the partials are indexed by i - t0 with component stride nt.
 __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, int N, const double *__restrict__ pos,
                                    const double *__restrict__ F, const double *__restrict__ T, PairConsts<double> c,
-                                   double a, double scale, double *__restrict__ U, int wall = 1)
+                                   double a, double scale, double *__restrict__ U, int wall = 1, int t0 = 0,
+                                   int nt = -1)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (nt < 0) nt = N;
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t0 + li;
+    if (li >= nt || i >= N) return;
     double ux = 0.0, uy = 0.0, uz = 0.0;
     for (int s = 0; s < splits; ++s) {
-        const size_t o = (size_t)s * 3 * N;
-        ux += part[o + i];
-        uy += part[o + N + i];
-        uz += part[o + 2 * N + i];
+        const size_t o = (size_t)s * 3 * nt;
+        ux += part[o + li];
+        uy += part[o + nt + li];
+        uz += part[o + 2 * nt + li];
     }
     const double z = pos[2 * N + i];
     const double si = wall ? H0(z / a) : 1.0;
@@ -1225,9 +1244,9 @@ __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, 
     else
         self_velocity<true, false>(zc, Fx, Fy, Fz, Tx, Ty, c, ux, uy, uz);
     const double k = si * scale;
-    U[i] = k * ux;
-    U[N + i] = k * uy;
-    U[2 * N + i] = k * uz;
+    U[li] = k * ux;
+    U[nt + li] = k * uy;
+    U[2 * nt + li] = k * uz;
 }
 
 void pair_grid(int64_t N, int num_sms, int precision, int slots, int *splits, int64_t *chunk)
@@ -1258,8 +1277,66 @@ size_t pair_partial_bytes(int64_t max_N, int num_sms)
     return (size_t)3 * sizeof(double) * (size_t)std::max(f64, f32);
 }
 
+// Rows t0 .. t1 - 1 of U = M_tt F + M_tr T (all N sources), written to U_rows with component stride
+// t1 - t0: the one-way kernels restricted to a range of targets (t0 a multiple of kTile).
+int mobility_rows_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, int64_t t0,
+                       int64_t t1, double *U_rows)
+{
+    const int N = (int)N64, nt = (int)(t1 - t0);
+    cudaStream_t st = ctx->stream;
+    const double a = ctx->p.a;
+    const bool fp64 = ctx->p.precision == RPB_FP64;
+    int splits;
+    int64_t chunk;
+    rows_grid_plan(nt, N64, ctx->num_sms, fp64, kTile, &splits, &chunk);
+    if ((size_t)splits * 3 * nt * sizeof(double) > ctx->ws.partial_bytes) {
+        set_error("internal: pair partial buffer too small for rows (nt=%d splits=%d)", nt, splits);
+        return RPB_EINVAL;
+    }
+    double *part = (double *)ctx->ws.partial;
+    const int pb = 256;
+    const dim3 grid((unsigned)((nt + kPairThreads - 1) / kPairThreads), (unsigned)splits);
+    const bool torque = T != nullptr;
+    if (fp64) {
+        SrcF64 *src = (SrcF64 *)ctx->ws.src;
+        pack_f64_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, ctx->p.wall, src);
+        const PairConsts<double> c = make_consts<double>(a);
+        if (!ctx->p.wall) {
+            if (torque)
+                pair_f64_kernel<true, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part, (int)t0, nt);
+            else
+                pair_f64_kernel<false, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part, (int)t0, nt);
+        } else if (torque) {
+            pair_f64_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part, (int)t0, nt);
+        } else {
+            pair_f64_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part, (int)t0, nt);
+        }
+    } else {
+        SrcF32 *src = (SrcF32 *)ctx->ws.src;
+        pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, 1, src);
+        const X2Consts c = make_x2_consts(a);
+        if (torque)
+            pair_f32x2_kernel<true><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part, (int)t0, nt);
+        else
+            pair_f32x2_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part, (int)t0, nt);
+    }
+    const int rb = 64;
+    pair_reduce_kernel<<<(nt + rb - 1) / rb, rb, 0, st>>>(part, splits, N, pos, F, T, make_consts<double>(a), a,
+                                                          1.0 / (8.0 * kPi * ctx->p.eta), U_rows, ctx->p.wall,
+                                                          (int)t0, nt);
+    count_launches(3);
+    return cuda_fail(cudaGetLastError(), "row pair kernels");
+}
+
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, double *U)
 {
+    if (ctx->hook && !ctx->in_hook) {  // the product is delegated (e.g. shared out by rows among processes)
+        ctx->in_hook = 1;
+        const int rc = ctx->hook(ctx->hook_user, N64, pos, F, T, U);
+        ctx->in_hook = 0;
+        if (rc != RPB_OK && rpb_last_error()[0] == 0) set_error("product hook returned %d", rc);
+        return rc;
+    }
     const int N = (int)N64;
     if (ctx->sym_enabled && ctx->p.wall && !(ctx->Lx > 0.0) && F && N >= 2 * kTile && (!T || ctx->sym_fused))
         return mobility_sym(ctx, N, pos, F, T, U);

@@ -128,6 +128,8 @@ struct BatchSymPlan {
     int ncta = 0, nseg = 0, ntiles = 0, seg_off = 0, row_off = 0, col_off = 0, inst_off = 0;
     bool valid = false;
     std::vector<int64_t> sizes;   // the suspension sizes the plan was built for
+    int seg_tiles = 0;            // ... and the run length of its row cut
+    int tt_minb = 5;              // resident CTAs per SM of the translation-translation kernel (4 or 5)
 };
 
 // Scratch owned by a context.
@@ -208,6 +210,9 @@ struct rpb_ctx {
     int f32_slots[2] = {0, 0};  // resident CTAs of the float32 one-way pair kernels (tt, with torques)
     rpb::Workspace ws;
     rpb::RunCtx *run = nullptr; // streams and device state of graph-replayed runs (rpb_run), made on first use
+    rpb_product_hook hook = nullptr;  // products delegated to the caller (rpb_set_product_hook)
+    void *hook_user = nullptr;
+    int in_hook = 0;                  // inside the hook: products are computed here
 };
 
 namespace rpb {
@@ -222,6 +227,9 @@ int cuda_fail(cudaError_t e, const char *what);
 // All pointers device, SoA float64.  Enqueued on ctx->stream.
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
                         double *U);
+// Rows t0 .. t1 - 1 of the product (component stride t1 - t0), one-way kernels over a target range.
+int mobility_rows_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T, int64_t t0,
+                       int64_t t1, double *U_rows);
 // Whether mobility_apply2_impl can take this product (float32 symmetric pass with two right-hand sides).
 bool mobility_apply2_ok(const rpb_ctx *ctx, int64_t N);
 // U = M_tt F + M_tr T and U2 = M_tt P in one symmetric pass (F, T, P non-null).
@@ -249,7 +257,9 @@ int forces_impl(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_para
 // packed one after another; grows the plan's scratch (not inside a stream capture).  Returns RPB_OK,
 // or an error; *ok is false when the plan would need more than the scratch limit (the caller then uses
 // the one-way kernels).
-int batch_sym_plan(BatchSymPlan &pl, int B, const int64_t *N, cudaStream_t st, bool *ok);
+// seg_tiles: the run length of every suspension's row cut (the results depend on it, not on the
+// companions).
+int batch_sym_plan(BatchSymPlan &pl, int B, const int64_t *N, cudaStream_t st, bool *ok, int seg_tiles);
 void batch_sym_free(BatchSymPlan &pl);
 // U_b = M_tt F_b (+ M_tr T_b) for every suspension of the plan, from packed float32 sources; active
 // masks suspensions (null: all).

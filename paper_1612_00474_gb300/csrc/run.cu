@@ -126,6 +126,10 @@ extern "C" int rpb_run(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int
         set_error("nsteps=%d outside [0, 2^32 - 1 - step]", nsteps);
         return RPB_EINVAL;
     }
+    if (ctx->hook) {
+        set_error("rpb_run: a context with a product hook cannot replay its steps from a graph");
+        return RPB_EINVAL;
+    }
     if (unconverged) *unconverged = 0;
     if (nsteps == 0) return RPB_OK;
     const int scheme = opts ? opts->scheme : RPB_SCHEME_AB;

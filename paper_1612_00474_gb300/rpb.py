@@ -23,7 +23,9 @@ EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", 
            "rpb_rfd_drift", "rpb_forces", "rpb_philox_normal", "rpb_ab_step", "rpb_last_error",
            "rpb_launch_count", "rpb_mobility_apply_noalloc", "rpb_batch_create", "rpb_batch_destroy",
            "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step", "rpb_batch_run",
-           "rpb_set_periodic", "rpb_set_preconditioner", "rpb_fma_peak", "rpb_run", "rpb_mobility_apply2")
+           "rpb_set_periodic", "rpb_set_preconditioner", "rpb_fma_peak", "rpb_run", "rpb_mobility_apply2",
+           "rpb_mobility_apply_rows", "rpb_set_product_hook", "rpb_batch_set_tiles", "rpb_batch_get_tiles",
+           "rpb_batch_tune")
 SCHEMES = {"AB": 0, "EM": 1}
 RFDS = {"centred": 0, "one-sided": 1}
 PRECONDITIONERS = {"none": 0, "block-diagonal": 1}
@@ -55,6 +57,18 @@ class ForceParams(ctypes.Structure):
 
 class StepStats(ctypes.Structure):
     _fields_ = [("lanczos_iters", ctypes.c_int), ("lanczos_err", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+# int hook(void *user, int64_t N, const double *pos, const double *F, const double *T, double *U)
+PRODUCT_HOOK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p)
+
+
+class BatchTiles(ctypes.Structure):
+    _fields_ = [("seg_tiles", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("symmetric", ctypes.c_int)]
+
+    def as_dict(self):
+        return dict(seg_tiles=self.seg_tiles, ctas_per_sm=self.ctas_per_sm, symmetric=bool(self.symmetric))
 
 
 class StepOptions(ctypes.Structure):
@@ -102,6 +116,12 @@ def load(build_if_missing=True):
     L.rpb_mobility_apply_noalloc.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp]
     L.rpb_fma_peak.argtypes = [i32, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
     L.rpb_mobility_apply2.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+    L.rpb_mobility_apply_rows.argtypes = [vp, i64, vp, vp, vp, i64, i64, vp]
+    L.rpb_set_product_hook.argtypes = [vp, PRODUCT_HOOK, vp]
+    L.rpb_batch_set_tiles.argtypes = [vp, ctypes.POINTER(BatchTiles)]
+    L.rpb_batch_get_tiles.argtypes = [vp, ctypes.POINTER(BatchTiles)]
+    L.rpb_batch_tune.argtypes = [vp, i32, ctypes.POINTER(i64), vp, i32, ctypes.POINTER(BatchTiles), i32,
+                                 ctypes.POINTER(BatchTiles), ctypes.POINTER(d), ctypes.POINTER(i32)]
     L.rpb_run.argtypes = [vp, i64, vp, vp, i64, u64, i32, d, d, d, i32, ctypes.POINTER(ForceParams),
                           ctypes.POINTER(StepOptions), ctypes.POINTER(StepStats), ctypes.POINTER(i64)]
     pi64 = ctypes.POINTER(i64)
@@ -238,6 +258,28 @@ class Context:
         _check(load().rpb_mobility_apply(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(F, n, "F"), _ptr(T, n, "T"),
                                          _ptr(out, n, "U")))
         return out
+
+    def mobility_apply_rows(self, pos, F, T, row0, row1, out=None):
+        """Rows row0 .. row1 - 1 of M_tt F + M_tr T, as a (3 (row1 - row0),) SoA tensor
+        (rpb_mobility_apply_rows); row0 a multiple of 128."""
+        n = pos.numel()
+        nr = int(row1) - int(row0)
+        out = self._empty(3 * nr, pos) if out is None else out
+        self._bind_stream()
+        _check(load().rpb_mobility_apply_rows(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(F, n, "F"), _ptr(T, n, "T"),
+                                              int(row0), int(row1), _ptr(out, 3 * nr, "U_rows")))
+        return out
+
+    def set_product_hook(self, fn):
+        """Delegate every product of this context to fn(N, pos, F, T, U) -> int, called with raw device
+        pointers (0 for a missing F or T) on the context's stream (rpb_set_product_hook); None
+        restores the library's own products."""
+        if fn is None:
+            self._hook = None
+            _check(load().rpb_set_product_hook(self._h, PRODUCT_HOOK(), None))
+            return
+        self._hook = PRODUCT_HOOK(lambda user, N, pos, F, T, U: fn(int(N), pos or 0, F or 0, T or 0, U or 0))
+        _check(load().rpb_set_product_hook(self._h, self._hook, None))
 
     def mobility_apply2(self, pos, F, T, P, out=None, out2=None):
         """(M_tt F + M_tr T, M_tt P) at the same positions, in one pass where the context can
@@ -392,6 +434,30 @@ class BatchContext:
         _check(load().rpb_batch_mobility_apply(self._h, B, Ns, self._ptrs(pos, "pos"), self._ptrs(F, "F", True),
                                                self._ptrs(T, "T", True), self._ptrs(out, "U")))
         return out
+
+    def set_tiles(self, seg_tiles=8, ctas_per_sm=5, symmetric=True):
+        """Tile schedule of the float32 products (rpb_batch_set_tiles)."""
+        t = BatchTiles(int(seg_tiles), int(ctas_per_sm), 1 if symmetric else 0)
+        _check(load().rpb_batch_set_tiles(self._h, ctypes.byref(t)))
+
+    def get_tiles(self):
+        t = BatchTiles()
+        _check(load().rpb_batch_get_tiles(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def tune(self, pos, reps=3):
+        """Time every candidate tile schedule on this batch and keep the fastest (rpb_batch_tune);
+        returns dict(best=..., candidates=[(schedule, weighted ms), ...])."""
+        B = len(pos)
+        Ns = (ctypes.c_int64 * B)(*[p.numel() // 3 for p in pos])
+        best = BatchTiles()
+        cand = (BatchTiles * 16)()
+        ms = (ctypes.c_double * 16)()
+        nc = ctypes.c_int(0)
+        self._bind_stream()
+        _check(load().rpb_batch_tune(self._h, B, Ns, self._ptrs(pos, "pos"), int(reps), ctypes.byref(best), 16, cand,
+                                     ms, ctypes.byref(nc)))
+        return dict(best=best.as_dict(), candidates=[(cand[k].as_dict(), ms[k]) for k in range(min(nc.value, 16))])
 
     def ab_step(self, pos, U_prev, steps, seeds, dt=0.01, delta=1e-6, tol=1e-3, max_iter=None, weight=1.0, U0=1.0,
                 b=0.1, torque=(0.0, 1.0, 0.0), raise_on_noconv=True):
