@@ -93,8 +93,10 @@ int rpb_set_stream(rpb_ctx *ctx, void *stream);
 /* Pseudo-periodic boundaries parallel to the wall (Appendix B): periods Lx, Ly (> 4a), or both 0 to
  * switch them off (the default).  When on, forces use the minimum image convention and the products
  * sum every source's minimum image and its eight shifts by one period (the unit cell and its eight
- * neighbour cells), i.e. nine times the pair work, with one-way kernels; positions may lie outside
- * the cell (they are folded in for the computation, and returned unfolded). */
+ * neighbour cells), i.e. nine times the pair work: float32 products with forces at N >= 256 in the
+ * symmetric kernel (each pair's nine images evaluated once for both directions), the others (float64,
+ * smaller N, torque-only products) in one-way kernels; positions may lie outside the cell (they are
+ * folded in for the computation, and returned unfolded). */
 int rpb_set_periodic(rpb_ctx *ctx, double Lx, double Ly);
 
 /* Preconditioner of the Lanczos square root (Sec. II.C reports trying a block-diagonal one; the
@@ -173,7 +175,8 @@ int rpb_rfd_drift(rpb_ctx *ctx, int64_t N, const double *pos, const double *Wt, 
                   double *drift);
 
 /* F = -weight z_hat + steric forces (Sec. III, Eq. soft_potential).  Pairs farther apart than
- * 2a + 50 b are skipped (their force is below 2e-22 U0/b).  A coincident pair exerts nothing. */
+ * 2a + 40 b are skipped (their force is below e^-40 U0/b ~ 4e-18 U0/b).  A coincident pair exerts
+ * nothing. */
 int rpb_forces(rpb_ctx *ctx, int64_t N, const double *pos, const rpb_force_params *fp, double *F);
 
 /* Standard normals from Philox4x32-10 (Salmon et al., SC'11): key = (seed low, seed high 32

@@ -19,10 +19,14 @@ Pieces and the passages they follow:
                  preconditioner that section reports trying), RFD drift (Sec. II.A), AB step (Eq. AB).
   philox.py      Philox4x32-10 Gaussian noise (generator of Salmon et al., SC'11).
 
+  equilibrium.py Metropolis Monte Carlo of the Gibbs-Boltzmann distribution (mcmc.c) and
+                 the height density and pair correlation of Appendix B (test statistics).
+
 Parity status: every function is pinned by tests/test_oracle_*.py against
-closed forms, invariants, library routines or brute force; the Philox 4x32
-constants are the published ones and only the 4x64 round structure is pinned
-against numpy's Philox (see philox.py).
+closed forms, invariants, library routines or brute force; Philox4x32-10 is
+pinned against the independent implementation in the Triton library (run on
+the CPU by its interpreter) and its 4x64 round structure against numpy's
+Philox (see philox.py).
 """
 from .core import (ab_step, blake_image_raw, blake_image_raw_batch, dense, forces, freespace_tr, freespace_tt, lanczos_sqrt,  # noqa: F401
                    mobility_apply, noise, pair_blocks, rel_err, rfd_drift, self_diagonal, wall_image_tr,
