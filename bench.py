@@ -94,7 +94,9 @@ def parse():
     ap.add_argument("--hg", type=float, default=1.5, help="fingering: gravitational height h_g / a")
     ap.add_argument("--fing-steps", type=int, default=2500, help="fingering: steps of each run (0.016 s each)")
     ap.add_argument("--sample-every", type=int, default=10, help="fingering: steps between front spectra")
-    ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=500, help="serving: number of requests")
+    ap.add_argument("--serial-sample-s", type=float, default=60.0,
+                    help="serving: seconds of real serial FP64 service measured on a sample of the requests")
     ap.add_argument("--load", type=float, default=0.85, help="serving: offered load relative to measured capacity")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: device-memory budget for resident state")
     ap.add_argument("--max-batch", type=int, default=256, help="serving: requests per batched step")
@@ -189,6 +191,16 @@ def measure_peaks(device_index):
         out[kind + "_ms"] = ms
     out["clocks"] = clocks_stop(clk)
     return out
+
+
+def cpu_baseline_line(args, N):
+    """The FP64 oracle's fused product on a row sample of an N-sphere monolayer, as a cpu_baseline entry."""
+    if args.no_cpu_baseline:
+        return None
+    v, info = oracle_sample(N, args.seed, min(args.cpu_seconds, 10.0))
+    return {"value": v, "unit": "Gpairs/s", "cores": info["cores"], "kind": "oracle",
+            "sample": (f"fused M_tt F + M_tr T of an N={N} monolayer on {info['rows']} target rows x {N} sources "
+                       f"({info['seconds']:.1f} s, FP64 oracle, OpenMP over target rows)")}
 
 
 def run_reference(args, rank, world):
@@ -507,6 +519,21 @@ def run_batched(args, rank, world, local_rank):
     ms = [total_s * 1e3 / args.steps] * args.steps
     # pair evaluations: each instance's converged iteration count (m of the last step as the estimate)
     pairs = args.steps * sum(float(N) * N * (3 + s["m"]) for N, s in zip(sizes, st))
+    # end to end: the states come from pinned host memory and return to it around the same run
+    hq = [t.cpu().pin_memory() for t in q]
+    hU = [t.cpu().pin_memory() for t in U]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d_, h_ in zip(q + U, hq + hU):
+        d_.copy_(h_, non_blocking=True)
+    st_e2e, _ = bt.run(q, U, [step] * B, seeds, nsteps=args.steps, lanczos_iters=args.lanczos_iters,
+                       dt=args.dt, delta=args.delta, tol=args.tol)
+    for d_, h_ in zip(q + U, hq + hU):
+        h_.copy_(d_, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_pairs = args.steps * sum(float(N) * N * (3 + s_["m"]) for N, s_ in zip(sizes, st_e2e))
+    step += args.steps
     # the same instances, one rpb_ab_step call each (one step of all B)
     ctx = rpb.Context(max_N=max(sizes), precision=args.precision, max_iter=64)
     torch.cuda.synchronize()
@@ -532,6 +559,12 @@ def run_batched(args, rank, world, local_rank):
                      "graph_run": {"steps": args.steps, "lanczos_iters_per_step": args.lanczos_iters,
                                    "unconverged_instance_steps": unconv, "host_driven_step_ms": ms_call,
                                    "max_m": m_used},
+                     "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": "Gpairs/s",
+                             "h2d_bytes_per_step": 48.0 * sum(sizes) / args.steps,
+                             "d2h_bytes_per_step": 48.0 * sum(sizes) / args.steps,
+                             "note": "all instances' positions and U^{n-1} copied from pinned host memory before "
+                                     "and back after one graph-replayed run of the timed steps"},
+                     "cpu_baseline": cpu_baseline_line(args, 2048),
                      "tiles": {"tuned": tuned["best"],
                                "candidates_ms": [[c, round(t, 4)] for c, t in tuned["candidates"]]},
                      "step_ms": [round(x, 3) for x in ms], "gpu_launches": int(launches), "clocks": clocks})
@@ -598,13 +631,34 @@ def run_serving(args, rank, world, local_rank):
         ctx.ab_step(qq, UU, 1, 5, delta=1e-6, tol=args.tol)
         torch.cuda.synchronize()
         pts.append((N, time.perf_counter() - t0))
-    ctx.close()
     A = np.array([[1.0, float(N) ** 2] for N, _ in pts])
     coef = np.linalg.lstsq(A, np.array([t for _, t in pts]), rcond=None)[0]
+    # the serial server for real on a sample: requests in arrival order, each served alone by the
+    # single-suspension FP64 path (its steps replayed from a CUDA graph), until the time budget is used;
+    # the measured service times check the fitted model the full queue is simulated with
+    sample = []
+    spent = 0.0
+    for r in sorted(reqs, key=lambda r: r.arrival):
+        pred = r.steps * (coef[0] + coef[1] * r.N * r.N)
+        if spent + pred > args.serial_sample_s:
+            continue
+        qq = torch.tensor(inputs.to_soa(r.pos0), dtype=torch.float64, device="cuda")
+        UU = torch.zeros_like(qq)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.run(qq, UU, 0, r.seed, r.steps, delta=1e-6, tol=args.tol, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        meas = time.perf_counter() - t0
+        spent += meas
+        sample.append({"rid": r.rid, "N": r.N, "steps": r.steps, "measured_s": meas, "predicted_s": pred})
+        if len(sample) >= 24:
+            break
+    ctx.close()
+    scale = (sum(x["measured_s"] for x in sample) / sum(x["predicted_s"] for x in sample)) if sample else 1.0
     tfree, lat64 = 0.0, []
     for r in sorted(reqs, key=lambda r: r.arrival):
         start = max(tfree, r.arrival)
-        tfree = start + r.steps * (coef[0] + coef[1] * r.N * r.N)
+        tfree = start + scale * r.steps * (coef[0] + coef[1] * r.N * r.N)
         lat64.append(tfree - r.arrival)
     line = _base_line(args, 1, srv.pairs / total / 1e9, "Gpairs/s", 1e3 * busy / max(1, len(fin)),
                       "f32" if args.precision == "fp32" else "f64",
@@ -618,8 +672,17 @@ def run_serving(args, rank, world, local_rank):
                                  "p99_latency_s": serve.percentile(lat64, 99),
                                  "request_steps_per_s": req_steps / max(tfree, 1e-9),
                                  "step_time_fit_s": {"c0": coef[0], "c2": coef[1]},
-                                 "basis": "FCFS queue simulated from rpb_ab_step FP64 step times measured at "
-                                          "N = 128, 1024, 4096, 16384"},
+                                 "measured_sample": sample, "fit_scale_from_sample": scale,
+                                 "basis": "FCFS queue over the same arrivals with service times from rpb_ab_step "
+                                          "FP64 step times measured at N = 128, 1024, 4096, 16384 (c0 + c2 N^2), "
+                                          "scaled by the ratio of real serial FP64 service (rpb_run) to that fit "
+                                          "on the measured sample of requests"},
+                 "e2e": {"value": srv.pairs / total / 1e9, "unit": "Gpairs/s",
+                         "h2d_bytes_per_step": 24.0 * sum(r.N for r in fin) / max(1, req_steps),
+                         "d2h_bytes_per_step": 24.0 * sum(r.N for r in fin) / max(1, req_steps),
+                         "note": "each request's initial positions come from host memory and its final positions "
+                                 "return to it inside the served latency; bytes per request-step"},
+                 "cpu_baseline": cpu_baseline_line(args, 4096),
                  "gpu_launches": int(launches), "clocks": clocks})
     print(json.dumps(line), flush=True)
 

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kPairThreads) batch_pair_f64_kernel(
             const double2 s = TORQUE ? ss[k] : make_double2(0.0, 0.0);
             const double2 u = TORQUE ? su[k] : make_double2(0.0, 0.0);
             double dx = 0.0, dy = 0.0, dz = 0.0;
-            pair_velocity<double, TORQUE>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c, dx, dy, dz);
+            pair_velocity_f64<TORQUE>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c, dx, dy, dz);
             if (!(diag && k == tid)) {
                 ux += dx;
                 uy += dy;

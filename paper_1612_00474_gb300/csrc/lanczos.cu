@@ -141,15 +141,25 @@ __global__ void norm_init_kernel(const double *__restrict__ red, int G, double *
     }
 }
 
-// One warp: the tridiagonal step for the single Krylov space (see lanczos_tail_warp).
+// One warp: the tridiagonal step for the single Krylov space (see lanczos_tail_warp).  Inside a
+// replayed graph (runs != null) lane 0 then counts this run of iteration k, records m = k + 1 and lets
+// the conditional node of iteration k + 1 run only if the iteration has not stopped.
 __global__ void __launch_bounds__(32) lanczos_tail_kernel(double *__restrict__ lz, LzLayout L, int k, double tol,
-                                                          const double *__restrict__ red_norm, int Gred)
+                                                          const double *__restrict__ red_norm, int Gred,
+                                                          cudaGraphConditionalHandle next = 0ull, int has_next = 0,
+                                                          unsigned long long *__restrict__ runs = nullptr,
+                                                          int *__restrict__ m_out = nullptr)
 {
     __shared__ double q0[kMaxIter];
     __shared__ double sl[kMaxIter];
     __shared__ double red[32];
     const double bn = warp_sum_partials(red_norm, Gred);  // the same value in every lane
     lanczos_tail_warp(lz, L, k, tol, lz[L.c1 + k] + lz[L.c2 + k], sqrt(bn), q0, sl, red);
+    if (runs && threadIdx.x == 0) {  // lane 0 wrote the status words
+        *runs += 1ull;
+        *m_out = k + 1;
+        if (has_next) cudaGraphSetConditional(next, lz[L.status + ST_STOP] == 0.0 ? 1u : 0u);
+    }
 }
 
 // g[r] = sum_{k < m} y[k] V[k][r]   (y already carries |W|); d_m (optional): read m from the device
@@ -220,16 +230,6 @@ int precond_scale(rpb_ctx *ctx, int64_t N, const double *x, double *out, bool in
                                                                                          inverse ? 1 : 0, out);
     count_launches(1);
     return cuda_fail(cudaGetLastError(), "preconditioner scale");
-}
-
-// Inside a replayed graph, after iteration k - 1 (m = k products so far): count this run, record m, and
-// let iteration k run only if the iteration has not stopped.
-__global__ void lz_iter_kernel(cudaGraphConditionalHandle next, int has_next, const double *__restrict__ status, int m,
-                               unsigned long long *__restrict__ runs, int *__restrict__ m_out)
-{
-    *runs += 1ull;
-    *m_out = m;
-    if (has_next) cudaGraphSetConditional(next, status[ST_STOP] == 0.0 ? 1u : 0u);
 }
 
 int lanczos_init(rpb_ctx *ctx, int64_t N, const double *W, bool *nw_zero, bool graph)
@@ -331,13 +331,14 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
             project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c1, nullptr);
             dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
             project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c2, red_norm);
-            lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G);
+            const bool has_next = k + 1 < max_iter;
+            if (gr)
+                lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G, has_next ? gr->hnd[k + 1] : 0ull,
+                                                      has_next ? 1 : 0, gr->state->iter_runs + k, &gr->state->m);
+            else
+                lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G);
             count_launches(5);
             if (gr) {
-                const bool has_next = k + 1 < max_iter;
-                lz_iter_kernel<<<1, 1, 0, st>>>(has_next ? gr->hnd[k + 1] : 0ull, has_next ? 1 : 0, status, k + 1,
-                                                gr->state->iter_runs + k, &gr->state->m);
-                count_launches(1);
                 if (has_next) {  // v_{k+1} (unused when this iteration stopped)
                     scale_kernel<<<G, kBlasThreads, 0, st>>>(w, n, status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
                     count_launches(1);

@@ -64,7 +64,9 @@ __device__ __forceinline__ void lanczos_tail_warp(double *__restrict__ lz, const
             }
             if (m == l) break;
             double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
+            // |g| <= |d| / (2 DBL_EPSILON |d|) here (e[l] passed the test above), so g^2 + 1 cannot
+            // overflow and the square root needs no hypot
+            double r = sqrt(fma(g, g, 1.0));
             g = d[m] - d[l] + e[l] / (g + copysign(r, g));
             double s = 1.0, c = 1.0, p = 0.0;
             bool restart = false;
@@ -90,11 +92,14 @@ __device__ __forceinline__ void lanczos_tail_warp(double *__restrict__ lz, const
                 p = s * r;
                 d[i + 1] = g + p;
                 g = c * r - bb;
-                const double a0 = z0[i + 1], a1 = z1[i + 1];
+                const double a0 = z0[i + 1];
                 z0[i + 1] = s * z0[i] + c * a0;
                 z0[i] = c * z0[i] - s * a0;
-                z1[i + 1] = s * z1[i] + c * a1;
-                z1[i] = c * z1[i] - s * a1;
+                if (n > 32) {  // rows lane + 32 exist only beyond 32 dimensions (float64 costs per warp instruction)
+                    const double a1 = z1[i + 1];
+                    z1[i + 1] = s * z1[i] + c * a1;
+                    z1[i] = c * z1[i] - s * a1;
+                }
             }
             if (restart) continue;
             d[l] -= p;
@@ -103,17 +108,17 @@ __device__ __forceinline__ void lanczos_tail_warp(double *__restrict__ lz, const
         }
     }
     if (lane == 0)
-        for (int j = 0; j < n; ++j) {
-            q0[j] = z0[j];
-            sl[j] = sqrt(fmax(d[j], 0.0));
-        }
+        for (int j = 0; j < n; ++j) q0[j] = z0[j];
+    // the eigenvalues are the same in every lane: lane j takes the square root of the j-th
+    if (lane < n) sl[lane] = sqrt(fmax(d[lane], 0.0));
+    if (lane + 32 < n) sl[lane + 32] = sqrt(fmax(d[lane + 32], 0.0));
     __syncwarp();
     const double nW = status[ST_NW];
     double y0 = 0.0, y1 = 0.0;
     for (int j = 0; j < n; ++j) {
         const double cj = sl[j] * q0[j];
         y0 = fma(z0[j], cj, y0);
-        y1 = fma(z1[j], cj, y1);
+        if (n > 32) y1 = fma(z1[j], cj, y1);
     }
     y0 *= nW;
     y1 *= nW;

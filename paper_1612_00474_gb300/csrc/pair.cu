@@ -1069,7 +1069,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
                 const double2 p = sp[k], q = sq[k], r = sr[k];
                 const double2 s = TORQUE ? ss[k] : make_double2(0.0, 0.0);
                 const double2 u = TORQUE ? su[k] : make_double2(0.0, 0.0);
-                pair_velocity<double, TORQUE, WALL>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c,
+                pair_velocity_f64<TORQUE, WALL>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c,
                                                     ux, uy, uz);
             }
         } else {
@@ -1078,7 +1078,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const SrcF64 *__
                 const double2 s = TORQUE ? ss[k] : make_double2(0.0, 0.0);
                 const double2 u = TORQUE ? su[k] : make_double2(0.0, 0.0);
                 double dx = 0.0, dy = 0.0, dz = 0.0;
-                pair_velocity<double, TORQUE, WALL>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c,
+                pair_velocity_f64<TORQUE, WALL>(tp.x - p.x, tp.y - p.y, tz, q.x, q.y, r.x, r.y, s.x, s.y, u.x, c,
                                                     dx, dy, dz);
                 if (k != self_k) {
                     ux += dx;
@@ -1144,7 +1144,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_periodic_f64_kernel(const S
             for (int nx = -1; nx <= 1; ++nx)
                 for (int ny = -1; ny <= 1; ++ny) {
                     if (self && nx == 0 && ny == 0) continue;
-                    pair_velocity<double, TORQUE, WALL>(dx + nx * Lx, dy + ny * Ly, tz, s.q.x, s.q.y, s.r.x, s.r.y,
+                    pair_velocity_f64<TORQUE, WALL>(dx + nx * Lx, dy + ny * Ly, tz, s.q.x, s.q.y, s.r.x, s.r.y,
                                                         s.s.x, s.s.y, s.u.x, c, ux, uy, uz);
                 }
         }
@@ -1249,6 +1249,68 @@ __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, 
     U[2 * nt + li] = k * uz;
 }
 
+// The same sum with one warp per target, for products split into many source chunks (small float64
+// products): lane l adds chunks l, l + 32, ... and a butterfly adds the lanes in a fixed order, so the
+// float64 additions spread over many warps instead of one dependent chain per target; lane 0 adds the
+// self term and writes.  Four targets per 128-thread block.
+__global__ void __launch_bounds__(128) pair_reduce_warp_kernel(const double *__restrict__ part, int splits, int N,
+                                                               const double *__restrict__ pos,
+                                                               const double *__restrict__ F,
+                                                               const double *__restrict__ T, PairConsts<double> c,
+                                                               double a, double scale, double *__restrict__ U,
+                                                               int wall, int t0, int nt)
+{
+    const int lane = threadIdx.x & 31;
+    const int li = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int i = t0 + li;
+    if (li >= nt || i >= N) return;  // the same for the whole warp
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int s = lane; s < splits; s += 32) {
+        const size_t o = (size_t)s * 3 * nt;
+        ux += part[o + li];
+        uy += part[o + nt + li];
+        uz += part[o + 2 * nt + li];
+    }
+    for (int m = 16; m > 0; m >>= 1) {
+        ux += __shfl_xor_sync(0xffffffffu, ux, m);
+        uy += __shfl_xor_sync(0xffffffffu, uy, m);
+        uz += __shfl_xor_sync(0xffffffffu, uz, m);
+    }
+    if (lane != 0) return;
+    const double z = pos[2 * N + i];
+    const double si = wall ? H0(z / a) : 1.0;
+    const double zc = wall ? fmax(z, a) : z;
+    const double Fx = F ? si * F[i] : 0.0, Fy = F ? si * F[N + i] : 0.0, Fz = F ? si * F[2 * N + i] : 0.0;
+    const double Tx = T ? si * T[i] : 0.0, Ty = T ? si * T[N + i] : 0.0;
+    if (wall)
+        self_velocity<true, true>(zc, Fx, Fy, Fz, Tx, Ty, c, ux, uy, uz);
+    else
+        self_velocity<true, false>(zc, Fx, Fy, Fz, Tx, Ty, c, ux, uy, uz);
+    const double k = si * scale;
+    U[li] = k * ux;
+    U[nt + li] = k * uy;
+    U[2 * nt + li] = k * uz;
+}
+
+// Chunk partials -> U (targets t0 .. t0 + nt - 1, nt < 0: all N): a thread per target for few chunks
+// (coalesced loads), a warp per target for many.
+static void launch_pair_reduce(cudaStream_t st, const double *part, int splits, int N, const double *pos,
+                               const double *F, const double *T, double a, double scale, double *U, int wall,
+                               int t0 = 0, int nt = -1)
+{
+    if (nt < 0) nt = N;
+    const PairConsts<double> c = make_consts<double>(a);
+    if (splits >= 16) {
+        pair_reduce_warp_kernel<<<(unsigned)((nt + 3) / 4), 128, 0, st>>>(part, splits, N, pos, F, T, c, a, scale, U,
+                                                                          wall, t0, nt);
+    } else {
+        // 64-target CTAs: the float64 self terms of a small product then spread over several SMs
+        const int rb = 64;
+        pair_reduce_kernel<<<(unsigned)((nt + rb - 1) / rb), rb, 0, st>>>(part, splits, N, pos, F, T, c, a, scale, U,
+                                                                          wall, t0, nt);
+    }
+}
+
 void pair_grid(int64_t N, int num_sms, int precision, int slots, int *splits, int64_t *chunk)
 {
     pair_grid_plan(N, num_sms, precision == RPB_FP64, slots, kTile, splits, chunk);
@@ -1320,10 +1382,8 @@ int mobility_rows_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doubl
         else
             pair_f32x2_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part, (int)t0, nt);
     }
-    const int rb = 64;
-    pair_reduce_kernel<<<(nt + rb - 1) / rb, rb, 0, st>>>(part, splits, N, pos, F, T, make_consts<double>(a), a,
-                                                          1.0 / (8.0 * kPi * ctx->p.eta), U_rows, ctx->p.wall,
-                                                          (int)t0, nt);
+    launch_pair_reduce(st, part, splits, N, pos, F, T, a, 1.0 / (8.0 * kPi * ctx->p.eta), U_rows, ctx->p.wall,
+                       (int)t0, nt);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "row pair kernels");
 }
@@ -1389,8 +1449,7 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
             else
                 pair_periodic_f64_kernel<false, false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, Lx, Ly, part);
         }
-        pair_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(part, splits, N, pos, F, T, make_consts<double>(a), a,
-                                                              1.0 / (8.0 * kPi * ctx->p.eta), U, ctx->p.wall);
+        launch_pair_reduce(st, part, splits, N, pos, F, T, a, 1.0 / (8.0 * kPi * ctx->p.eta), U, ctx->p.wall);
         count_launches(4);
         return cuda_fail(cudaGetLastError(), "periodic pair kernels");
     }
@@ -1431,11 +1490,7 @@ int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doub
             pair_f64_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
         }
     }
-    const PairConsts<double> cd = make_consts<double>(a);
-    // 64-sphere CTAs: the float64 self terms of a small product then spread over several SMs
-    const int rb = 64;
-    pair_reduce_kernel<<<(N + rb - 1) / rb, rb, 0, st>>>(part, splits, N, pos, F, T, cd, a,
-                                                          1.0 / (8.0 * kPi * ctx->p.eta), U, ctx->p.wall);
+    launch_pair_reduce(st, part, splits, N, pos, F, T, a, 1.0 / (8.0 * kPi * ctx->p.eta), U, ctx->p.wall);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "pair kernels");
 }
@@ -1925,8 +1980,7 @@ extern "C" int rpb_mobility_apply_noalloc(int64_t N64, const double *pos, const 
         else
             pair_f64_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part);
     }
-    pair_reduce_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(part, splits, N, pos, F, T, make_consts<double>(a), a,
-                                                          1.0 / (8.0 * kPi * p->eta), U);
+    launch_pair_reduce(st, part, splits, N, pos, F, T, a, 1.0 / (8.0 * kPi * p->eta), U, 1);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "rpb_mobility_apply_noalloc kernels");
 }

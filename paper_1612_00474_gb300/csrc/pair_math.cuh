@@ -103,6 +103,77 @@ __device__ __forceinline__ void pair_velocity(R rx, R ry, R zi, R zj, R Fx, R Fy
     }
 }
 
+// Float64 target velocity from one source with the wall: the same block as pair_velocity, its wall
+// coefficients evaluated as polynomials in s = 1/|R|^2 with height-only coefficients (see the
+// packed float32 form below for the algebra): about half the float64 operations of the direct
+// form, which matters where float64 runs at a small fraction of the float32 rate.  Valid for r = 0
+// (the self pair, r2 = 0, takes the overlap branch).  Accumulates into (ux, uy, uz).
+template <bool TORQUE>
+__device__ __forceinline__ void pair_velocity_wall64(double rx, double ry, double zi, double zj, double Fx, double Fy,
+                                                     double Fz, double Tx, double Ty, double Tz,
+                                                     const PairConsts<double> &c, double &ux, double &uy, double &uz)
+{
+    const double a2 = c.a2, a4 = a2 * a2;
+    const double rz = zi - zj;
+    const double rho2 = fma(rx, rx, ry * ry);
+    const double r2 = fma(rz, rz, rho2);
+    const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;
+    const double r = r2 * ir;
+    const double Rz = zi + zj;
+    const double Z = Rz * Rz;
+    const double u = rsqrt(rho2 + Z);
+    const double ir2 = ir * ir, ir3 = ir * ir2;
+    const bool far = r >= c.two_a;
+    const double c1mu = far ? fma(c.two_3_a2, ir3, ir - u) : fma(c.near_c1, fma(-c.near_r, r, 1.0), -u);
+    const double c2 = far ? fma(-c.two_a2, ir3 * ir2, ir3) : c.near_c2 * ir;
+    const double s = u * u, u3 = s * u, u5 = u3 * s, sZ = s * Z;
+    const double p = fma(-2.0 * zj, zi, -(2.0 / 3.0) * a2);
+    const double q = fma(c.two_a2, Z, (2.0 / 3.0) * a4);
+    const double XA = fma(s, fma(sZ, (-10.0 / 3.0) * a4, q), p);
+    const double XB2 = fma(s, fma(sZ, (140.0 / 3.0) * a4, fma(-20.0 * a2, Z, (-20.0 / 3.0) * a4)), -6.0 * p);
+    const double Eh = fma(s, fma(sZ, 20.0 * a4, fma(-4.0 * a2, Z, (-8.0 / 3.0) * a4)), -4.0 * zj * zj);
+    const double b2 = u5 * XB2;
+    const double T2 = 2.0 * u3 * zj;
+    const double u5Rz = u5 * Rz, u7Rz = u5Rz * s;
+    const double cF = fma(u3, XA, c1mu);
+    const double cFE = fma(u3, Eh, cF);
+    const double B3 = fma(0.5, b2, -u3);
+    const double C3 = fma(-Rz, b2, fma(u7Rz, (20.0 / 3.0) * a4, T2));
+    const double D3 = fma(u7Rz, (-20.0 / 3.0) * a4, T2);
+    const double pF = fma(rx, Fx, ry * Fy);
+    const double w = fma(Rz, Fz, pF);
+    const double k2 = c2 * fma(rz, Fz, pF);
+    const double ke = fma(B3, w, C3 * Fz);
+    const double kk = k2 + ke;
+    ux = fma(cF, Fx, fma(kk, rx, ux));
+    uy = fma(cF, Fy, fma(kk, ry, uy));
+    uz = fma(cFE, Fz, fma(k2, rz, fma(ke, Rz, fma(D3, w, uz))));
+    if (TORQUE) {
+        const double ct = far ? ir3 : c.near_tr * fma(-c.near_tr_r, r, 1.0);
+        const double dcp = ct - u3;
+        const double m2 = fma(u5Rz, c.two_a2, dcp * rz);
+        const double kt = fma(6.0 * zi, u5, -10.0 * a2 * u7Rz);
+        const double zt = fma(-Rz, kt, fma(-c.two_a2, u5, dcp));
+        const double tz3 = fma(Tx, ry, -(Ty * rx));
+        const double dTz = dcp * Tz, ktz = kt * tz3;
+        ux = fma(Ty, m2, fma(-dTz, ry, fma(-ktz, rx, ux)));
+        uy = fma(-Tx, m2, fma(dTz, rx, fma(-ktz, ry, uy)));
+        uz = fma(tz3, zt, uz);
+    }
+}
+
+// The float64 pair of the kernels: the polynomial form with the wall, the free-space form without.
+template <bool TORQUE, bool WALL = true>
+__device__ __forceinline__ void pair_velocity_f64(double rx, double ry, double zi, double zj, double Fx, double Fy,
+                                                  double Fz, double Tx, double Ty, double Tz,
+                                                  const PairConsts<double> &c, double &ux, double &uy, double &uz)
+{
+    if (WALL)
+        pair_velocity_wall64<TORQUE>(rx, ry, zi, zj, Fx, Fy, Fz, Tx, Ty, Tz, c, ux, uy, uz);
+    else
+        pair_velocity<double, TORQUE, false>(rx, ry, zi, zj, Fx, Fy, Fz, Tx, Ty, Tz, c, ux, uy, uz);
+}
+
 // Self term M_ii (F, T) in float64, in units of 1/(8 pi eta), F and T with s_i folded in, at the
 // clamped height h: the r = 0 limit of pair_velocity in closed form.  With x = a/h the wall-corrected
 // self mobilities are mu0 (1 - 9x/16 + x^3/8 - x^5/16) parallel and mu0 (1 - 9x/8 + x^3/2 - x^5/8)

@@ -15,7 +15,10 @@ paper's units); 12000 steps per scheme, sampled every 20.
 
 Bounds: the statistical error of each histogram bin is estimated by batch means over 6 blocks of
 each run (BD and Monte Carlo), and the comparison allows 4 combined standard errors plus a bias
-allowance for the finite dt, stated below with the values measured when they were set.
+allowance for the finite dt (1% of the mean height, 5% of the peak of P(h), 0.05 in g), and bounds
+the L2 errors of P(h) and g(r) (the paper's measure, Fig. 4 inset) by 0.03 and 0.06.  Measured when
+they were set (GB300): EM mean height -0.004 (standard error 0.006) off, L2 errors 0.011 and 0.032;
+AB -0.014 (0.008), 0.011 and 0.026.
 """
 import math
 
@@ -95,8 +98,8 @@ def test_interacting_equilibrium(gpu_lib, monte_carlo, scheme):
     bd_samples = _bd(gpu_lib, S_mc[-1], scheme)
     assert np.isfinite(bd_samples).all() and bd_samples[..., 2].min() > 0.5
     r = _compare(_stats(bd_samples), mc, scheme)
-    # bias allowance of the finite dt, beside 4 standard errors (set from the measured errors, see docstring)
-    assert abs(r["dh"]) <= 4 * r["sh"] + 0.02 * mc["h"]
-    assert np.all(np.abs(r["dP"]) <= 4 * r["sP"] + 0.1 * mc["P"].max())
-    assert np.all(np.abs(r["dg"]) <= 4 * r["sg"] + 0.1)
-    assert r["l2P"] <= 0.1 and r["l2g"] <= 0.15
+    # 4 standard errors plus the finite-dt bias allowance (see the docstring for the measured values)
+    assert abs(r["dh"]) <= 4 * r["sh"] + 0.01 * mc["h"]
+    assert np.all(np.abs(r["dP"]) <= 4 * r["sP"] + 0.05 * mc["P"].max())
+    assert np.all(np.abs(r["dg"]) <= 4 * r["sg"] + 0.05)
+    assert r["l2P"] <= 0.03 and r["l2g"] <= 0.06

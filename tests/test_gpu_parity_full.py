@@ -9,6 +9,7 @@ increment split into the parts the tolerances of the method's readings apply to.
   - One FP64 AB step of the 256-sphere configuration with its increment split: the velocity U^n and
     the Brownian increment g at 1e-10, the drift at its a/delta-amplified bound (reported), and the
     increment without the drift (dt (3/2 U^n - 1/2 U^{n-1}) + sqrt(2 kT dt) g) at 1e-10.
+  - The FP32 path's drift (delta = 5e-3 a) against the FP64 oracle's (delta = 1e-6 a), reported.
 """
 import numpy as np
 import pytest
@@ -37,7 +38,7 @@ def maxrel(x, ref):
 def test_two_rhs_pass_n65536_sampled_rows(gpu_lib):
     N = 65536
     pos = inputs.monolayer(N, seed=0)
-    F = O.forces(pos[:0]) if False else inputs.vectors(N, 9)
+    F = inputs.vectors(N, 9)
     T = np.tile([0.0, 1.0, 0.0], (N, 1))
     W = O.noise(N, 0, 0, 0)
     P = W / np.linalg.norm(W)  # v_0 of the Lanczos iteration
@@ -121,3 +122,24 @@ def test_ab_step_increment_parts_n256(gpu_lib):
     assert e <= 1e-10, e
     # and the whole increment, the drift's share included
     assert maxrel(inc, inc_ref) <= 1e-8
+
+
+def test_fp32_drift_against_fp64_oracle_drift(gpu_lib):
+    """The float32 path computes the RFD drift with delta = 5e-3 a (delta ~ eps^(1/3) a for float32
+    products, Sec. II.A); its distance from the FP64 oracle's drift at delta = 1e-6 a is the
+    truncation error O(delta^2) plus the float32 product error amplified by a/delta.  Bound 1e-3
+    relative (max-norm); the value is printed."""
+    N = 4096
+    pos = inputs.monolayer(N, seed=31)
+    Wt = O.noise(N, 7, 0, 1)
+    ref = O.rfd_drift(pos, Wt, delta=1e-6)
+    ctx = gpu_lib.Context(max_N=N, precision="fp32", max_iter=16)
+    try:
+        got = host(ctx.rfd_drift(dev(pos), dev(Wt), delta=5e-3), N)
+    finally:
+        ctx.close()
+    err = maxrel(got, ref)
+    l2 = O.rel_err(got, ref)
+    print(f"\nFP32 drift (delta = 5e-3 a) vs FP64 oracle drift (delta = 1e-6 a), N = {N}: max-norm {err:.2e}, "
+          f"2-norm {l2:.2e}")
+    assert err <= 1e-3
