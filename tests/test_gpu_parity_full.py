@@ -126,20 +126,27 @@ def test_ab_step_increment_parts_n256(gpu_lib):
 
 def test_fp32_drift_against_fp64_oracle_drift(gpu_lib):
     """The float32 path computes the RFD drift with delta = 5e-3 a (delta ~ eps^(1/3) a for float32
-    products, Sec. II.A); its distance from the FP64 oracle's drift at delta = 1e-6 a is the
-    truncation error O(delta^2) plus the float32 product error amplified by a/delta.  Bound 1e-3
-    relative (max-norm); the value is printed."""
+    products, Sec. II.A).  Against the FP64 oracle at the same delta its error is the float32 product
+    error amplified by a/delta: bound 1e-3 (max-norm).  Against the oracle at delta = 1e-6 a it also
+    carries the finite difference's truncation, which the regularised mobility makes first order
+    where it is not smooth -- spheres within delta of the clamp height z = a and pairs within delta of
+    contact r = 2a (the oracle alone differs from itself by the same amount between the two deltas);
+    that distance is printed and bounded loosely (2-norm 0.05)."""
     N = 4096
     pos = inputs.monolayer(N, seed=31)
     Wt = O.noise(N, 7, 0, 1)
-    ref = O.rfd_drift(pos, Wt, delta=1e-6)
+    ref_same = O.rfd_drift(pos, Wt, delta=5e-3)
+    ref_fine = O.rfd_drift(pos, Wt, delta=1e-6)
     ctx = gpu_lib.Context(max_N=N, precision="fp32", max_iter=16)
     try:
         got = host(ctx.rfd_drift(dev(pos), dev(Wt), delta=5e-3), N)
     finally:
         ctx.close()
-    err = maxrel(got, ref)
-    l2 = O.rel_err(got, ref)
-    print(f"\nFP32 drift (delta = 5e-3 a) vs FP64 oracle drift (delta = 1e-6 a), N = {N}: max-norm {err:.2e}, "
-          f"2-norm {l2:.2e}")
+    err = maxrel(got, ref_same)
+    fine_max, fine_l2 = maxrel(got, ref_fine), O.rel_err(got, ref_fine)
+    oracle_l2 = O.rel_err(ref_same, ref_fine)
+    print(f"\nFP32 drift (delta = 5e-3 a), N = {N}: vs the FP64 oracle at the same delta {err:.2e} (max-norm); "
+          f"vs the oracle at delta = 1e-6 a {fine_max:.2e} (max-norm), {fine_l2:.2e} (2-norm); the oracle's own "
+          f"change between the two deltas {oracle_l2:.2e} (2-norm)")
     assert err <= 1e-3
+    assert fine_l2 <= 0.05
