@@ -333,6 +333,10 @@ int rpb_destroy(rpb_ctx *ctx)
     g_err[0] = 0;
     int rc = cuda_fail(cudaStreamSynchronize(ctx->stream), "rpb_destroy sync");
     run_free(ctx);
+    if (ctx->lz_side) cudaStreamSynchronize(ctx->lz_side);
+    if (ctx->lz_ev_a) cudaEventDestroy(ctx->lz_ev_a);
+    if (ctx->lz_ev_t) cudaEventDestroy(ctx->lz_ev_t);
+    if (ctx->lz_side) cudaStreamDestroy(ctx->lz_side);
     free_ws(ctx->ws);
     delete ctx;
     return rc;

@@ -127,6 +127,22 @@ __global__ void scale_kernel(const double *__restrict__ w, int64_t n, const doub
         v[r] = w[r] * s;
 }
 
+// v[r] = w[r] / |w|, |w|^2 summed from the norm partials by one warp in the fixed order the
+// tridiagonal kernel uses for beta_k (so 1/|w| is bitwise its 1/beta_k).
+__global__ void scale_norm_kernel(const double *__restrict__ w, int64_t n, const double *__restrict__ red_norm,
+                                  int Gred, double *__restrict__ v)
+{
+    __shared__ double inv;
+    if (threadIdx.x < 32) {
+        const double bn = warp_sum_partials(red_norm, Gred);
+        if (threadIdx.x == 0) inv = 1.0 / sqrt(bn);
+    }
+    __syncthreads();
+    const double s = inv;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        v[r] = w[r] * s;
+}
+
 // |W| from its squared-norm partials.
 __global__ void norm_init_kernel(const double *__restrict__ red, int G, double *__restrict__ status)
 {
@@ -274,6 +290,17 @@ int lanczos_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, do
     return lanczos_run(ctx, N, pos, g, tol, max_iter, false, iters_out, err_out, converged_out, gr);
 }
 
+// w = M v (with the preconditioner: P M P v), on the context's stream
+static int lanczos_product(rpb_ctx *ctx, int64_t N, const double *pos, const double *v, double *w)
+{
+    int rc;
+    if (!ctx->precond) return mobility_apply_impl(ctx, N, pos, v, nullptr, w);
+    if ((rc = precond_scale(ctx, N, v, ctx->ws.pcx, false)) ||
+        (rc = mobility_apply_impl(ctx, N, pos, ctx->ws.pcx, nullptr, w)))
+        return rc;
+    return precond_scale(ctx, N, w, w, false);
+}
+
 int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double tol, int max_iter, bool first_done,
                 int *iters_out, double *err_out, int *converged_out, LzGraph *gr)
 {
@@ -306,7 +333,62 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
                 return rc;
         }
     }
+    // Host-driven: the tridiagonal step of iteration k runs on a side stream while the context's
+    // stream goes on with v_{k+1} = w / |w| and, for short products, the product M v_{k+1} (discarded if
+    // iteration k stopped); the norm partials alternate between two buffers so that the side stream's
+    // reads never meet the next iteration's writes.
+    if (!gr && !ctx->lz_side) {
+        if ((rc = cuda_fail(cudaStreamCreateWithFlags(&ctx->lz_side, cudaStreamNonBlocking), "lanczos side stream")) ||
+            (rc = cuda_fail(cudaEventCreateWithFlags(&ctx->lz_ev_a, cudaEventDisableTiming), "lanczos event")) ||
+            (rc = cuda_fail(cudaEventCreateWithFlags(&ctx->lz_ev_t, cudaEventDisableTiming), "lanczos event")))
+            return rc;
+    }
+    // Speculate only where a product is short: one product is wasted per solve (after the stopping
+    // iteration) and about one tridiagonal step (~55 us) is saved per iteration; the estimate uses the
+    // measured per-pair times of the one-way float64 and symmetric float32 kernels on this part.
+    const double t_product = (ctx->Lx > 0.0 ? 9.0 : 1.0) * (double)N * (double)N *
+                             (ctx->p.precision == RPB_FP64 ? 5e-10 : 1.3e-12);
+    const bool speculate = t_product < 3e-4;
+    bool have_product = false;  // w already holds M v_k (the speculative product of iteration k - 1)
     for (int k = 0; k < max_iter; ++k) {
+        if (!gr) {
+            const double *vk = V + (size_t)k * ld;
+            double *rn = red + (size_t)(ctx->max_iter + 1 + (k & 1)) * G;
+            rc = RPB_OK;
+            if (!(k == 0 && first_done) && !have_product) rc = lanczos_product(ctx, N, pos, vk, w);
+            have_product = false;
+            if (rc) return rc;
+            const int nv = k + 1;
+            dots_kernel<<<dim3(G, nv), kBlasThreads, 0, main_st>>>(V, ld, n, w, red);
+            project_out_kernel<<<G, kBlasThreads, 0, main_st>>>(V, ld, n, nv, red, G, w, lz + L.c1, nullptr);
+            dots_kernel<<<dim3(G, nv), kBlasThreads, 0, main_st>>>(V, ld, n, w, red);
+            project_out_kernel<<<G, kBlasThreads, 0, main_st>>>(V, ld, n, nv, red, G, w, lz + L.c2, rn);
+            if ((rc = cuda_fail(cudaEventRecord(ctx->lz_ev_a, main_st), "event record")) ||
+                (rc = cuda_fail(cudaStreamWaitEvent(ctx->lz_side, ctx->lz_ev_a, 0), "stream wait")))
+                return rc;
+            lanczos_tail_kernel<<<1, 32, 0, ctx->lz_side>>>(lz, L, k, tol, rn, G);
+            count_launches(5);
+            if ((rc = cuda_fail(cudaMemcpyAsync(hs, status, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->lz_side),
+                                "status copy")) ||
+                (rc = cuda_fail(cudaEventRecord(ctx->lz_ev_t, ctx->lz_side), "event record")))
+                return rc;
+            if (k + 1 < max_iter) {  // v_{k+1} (unused if this iteration stops)
+                scale_norm_kernel<<<G, kBlasThreads, 0, main_st>>>(w, n, rn, G, V + (size_t)(k + 1) * ld);
+                count_launches(1);
+                if (speculate) {
+                    if ((rc = lanczos_product(ctx, N, pos, V + (size_t)(k + 1) * ld, w))) return rc;
+                    have_product = true;
+                }
+            }
+            if ((rc = cuda_fail(cudaEventSynchronize(ctx->lz_ev_t), "lanczos iteration"))) return rc;
+            m = k + 1;
+            eps = hs[ST_EPS];
+            if (hs[ST_STOP] != 0.0) {
+                stopped = true;
+                break;
+            }
+            continue;
+        }
         const bool cond = gr && k >= 1;
         if (cond) {
             if ((rc = graph_begin_if(main_st, gr->body, gr->hnd[k]))) return rc;
@@ -316,15 +398,7 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
         const uint64_t before = rpb_launch_count();
         const double *vk = V + (size_t)k * ld;
         rc = RPB_OK;
-        if (!(k == 0 && first_done)) {
-            if (ctx->precond) {  // w = P M P v_k
-                if (!(rc = precond_scale(ctx, N, vk, ctx->ws.pcx, false)) &&
-                    !(rc = mobility_apply_impl(ctx, N, pos, ctx->ws.pcx, nullptr, w)))
-                    rc = precond_scale(ctx, N, w, w, false);
-            } else {
-                rc = mobility_apply_impl(ctx, N, pos, vk, nullptr, w);
-            }
-        }
+        if (!(k == 0 && first_done)) rc = lanczos_product(ctx, N, pos, vk, w);
         if (!rc) {
             const int nv = k + 1;
             dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
@@ -332,32 +406,14 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
             dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
             project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c2, red_norm);
             const bool has_next = k + 1 < max_iter;
-            if (gr)
-                lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G, has_next ? gr->hnd[k + 1] : 0ull,
-                                                      has_next ? 1 : 0, gr->state->iter_runs + k, &gr->state->m);
-            else
-                lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G);
+            lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G, has_next ? gr->hnd[k + 1] : 0ull,
+                                                  has_next ? 1 : 0, gr->state->iter_runs + k, &gr->state->m);
             count_launches(5);
-            if (gr) {
-                if (has_next) {  // v_{k+1} (unused when this iteration stopped)
-                    scale_kernel<<<G, kBlasThreads, 0, st>>>(w, n, status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
-                    count_launches(1);
-                }
-                rc = cuda_fail(cudaGetLastError(), "lanczos kernels");
-            } else {
-                if (!(rc = cuda_fail(cudaMemcpyAsync(hs, status, 8 * sizeof(double), cudaMemcpyDeviceToHost, st),
-                                     "status copy")))
-                    rc = cuda_fail(cudaStreamSynchronize(st), "lanczos iteration");
-                if (!rc) {
-                    m = k + 1;
-                    eps = hs[ST_EPS];
-                    if (hs[ST_STOP] != 0.0) stopped = true;
-                    if (!stopped && k + 1 < max_iter) {
-                        scale_kernel<<<G, kBlasThreads, 0, st>>>(w, n, status, ST_INV_BETA, V + (size_t)(k + 1) * ld);
-                        count_launches(1);
-                    }
-                }
+            if (has_next) {  // v_{k+1} (unused when this iteration stopped)
+                scale_norm_kernel<<<G, kBlasThreads, 0, st>>>(w, n, red_norm, G, V + (size_t)(k + 1) * ld);
+                count_launches(1);
             }
+            rc = cuda_fail(cudaGetLastError(), "lanczos kernels");
         }
         if (cond) {
             gr->iter_launches[k] = (int)(rpb_launch_count() - before);
@@ -369,6 +425,8 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
         if (rc) return rc;
         if (stopped) break;
     }
+    // the combination reads y, which the side stream's tridiagonal step wrote
+    if (!gr && (rc = cuda_fail(cudaStreamWaitEvent(main_st, ctx->lz_ev_t, 0), "stream wait"))) return rc;
     combine_kernel<<<G, kBlasThreads, 0, main_st>>>(V, ld, n, m, lz + L.y, g, gr ? &gr->state->m : nullptr);
     count_launches(1);
     if (ctx->precond && (rc = precond_scale(ctx, N, g, g, true))) return rc;  // g = D^{1/2} y

@@ -213,6 +213,9 @@ struct rpb_ctx {
     rpb_product_hook hook = nullptr;  // products delegated to the caller (rpb_set_product_hook)
     void *hook_user = nullptr;
     int in_hook = 0;                  // inside the hook: products are computed here
+    // host-driven Lanczos: the side stream its tridiagonal steps run on, and its two events
+    cudaStream_t lz_side = nullptr;
+    cudaEvent_t lz_ev_a = nullptr, lz_ev_t = nullptr;
 };
 
 namespace rpb {
