@@ -68,7 +68,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--N", type=int, default=65536)
+    ap.add_argument("--N", type=int, default=None,
+                    help="spheres; default 65536 (monolayer, reference arm, bound of the lanczos sweep), 4096 "
+                         "(accuracy) or 32768 (fingering)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--dt", type=float, default=0.01)
     ap.add_argument("--delta", type=float, default=None,
@@ -78,9 +80,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--periodic", action="store_true",
                     help="monolayer: pseudo-periodic boundaries with the monolayer's square as the unit cell")
-    ap.add_argument("--split", choices=["replicas", "rows"], default="replicas",
+    ap.add_argument("--split", choices=["replicas", "pairs", "rows"], default="replicas",
                     help="monolayer under torchrun: independent replicas (weak scaling) or one suspension whose "
-                         "products are shared by target rows among the ranks (strong scaling)")
+                         "products are shared among the ranks (strong scaling), by equal runs of the symmetric "
+                         "pass's pair triangle summed with an all-reduce (pairs) or by target rows gathered with "
+                         "an all-gather (rows)")
     ap.add_argument("--precondition", action="store_true",
                     help="monolayer: block-diagonal Lanczos preconditioner (an option; the paper's runs use none)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -264,12 +268,13 @@ def run_ours(args, rank, world, local_rank):
     dist = init_dist(world)
 
     N = args.N
-    rows = args.split == "rows" and world > 1
-    if rows:  # one suspension, its products shared by target rows (same seed and state on every rank)
+    shared = args.split in ("pairs", "rows") and world > 1
+    rows = shared and args.split == "rows"
+    if shared:  # one suspension, its products shared among the ranks (same seed and state on every rank)
         from paper_1612_00474_gb300.split import SplitContext
 
         seed = args.seed
-        ctx = SplitContext(N, precision=args.precision, max_iter=64)
+        ctx = SplitContext(N, mode=args.split, precision=args.precision, max_iter=64)
     else:
         seed = args.seed + rank  # independent replicas, one suspension per rank
         ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=64)
@@ -366,7 +371,7 @@ def run_ours(args, rank, world, local_rank):
     # max of the times and sum of the work over ranks
     # max of the times over ranks; the work summed over ranks for replicas, once for a shared suspension
     (total_s, e2e_s), (pairs, e2e_pairs) = aggregate(dist, [total_s, e2e_s], [pairs, e2e_pairs], device="cuda")
-    if rows:
+    if shared:
         pairs, e2e_pairs = pairs / world, e2e_pairs / world
     if dist:
         dist.barrier()
@@ -393,6 +398,7 @@ def run_ours(args, rank, world, local_rank):
             peak_basis = (f"measured on this GPU by rpb_fma_peak: DFMA {peak:.3f} TFLOP/s (nominal "
                           f"{FP64_NOMINAL_TFLOPS})")
         sym = args.precision == "fp32" and os.environ.get("RPB_FP32_SYM") != "0" and N >= 256 and not rows
+        share = 1.0 / world if shared else 1.0  # rank 0's share of the triangle's tile units (pairs split)
         diag = float(N) * 128
         if args.periodic and sym:  # nine images of each unordered pair once, both ways
             flops_tt = 9.0 * (FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag)
@@ -401,8 +407,11 @@ def run_ours(args, rank, world, local_rank):
             flops_tt = 9.0 * N * N * FLOPS_TT
             kernel = f"pair_periodic_f{args.precision[2:]}_kernel<false,true> (translation-translation, 9 images)"
         elif sym:  # each unordered pair once (135 flop) except inside the 128-wide diagonal tiles (106 flop each way)
-            flops_tt = FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag
+            flops_tt = share * (FLOPS_SYM * (float(N) * N - diag) / 2 + FLOPS_TT * diag)
             kernel = "pair_f32x2_sym_kernel (translation-translation, reciprocity)"
+            if shared:
+                kernel += (f" over rank 0's share (1/{world} of the triangle's tile units), timed with the "
+                           f"all-reduce of the partial products")
         elif rows:  # this rank's rows against all sources, timed with the all-gather of the other rows
             a_, b_ = ctx.split(N).mine
             flops_tt = float(b_ - a_) * N * FLOPS_TT
@@ -417,7 +426,7 @@ def run_ours(args, rank, world, local_rank):
             # the FP32 pipe's operation rate: one lane operation per lane per clock, whether an FMA, a
             # multiply or an add (a third of the pair's operations are multiplies and adds that cannot be
             # fused, so the flop fraction understates how busy the pipe is)
-            ops = (9.0 if args.periodic else 1.0) * OPS_SYM_KERNEL * (float(N) * N - diag) / 2
+            ops = share * (9.0 if args.periodic else 1.0) * OPS_SYM_KERNEL * (float(N) * N - diag) / 2
             ops_peak = fp32_peak / 2  # one FMA is one lane operation
             ops_view = {"per_unordered_pair": OPS_SYM_KERNEL, "basis": "the kernel's own operation count",
                         "achieved": ops / t_tt / 1e12, "peak": ops_peak, "unit": "Top/s",
@@ -426,15 +435,15 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "strong" if rows else "weak", "vs_baseline": None,
+            "scaling": "strong" if shared else "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(args), "N": N, "precision": args.precision,
-                       "pair_arith": args.precision, "lanczos_arith": "f64", "parallelism": f"rows x{world}" if rows else f"replicas x{world}",
+                       "pair_arith": args.precision, "lanczos_arith": "f64", "parallelism": f"{args.split} x{world}" if shared else f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps",
                        "periodic": [cell_side(N)] * 2 if args.periodic else None,
                        "pair_evaluations_per_product": images * N * N},
-            "steps_per_s": args.steps * world / total_s,
+            "steps_per_s": args.steps * (1 if shared else world) / total_s,
             "lanczos_m": ms_list,
             "step_ms": [round(x, 3) for x in step_ms],
             "matvec": {"tt_ms": t_tt * 1e3, "fused_ms": t_fused * 1e3,
@@ -998,7 +1007,7 @@ def run_fingering(args, rank, world, local_rank):
     if rank != 0:
         return
     units = fingering_units()
-    N, hg, U0, b = 32768 if args.N == 65536 else args.N, args.hg, 4.0, 0.1
+    N, hg, U0, b = args.N, args.hg, 4.0, 0.1
     weight = 1.0 / (hg - 1.0)
     torque = (0.0, units["torque"], 0.0)
     pos0 = fingering_initial(N, hg, U0, b, args.seed)
@@ -1065,6 +1074,8 @@ def run_fingering(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    if args.N is None:
+        args.N = {"accuracy": 4096, "fingering": 32768}.get(args.workload, 65536)
     if args.delta is None:
         args.delta = 1e-6 if args.precision == "fp64" else 5e-3
     rank = int(os.environ.get("RANK", "0"))

@@ -131,6 +131,24 @@ int rpb_mobility_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double 
 int rpb_mobility_apply_rows(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
                             int64_t row0, int64_t row1, double *U_rows);
 
+/* Share `part` of `nparts` of U = M_tt F + M_tr T (Sec. II.B's direct summation split among
+ * processes): the shares of parts 0 .. nparts-1 add up to the product (up to the rounding of that
+ * sum), so a group of processes, one per GPU, each computing its share and summing them with an
+ * all-reduce, obtains the product.  Where the context uses the symmetric pass (float32 pairs, wall
+ * on, N >= 256, F given), share p evaluates the p-th of nparts equal contiguous runs of the unordered
+ * (target tile, source tile) units of the upper triangle -- each pair once, both of its directions
+ * (reciprocity, M_ji = M_ij^T), so nparts processes share the work of one symmetric pass -- and
+ * share 0 adds the self terms; pseudo-periodic images included.  Otherwise share p is the rows of the
+ * p-th of nparts tile-aligned row ranges (one-way kernels) and zeros elsewhere, or, for
+ * pseudo-periodic one-way products and float32 contexts without the wall, the whole product for
+ * share 0 and zeros for the others.  nparts = 1 is rpb_mobility_apply without the product hook.
+ * pos, F, T as for rpb_mobility_apply; U: 3N doubles (every entry written), aliasing no input.
+ * 0 <= part < nparts <= 4096, else RPB_EINVAL.  Never goes through the product hook (it is meant to
+ * be called from one).  The symmetric share's schedule is built on the host and copied to the device
+ * the first time a given (N, part, nparts) is used (the stream is synchronised then). */
+int rpb_mobility_apply_part(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
+                            int part, int nparts, double *U);
+
 /* A product computed by the caller: must write all 3N entries of U = M_tt F + M_tr T (F or T may be
  * NULL) on the context's stream and return RPB_OK, or an error code that the library passes on. */
 typedef int (*rpb_product_hook)(void *user, int64_t N, const double *pos, const double *F, const double *T,
@@ -138,8 +156,9 @@ typedef int (*rpb_product_hook)(void *user, int64_t N, const double *pos, const 
 
 /* Delegate every product of this context to hook (NULL restores the library's own): rpb_mobility_apply,
  * the products inside rpb_lanczos_sqrt_apply, rpb_rfd_drift, rpb_ab_step and rpb_step.  It lets a
- * suspension be shared among processes by target rows (each computes its rows with
- * rpb_mobility_apply_rows and the rows are gathered, Sec. II.B), while everything else of the step --
+ * suspension be shared among processes (each computes its share with rpb_mobility_apply_part and the
+ * shares are summed, or its rows with rpb_mobility_apply_rows and the rows are gathered, Sec. II.B),
+ * while everything else of the step --
  * forces, noise, the Lanczos recurrence and its float64 Gram-Schmidt and tridiagonal square root, the
  * drift and the update -- runs unchanged in every process on the gathered vectors.  Inside the hook,
  * products on this context are the library's own (no recursion).  With a hook, the two-right-hand-side

@@ -298,7 +298,7 @@ int rpb_create(rpb_ctx **out, const rpb_params *p, int64_t max_N, int max_iter, 
             w.sym_index_ints = sym_index_ints(max_N, c->num_sms);
             w.sym_tgt_bytes = mult * sym_tgt_part_bytes(max_N, c->num_sms);
             w.sym_src_bytes = mult * src_bytes;
-            if (cudaMalloc(&w.sym_index, w.sym_index_ints * sizeof(int)) != cudaSuccess ||
+            if (cudaMalloc(&w.sym_index, 2 * w.sym_index_ints * sizeof(int)) != cudaSuccess ||
                 cudaMalloc(&w.sym_tgt, w.sym_tgt_bytes) != cudaSuccess ||
                 cudaMalloc(&w.sym_src, w.sym_src_bytes) != cudaSuccess ||
                 (c->sym_rhs2 && cudaMalloc(&w.src2, (size_t)max_N * sizeof(float4)) != cudaSuccess)) {
@@ -435,6 +435,26 @@ int rpb_mobility_apply_rows(rpb_ctx *ctx, int64_t N, const double *pos, const do
     if (!F && !T)
         return cuda_fail(cudaMemsetAsync(U_rows, 0, 3 * (row1 - row0) * sizeof(double), ctx->stream), "memset U");
     return mobility_rows_impl(ctx, N, pos, F, T, row0, row1, U_rows);
+}
+
+int rpb_mobility_apply_part(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T, int part,
+                            int nparts, double *U)
+{
+    g_err[0] = 0;
+    int rc;
+    if ((rc = check_ctx_N(ctx, N)) || (rc = check_vec(pos, "pos", false)) || (rc = check_vec(F, "F", true)) ||
+        (rc = check_vec(T, "T", true)) || (rc = check_vec(U, "U", false)))
+        return rc;
+    if (nparts < 1 || nparts > 4096 || part < 0 || part >= nparts) {
+        set_error("share %d of %d: need 0 <= part < nparts <= 4096", part, nparts);
+        return RPB_EINVAL;
+    }
+    if (U == pos || U == F || U == T) {
+        set_error("U aliases an input");
+        return RPB_EINVAL;
+    }
+    if (!F && !T) return cuda_fail(cudaMemsetAsync(U, 0, 3 * N * sizeof(double), ctx->stream), "memset U");
+    return mobility_part_impl(ctx, N, pos, F, T, part, nparts, U);
 }
 
 int rpb_set_product_hook(rpb_ctx *ctx, rpb_product_hook hook, void *user)

@@ -640,7 +640,9 @@ __global__ void __launch_bounds__(kPairThreads, MINB) pair_f32x2_sym_kernel(cons
 }
 
 // Row partials of the targets plus column partials of the sources, fixed order; float64 self term
-// (with the torque's wall self coupling when T is given); s_i / (8 pi eta).  NC = 6: the partials also
+// (with the torque's wall self coupling when T is given; left out when self_term is 0, for all but
+// one share of a shared product); s_i / (8 pi eta).  col_rows: the rows [r0, r1) of each column that
+// the schedule wrote (null: all rows above the diagonal).  NC = 6: the partials also
 // carry a second translation-translation right-hand side P, written to U2 with its own self term.
 // BATCH: tiles of many suspensions (tile_inst: the suspension of each tile; sinst as in the pair
 // kernel); the column of tile b holds the rows tile0 .. b - 1 of its suspension, summed in an order
@@ -654,7 +656,8 @@ __global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_red
                                        double *__restrict__ U2 = nullptr,
                                        const SymInst *__restrict__ sinst = nullptr,
                                        const int *__restrict__ tile_inst = nullptr,
-                                       const int *__restrict__ active = nullptr)
+                                       const int *__restrict__ active = nullptr,
+                                       const int *__restrict__ col_rows = nullptr, int self_term = 1)
 {
     // one CTA of 768 threads (384 batched) per 128-sphere tile, the longest columns first; thread (half, q, l):
     // component q of sphere l, rows of its column congruent to `half` modulo HALVES
@@ -681,13 +684,16 @@ __global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_red
     // column of float32 partials: four independent compensated float32 sums per thread (GB300's
     // float64 rate would make a float64 add per partial the bottleneck; one chain per thread would
     // leave the column latency-bound), converted once and added in a fixed order
+    // rows [r0, r1) of the column (a share of the triangle writes only some of them)
+    const int r0 = BATCH ? tb : (col_rows ? col_rows[2 * b] : 0);
+    const int r1 = BATCH ? b : (col_rows ? col_rows[2 * b + 1] : b);
     const float *col = src_part + (size_t)col_start[b] * NC * kTile + q * kTile + l;
     float cs[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int bb = tb + half; bb < b; bb += 4 * HALVES) {
+    for (int bb = r0 + half; bb < r1; bb += 4 * HALVES) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int row = bb + HALVES * u;
-            if (row < b) {
+            if (row < r1) {
                 const float yv = col[(size_t)row * NC * kTile] - cc[u];
                 const float tv = cs[u] + yv;
                 cc[u] = (tv - cs[u]) - yv;
@@ -715,7 +721,9 @@ __global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_red
     const double k = si * scale;
     if (q == 0) {
         double ux = s[0][l], uy = s[1][l], uz = s[2][l];
-        if (T)
+        if (!self_term)
+            ;
+        else if (T)
             self_velocity<true>(zc, si * F[i], si * F[N + i], si * F[2 * N + i], si * T[i], si * T[N + i], c, ux, uy,
                                 uz);
         else
@@ -725,7 +733,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_red
         U[2 * N + i] = k * uz;
     } else if (NC == 6) {
         double ux = s[3 % NC][l], uy = s[4 % NC][l], uz = s[5 % NC][l];
-        self_velocity<false>(zc, si * P[i], si * P[N + i], si * P[2 * N + i], 0.0, 0.0, c, ux, uy, uz);
+        if (self_term) self_velocity<false>(zc, si * P[i], si * P[N + i], si * P[2 * N + i], 0.0, 0.0, c, ux, uy, uz);
         U2[i] = k * ux;
         U2[N + i] = k * uy;
         U2[2 * N + i] = k * uz;
@@ -758,96 +766,112 @@ size_t sym_index_ints(int64_t max_N, int num_sms)
 {
     const int64_t nb = (max_N + kTile - 1) / kTile;
     const int64_t maxcta = (int64_t)kSymMaxCtaPerSm * num_sms;
-    return (size_t)(4 * maxcta + 4 * (maxcta + nb + 1) + 2 * (nb + 1));
+    return (size_t)(4 * maxcta + 4 * (maxcta + nb + 1) + 4 * (nb + 1));
 }
 
-// Symmetric translation-translation product (float32 pairs); requires ctx->ws.sym_* scratch.
-// Schedule of the symmetric pass for N (built and copied to the device when N changes).
-static int sym_prepare(rpb_ctx *ctx, int N)
+// Schedule of the symmetric pass for N, share `part` of `nparts` (built and copied to the device when
+// they change): the whole triangle in ws.sym, a share in ws.sym_part.
+static int sym_prepare(rpb_ctx *ctx, int N, const SymSched **out, int part = 0, int nparts = 1)
 {
     Workspace &w = ctx->ws;
-    if (w.sym_N == N) return RPB_OK;
+    SymSched &sc = nparts == 1 ? w.sym : w.sym_part;
+    *out = &sc;
+    if (sc.N == N && sc.part == part && sc.nparts == nparts) return RPB_OK;
+    sc.N = -1;
     cudaStream_t st = ctx->stream;
-    std::vector<int> cta4, seg4, row_seg, col_start;
-    sym_schedule(N, ctx->num_sms, kTile, cta4, seg4, row_seg, col_start);
-    const size_t need = cta4.size() + seg4.size() + row_seg.size() + col_start.size();
+    std::vector<int> cta4, seg4, row_seg, col_start, col_rows;
+    int64_t u0, u1;
+    sym_part_units(N, kTile, part, nparts, &u0, &u1);
+    sym_schedule_range(N, ctx->num_sms, kTile, u0, u1, cta4, seg4, row_seg, col_start, col_rows);
+    const size_t need = cta4.size() + seg4.size() + row_seg.size() + col_start.size() + col_rows.size();
     if (need > w.sym_index_ints || seg4.size() / 4 * 3 * kTile * sizeof(double) > w.sym_tgt_bytes) {
         set_error("internal: symmetric schedule larger than its scratch (N=%d)", N);
         return RPB_EINVAL;
     }
     std::vector<int> host(need);
     size_t o = 0;
-    for (const std::vector<int> *v : {&cta4, &seg4, &row_seg, &col_start}) {
+    for (const std::vector<int> *v : {&cta4, &seg4, &row_seg, &col_start, &col_rows}) {
         std::copy(v->begin(), v->end(), host.begin() + o);
         o += v->size();
     }
+    sc.index = w.sym_index + (nparts == 1 ? 0 : w.sym_index_ints);
     int rc;
-    if ((rc = cuda_fail(cudaMemcpyAsync(w.sym_index, host.data(), need * sizeof(int), cudaMemcpyHostToDevice, st),
+    if ((rc = cuda_fail(cudaMemcpyAsync(sc.index, host.data(), need * sizeof(int), cudaMemcpyHostToDevice, st),
                         "symmetric schedule copy")))
         return rc;
     if ((rc = cuda_fail(cudaStreamSynchronize(st), "symmetric schedule copy"))) return rc;
-    w.sym_N = N;
-    w.sym_ncta = (int)(cta4.size() / 4);
-    w.sym_nseg = (int)(seg4.size() / 4);
-    w.sym_seg_off = (int)cta4.size();
-    w.sym_row_off = (int)(cta4.size() + seg4.size());
-    w.sym_col_off = (int)(cta4.size() + seg4.size() + row_seg.size());
+    sc.N = N;
+    sc.part = part;
+    sc.nparts = nparts;
+    sc.ncta = (int)(cta4.size() / 4);
+    sc.nseg = (int)(seg4.size() / 4);
+    sc.seg_off = (int)cta4.size();
+    sc.row_off = sc.seg_off + (int)seg4.size();
+    sc.col_off = sc.row_off + (int)row_seg.size();
+    sc.rows_off = sc.col_off + (int)col_start.size();
     return RPB_OK;
 }
 
 int pair_prepare(rpb_ctx *ctx, int64_t N)
 {
-    if (ctx->sym_enabled && N >= 2 * kTile && N <= ctx->max_N) return sym_prepare(ctx, (int)N);
+    const SymSched *sc;
+    if (ctx->sym_enabled && N >= 2 * kTile && N <= ctx->max_N) return sym_prepare(ctx, (int)N, &sc);
     return RPB_OK;
 }
 
 // Symmetric product (float32 pairs), translation-translation or, with T, the fused product;
-// requires ctx->ws.sym_* scratch.
-static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F, const double *T, double *U)
+// requires ctx->ws.sym_* scratch.  With nparts > 1: share `part` of the triangle's pairs, the self
+// terms with share 0 only (the shares add up to the product).
+static int mobility_sym(rpb_ctx *ctx, int N, const double *pos, const double *F, const double *T, double *U,
+                        int part = 0, int nparts = 1)
 {
     cudaStream_t st = ctx->stream;
     Workspace &w = ctx->ws;
+    const SymSched *sc;
     int rc;
-    if ((rc = sym_prepare(ctx, N))) return rc;
+    if ((rc = sym_prepare(ctx, N, &sc, part, nparts))) return rc;
     const double a = ctx->p.a;
     SrcF32 *src = (SrcF32 *)w.src;
     const int pb = 256;
     pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, 1, src);
-    const SymCta *ctas = (const SymCta *)w.sym_index;
-    const SymSeg *segs = (const SymSeg *)(w.sym_index + w.sym_seg_off);
+    const SymCta *ctas = (const SymCta *)sc->index;
+    const SymSeg *segs = (const SymSeg *)(sc->index + sc->seg_off);
     const X2Consts c = make_x2_consts(a);
-    const int *cs = w.sym_index + w.sym_col_off;
-    if (T) {
-        pair_f32x2_sym_kernel<kFusedMinBlocks, true><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs,
-                                                                                      w.sym_tgt, w.sym_src);
-    } else {
-        pair_f32x2_sym_kernel<kTtMinBlocks, false><<<w.sym_ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs,
-                                                                                        w.sym_tgt, w.sym_src);
+    const int *cs = sc->index + sc->col_off;
+    if (sc->ncta > 0) {
+        if (T)
+            pair_f32x2_sym_kernel<kFusedMinBlocks, true><<<sc->ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs,
+                                                                                            w.sym_tgt, w.sym_src);
+        else
+            pair_f32x2_sym_kernel<kTtMinBlocks, false><<<sc->ncta, kPairThreads, 0, st>>>(src, N, ctas, segs, c, cs,
+                                                                                          w.sym_tgt, w.sym_src);
     }
-    pair_sym_reduce_kernel<3><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
-                                                             cs, N, pos, F, T, make_consts<double>(a), a,
-                                                             1.0 / (8.0 * kPi * ctx->p.eta), U);
-    count_launches(3);
+    pair_sym_reduce_kernel<3><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(
+        w.sym_tgt, w.sym_src, sc->index + sc->row_off, cs, N, pos, F, T, make_consts<double>(a), a,
+        1.0 / (8.0 * kPi * ctx->p.eta), U, nullptr, nullptr, nullptr, nullptr, nullptr, sc->index + sc->rows_off,
+        part == 0);
+    count_launches(sc->ncta > 0 ? 3 : 2);
     return cuda_fail(cudaGetLastError(), "symmetric pair kernels");
 }
 
 // The symmetric product in pseudo-periodic mode: positions already folded into the unit cell
-// (pos_w; the self terms use the heights of pos, which the fold leaves unchanged).
+// (pos_w; the self terms use the heights of pos, which the fold leaves unchanged); shares as above.
 static int mobility_sym_periodic(rpb_ctx *ctx, int N, const double *pos_w, const double *pos, const double *F,
-                                 const double *T, double *U)
+                                 const double *T, double *U, int part = 0, int nparts = 1)
 {
     cudaStream_t st = ctx->stream;
     Workspace &w = ctx->ws;
+    const SymSched *sc;
     int rc;
-    if ((rc = sym_prepare(ctx, N))) return rc;
+    if ((rc = sym_prepare(ctx, N, &sc, part, nparts))) return rc;
     const double a = ctx->p.a;
     SrcF32 *src = (SrcF32 *)w.src;
     const int pb = 256;
     pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos_w, F, T, N, a, 1, src);
-    const SymCta *ctas = (const SymCta *)w.sym_index;
-    const SymSeg *segs = (const SymSeg *)(w.sym_index + w.sym_seg_off);
+    const SymCta *ctas = (const SymCta *)sc->index;
+    const SymSeg *segs = (const SymSeg *)(sc->index + sc->seg_off);
     const X2Consts c = make_x2_consts(a);
-    const int *cs = w.sym_index + w.sym_col_off;
+    const int *cs = sc->index + sc->col_off;
     PerLen pl;
     pl.xh = (float)ctx->Lx;
     pl.xl = (float)(ctx->Lx - (double)pl.xh);
@@ -855,16 +879,19 @@ static int mobility_sym_periodic(rpb_ctx *ctx, int N, const double *pos_w, const
     pl.yl = (float)(ctx->Ly - (double)pl.yh);
     pl.ix = 1.f / pl.xh;
     pl.iy = 1.f / pl.yh;
-    if (T)
-        pair_f32x2_sym_kernel<kPerMinBlocks, true, false, true><<<w.sym_ncta, kPairThreads, 0, st>>>(
-            src, N, ctas, segs, c, cs, w.sym_tgt, w.sym_src, nullptr, pl);
-    else
-        pair_f32x2_sym_kernel<kPerMinBlocks, false, false, true><<<w.sym_ncta, kPairThreads, 0, st>>>(
-            src, N, ctas, segs, c, cs, w.sym_tgt, w.sym_src, nullptr, pl);
-    pair_sym_reduce_kernel<3><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off,
-                                                             cs, N, pos, F, T, make_consts<double>(a), a,
-                                                             1.0 / (8.0 * kPi * ctx->p.eta), U);
-    count_launches(3);
+    if (sc->ncta > 0) {
+        if (T)
+            pair_f32x2_sym_kernel<kPerMinBlocks, true, false, true><<<sc->ncta, kPairThreads, 0, st>>>(
+                src, N, ctas, segs, c, cs, w.sym_tgt, w.sym_src, nullptr, pl);
+        else
+            pair_f32x2_sym_kernel<kPerMinBlocks, false, false, true><<<sc->ncta, kPairThreads, 0, st>>>(
+                src, N, ctas, segs, c, cs, w.sym_tgt, w.sym_src, nullptr, pl);
+    }
+    pair_sym_reduce_kernel<3><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(
+        w.sym_tgt, w.sym_src, sc->index + sc->row_off, cs, N, pos, F, T, make_consts<double>(a), a,
+        1.0 / (8.0 * kPi * ctx->p.eta), U, nullptr, nullptr, nullptr, nullptr, nullptr, sc->index + sc->rows_off,
+        part == 0);
+    count_launches(sc->ncta > 0 ? 3 : 2);
     return cuda_fail(cudaGetLastError(), "periodic symmetric pair kernels");
 }
 
@@ -1000,9 +1027,10 @@ int mobility_apply2_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const dou
     const int N = (int)N64;
     cudaStream_t st = ctx->stream;
     Workspace &w = ctx->ws;
+    const SymSched *sc;
     int rc;
-    if ((rc = sym_prepare(ctx, N))) return rc;
-    if ((size_t)w.sym_nseg * 6 * kTile * sizeof(double) > w.sym_tgt_bytes ||
+    if ((rc = sym_prepare(ctx, N, &sc))) return rc;
+    if ((size_t)sc->nseg * 6 * kTile * sizeof(double) > w.sym_tgt_bytes ||
         sym_src_part_bytes(N) * 2 > w.sym_src_bytes) {
         set_error("internal: two-right-hand-side scratch too small (N=%d)", N);
         return RPB_EINVAL;
@@ -1013,14 +1041,14 @@ int mobility_apply2_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const dou
     const int pb = 256;
     pack_f32_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, F, T, N, a, 1, src);
     pack_rhs2_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, P, N, a, src2);
-    const SymCta *ctas = (const SymCta *)w.sym_index;
-    const SymSeg *segs = (const SymSeg *)(w.sym_index + w.sym_seg_off);
-    const int *cs = w.sym_index + w.sym_col_off;
-    pair_f32x2_sym_kernel<kRhs2MinBlocks, true, true><<<w.sym_ncta, kPairThreads, 0, st>>>(
+    const SymCta *ctas = (const SymCta *)sc->index;
+    const SymSeg *segs = (const SymSeg *)(sc->index + sc->seg_off);
+    const int *cs = sc->index + sc->col_off;
+    pair_f32x2_sym_kernel<kRhs2MinBlocks, true, true><<<sc->ncta, kPairThreads, 0, st>>>(
         src, N, ctas, segs, make_x2_consts(a), cs, w.sym_tgt, w.sym_src, src2);
     pair_sym_reduce_kernel<6><<<(N + kTile - 1) / kTile, 6 * kTile, 0, st>>>(
-        w.sym_tgt, w.sym_src, w.sym_index + w.sym_row_off, cs, N, pos, F, T, make_consts<double>(a), a,
-        1.0 / (8.0 * kPi * ctx->p.eta), U, P, U2);
+        w.sym_tgt, w.sym_src, sc->index + sc->row_off, cs, N, pos, F, T, make_consts<double>(a), a,
+        1.0 / (8.0 * kPi * ctx->p.eta), U, P, U2, nullptr, nullptr, nullptr, sc->index + sc->rows_off);
     count_launches(4);
     return cuda_fail(cudaGetLastError(), "two-right-hand-side symmetric kernels");
 }
@@ -1217,13 +1245,15 @@ __global__ void __launch_bounds__(kPairThreads) pair_periodic_f32_kernel(const S
 }
 
 // Sum the chunk partials in order, add the float64 self term, apply s_i / (8 pi eta).  Targets t0 ..
-// t0 + nt - 1 (nt < 0: all N); U and the partials are indexed by i - t0 with component stride nt.
+// t0 + nt - 1 (nt < 0: all N); U and the partials are indexed by i - t0, the partials with component
+// stride nt, U with component stride ldu (ldu < 0: nt).
 __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, int N, const double *__restrict__ pos,
                                    const double *__restrict__ F, const double *__restrict__ T, PairConsts<double> c,
                                    double a, double scale, double *__restrict__ U, int wall = 1, int t0 = 0,
-                                   int nt = -1)
+                                   int nt = -1, int ldu = -1)
 {
     if (nt < 0) nt = N;
+    if (ldu < 0) ldu = nt;
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t0 + li;
     if (li >= nt || i >= N) return;
@@ -1245,8 +1275,8 @@ __global__ void pair_reduce_kernel(const double *__restrict__ part, int splits, 
         self_velocity<true, false>(zc, Fx, Fy, Fz, Tx, Ty, c, ux, uy, uz);
     const double k = si * scale;
     U[li] = k * ux;
-    U[nt + li] = k * uy;
-    U[2 * nt + li] = k * uz;
+    U[ldu + li] = k * uy;
+    U[2 * ldu + li] = k * uz;
 }
 
 // The same sum with one warp per target, for products split into many source chunks (small float64
@@ -1258,7 +1288,7 @@ __global__ void __launch_bounds__(128) pair_reduce_warp_kernel(const double *__r
                                                                const double *__restrict__ F,
                                                                const double *__restrict__ T, PairConsts<double> c,
                                                                double a, double scale, double *__restrict__ U,
-                                                               int wall, int t0, int nt)
+                                                               int wall, int t0, int nt, int ldu)
 {
     const int lane = threadIdx.x & 31;
     const int li = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -1288,26 +1318,27 @@ __global__ void __launch_bounds__(128) pair_reduce_warp_kernel(const double *__r
         self_velocity<true, false>(zc, Fx, Fy, Fz, Tx, Ty, c, ux, uy, uz);
     const double k = si * scale;
     U[li] = k * ux;
-    U[nt + li] = k * uy;
-    U[2 * nt + li] = k * uz;
+    U[ldu + li] = k * uy;
+    U[2 * ldu + li] = k * uz;
 }
 
-// Chunk partials -> U (targets t0 .. t0 + nt - 1, nt < 0: all N): a thread per target for few chunks
-// (coalesced loads), a warp per target for many.
+// Chunk partials -> U (targets t0 .. t0 + nt - 1, nt < 0: all N; U's component stride ldu, ldu < 0:
+// nt): a thread per target for few chunks (coalesced loads), a warp per target for many.
 static void launch_pair_reduce(cudaStream_t st, const double *part, int splits, int N, const double *pos,
                                const double *F, const double *T, double a, double scale, double *U, int wall,
-                               int t0 = 0, int nt = -1)
+                               int t0 = 0, int nt = -1, int ldu = -1)
 {
     if (nt < 0) nt = N;
+    if (ldu < 0) ldu = nt;
     const PairConsts<double> c = make_consts<double>(a);
     if (splits >= 16) {
         pair_reduce_warp_kernel<<<(unsigned)((nt + 3) / 4), 128, 0, st>>>(part, splits, N, pos, F, T, c, a, scale, U,
-                                                                          wall, t0, nt);
+                                                                          wall, t0, nt, ldu);
     } else {
         // 64-target CTAs: the float64 self terms of a small product then spread over several SMs
         const int rb = 64;
         pair_reduce_kernel<<<(unsigned)((nt + rb - 1) / rb), rb, 0, st>>>(part, splits, N, pos, F, T, c, a, scale, U,
-                                                                          wall, t0, nt);
+                                                                          wall, t0, nt, ldu);
     }
 }
 
@@ -1340,9 +1371,9 @@ size_t pair_partial_bytes(int64_t max_N, int num_sms)
 }
 
 // Rows t0 .. t1 - 1 of U = M_tt F + M_tr T (all N sources), written to U_rows with component stride
-// t1 - t0: the one-way kernels restricted to a range of targets (t0 a multiple of kTile).
+// ldu (ldu < 0: t1 - t0): the one-way kernels restricted to a range of targets (t0 a multiple of kTile).
 int mobility_rows_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, int64_t t0,
-                       int64_t t1, double *U_rows)
+                       int64_t t1, double *U_rows, int64_t ldu)
 {
     const int N = (int)N64, nt = (int)(t1 - t0);
     cudaStream_t st = ctx->stream;
@@ -1383,20 +1414,68 @@ int mobility_rows_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const doubl
             pair_f32x2_kernel<false><<<grid, kPairThreads, 0, st>>>(src, N, (int)chunk, c, part, (int)t0, nt);
     }
     launch_pair_reduce(st, part, splits, N, pos, F, T, a, 1.0 / (8.0 * kPi * ctx->p.eta), U_rows, ctx->p.wall,
-                       (int)t0, nt);
+                       (int)t0, nt, (int)ldu);
     count_launches(3);
     return cuda_fail(cudaGetLastError(), "row pair kernels");
 }
 
+static int mobility_direct(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T,
+                           double *U);
+
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, double *U)
 {
-    if (ctx->hook && !ctx->in_hook) {  // the product is delegated (e.g. shared out by rows among processes)
+    if (ctx->hook && !ctx->in_hook) {  // the product is delegated (e.g. shared out among processes)
         ctx->in_hook = 1;
         const int rc = ctx->hook(ctx->hook_user, N64, pos, F, T, U);
         ctx->in_hook = 0;
         if (rc != RPB_OK && rpb_last_error()[0] == 0) set_error("product hook returned %d", rc);
         return rc;
     }
+    return mobility_direct(ctx, N64, pos, F, T, U);
+}
+
+// Rows [r0, r1) of share `part` of `nparts`: whole 128-row tiles, as equal as the tiles allow.
+static void part_rows(int64_t N, int part, int nparts, int64_t *r0, int64_t *r1)
+{
+    const int64_t tiles = (N + kTile - 1) / kTile;
+    const int64_t base = tiles / nparts, extra = tiles % nparts;
+    const int64_t t0 = part * base + std::min<int64_t>(part, extra);
+    const int64_t t1 = t0 + base + (part < extra ? 1 : 0);
+    *r0 = std::min(N, t0 * kTile);
+    *r1 = std::min(N, t1 * kTile);
+}
+
+int mobility_part_impl(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T, int part,
+                       int nparts, double *U)
+{
+    if (nparts == 1) return mobility_direct(ctx, N64, pos, F, T, U);
+    const int N = (int)N64;
+    cudaStream_t st = ctx->stream;
+    const bool sym = ctx->sym_enabled && ctx->p.wall && F && N >= 2 * kTile && (!T || ctx->sym_fused);
+    if (sym && !(ctx->Lx > 0.0)) return mobility_sym(ctx, N, pos, F, T, U, part, nparts);
+    if (sym && ctx->p.precision == RPB_FP32) {
+        const int pb = 256;
+        wrap_kernel<<<(N + pb - 1) / pb, pb, 0, st>>>(pos, N, ctx->Lx, ctx->Ly, ctx->ws.pos_w);
+        count_launches(1);
+        return mobility_sym_periodic(ctx, N, ctx->ws.pos_w, pos, F, T, U, part, nparts);
+    }
+    int rc;
+    if ((rc = cuda_fail(cudaMemsetAsync(U, 0, (size_t)3 * N * sizeof(double), st), "part product zero fill")))
+        return rc;
+    // the pseudo-periodic one-way kernels and the float32 ones without the wall take all targets:
+    // share 0 holds the product
+    if (ctx->Lx > 0.0 || (ctx->p.precision == RPB_FP32 && !ctx->p.wall))
+        return part == 0 && (F || T) ? mobility_direct(ctx, N64, pos, F, T, U) : RPB_OK;
+    if (!F && !T) return RPB_OK;
+    int64_t r0, r1;
+    part_rows(N64, part, nparts, &r0, &r1);
+    if (r1 <= r0) return RPB_OK;
+    return mobility_rows_impl(ctx, N64, pos, F, T, r0, r1, U + r0, N64);
+}
+
+static int mobility_direct(rpb_ctx *ctx, int64_t N64, const double *pos, const double *F, const double *T,
+                           double *U)
+{
     const int N = (int)N64;
     if (ctx->sym_enabled && ctx->p.wall && !(ctx->Lx > 0.0) && F && N >= 2 * kTile && (!T || ctx->sym_fused))
         return mobility_sym(ctx, N, pos, F, T, U);
@@ -1847,7 +1926,7 @@ typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
 typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
 // Process-unique id of the calling thread's current CUDA context (driver entry points through the
-// runtime, so the library needs no link against the driver library).
+// runtime, so the library needs no link against the driver library).  Called with g_noalloc_mu held.
 static int current_ctx_id(unsigned long long *id)
 {
     static CtxGetCurrentFn get_current = nullptr;
@@ -1896,9 +1975,9 @@ static int noalloc_setup(cudaStream_t st, void **ptr, int *sms)
     // (a runtime call on the stream: it also makes the device's context current if nothing has yet)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if ((rc = cuda_fail(cudaStreamIsCapturing(st, &cs), "cudaStreamIsCapturing"))) return rc;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);  // also guards the driver entry points' first lookup
     unsigned long long id = 0;
     if ((rc = current_ctx_id(&id))) return rc;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
     NoAllocSlot &sl = g_noalloc[dev];
     if (!sl.ptr || sl.ctx_id != id) {
         if (cs != cudaStreamCaptureStatusNone) {

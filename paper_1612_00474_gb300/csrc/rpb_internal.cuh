@@ -132,6 +132,15 @@ struct BatchSymPlan {
     int tt_minb = 5;              // resident CTAs per SM of the translation-translation kernel (4 or 5)
 };
 
+// A schedule of the symmetric pass on the device (sym_schedule_range): the CTA table and segment table
+// (4 ints each), row_seg, col_start and col_rows at the given offsets of `index`, for share `part` of
+// `nparts` equal shares of the triangle of N spheres.
+struct SymSched {
+    int *index = nullptr;
+    int N = -1, part = 0, nparts = 1;
+    int ncta = 0, nseg = 0, seg_off = 0, row_off = 0, col_off = 0, rows_off = 0;
+};
+
 // Scratch owned by a context.
 struct Workspace {
     void *src = nullptr;          // packed sources, max_N records (SrcF64 size)
@@ -156,15 +165,16 @@ struct Workspace {
     double *host_status = nullptr; // pinned host copy of the Lanczos status word
     double *pc = nullptr;          // block-diagonal preconditioner D^{-1/2} (3 max_N), rpb_set_preconditioner
     double *pcx = nullptr;         // a Krylov vector scaled by it
-    // symmetric translation-translation pass (float32 contexts): schedule, row and column partials
-    int *sym_index = nullptr;      // CTA table and segment table (4 ints each), row_seg, col_start
+    // symmetric translation-translation pass (float32 contexts): schedules, row and column partials
+    int *sym_index = nullptr;      // room for two schedules of sym_index_ints each (sym.index, sym_part.index)
     size_t sym_index_ints = 0;
     double *sym_tgt = nullptr;
     size_t sym_tgt_bytes = 0;
     float *sym_src = nullptr;
     size_t sym_src_bytes = 0;
     void *src2 = nullptr;          // second right-hand side of the two-RHS symmetric pass (float4 per sphere)
-    int sym_N = -1, sym_ncta = 0, sym_nseg = 0, sym_seg_off = 0, sym_row_off = 0, sym_col_off = 0;
+    SymSched sym;       // the whole triangle
+    SymSched sym_part;  // one share of it (rpb_mobility_apply_part)
 };
 
 constexpr int kRunMaxIter = 64;  // = kMaxIter of the Lanczos state
@@ -230,9 +240,13 @@ int cuda_fail(cudaError_t e, const char *what);
 // All pointers device, SoA float64.  Enqueued on ctx->stream.
 int mobility_apply_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T,
                         double *U);
-// Rows t0 .. t1 - 1 of the product (component stride t1 - t0), one-way kernels over a target range.
+// Rows t0 .. t1 - 1 of the product (component stride ldu, ldu < 0: t1 - t0), one-way kernels over a
+// target range.
 int mobility_rows_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T, int64_t t0,
-                       int64_t t1, double *U_rows);
+                       int64_t t1, double *U_rows, int64_t ldu = -1);
+// Share `part` of `nparts` of the product (rpb_mobility_apply_part); never goes through the product hook.
+int mobility_part_impl(rpb_ctx *ctx, int64_t N, const double *pos, const double *F, const double *T, int part,
+                       int nparts, double *U);
 // Whether mobility_apply2_impl can take this product (float32 symmetric pass with two right-hand sides).
 bool mobility_apply2_ok(const rpb_ctx *ctx, int64_t N);
 // U = M_tt F + M_tr T and U2 = M_tt P in one symmetric pass (F, T, P non-null).

@@ -25,7 +25,7 @@ EXPORTS = ("rpb_create", "rpb_destroy", "rpb_set_stream", "rpb_mobility_apply", 
            "rpb_batch_set_stream", "rpb_batch_mobility_apply", "rpb_batch_ab_step", "rpb_step", "rpb_batch_run",
            "rpb_set_periodic", "rpb_set_preconditioner", "rpb_fma_peak", "rpb_run", "rpb_mobility_apply2",
            "rpb_mobility_apply_rows", "rpb_set_product_hook", "rpb_batch_set_tiles", "rpb_batch_get_tiles",
-           "rpb_batch_tune")
+           "rpb_batch_tune", "rpb_mobility_apply_part")
 SCHEMES = {"AB": 0, "EM": 1}
 RFDS = {"centred": 0, "one-sided": 1}
 PRECONDITIONERS = {"none": 0, "block-diagonal": 1}
@@ -117,6 +117,7 @@ def load(build_if_missing=True):
     L.rpb_fma_peak.argtypes = [i32, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
     L.rpb_mobility_apply2.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     L.rpb_mobility_apply_rows.argtypes = [vp, i64, vp, vp, vp, i64, i64, vp]
+    L.rpb_mobility_apply_part.argtypes = [vp, i64, vp, vp, vp, i32, i32, vp]
     L.rpb_set_product_hook.argtypes = [vp, PRODUCT_HOOK, vp]
     L.rpb_batch_set_tiles.argtypes = [vp, ctypes.POINTER(BatchTiles)]
     L.rpb_batch_get_tiles.argtypes = [vp, ctypes.POINTER(BatchTiles)]
@@ -268,6 +269,16 @@ class Context:
         self._bind_stream()
         _check(load().rpb_mobility_apply_rows(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(F, n, "F"), _ptr(T, n, "T"),
                                               int(row0), int(row1), _ptr(out, 3 * nr, "U_rows")))
+        return out
+
+    def mobility_apply_part(self, pos, F, T, part, nparts, out=None):
+        """Share `part` of `nparts` of M_tt F + M_tr T, a (3N,) SoA tensor (rpb_mobility_apply_part): the
+        shares of parts 0 .. nparts - 1 add up to the product."""
+        n = pos.numel()
+        out = self._empty(n, pos) if out is None else out
+        self._bind_stream()
+        _check(load().rpb_mobility_apply_part(self._h, n // 3, _ptr(pos, n, "pos"), _ptr(F, n, "F"), _ptr(T, n, "T"),
+                                              int(part), int(nparts), _ptr(out, n, "U")))
         return out
 
     def set_product_hook(self, fn):

@@ -1,21 +1,27 @@
-"""One suspension shared among processes (one per GPU) by target rows.
+"""One suspension shared among processes (one per GPU).
 
-The product U = M_tt F + M_tr T is a direct summation over all pairs (Sec. II.B): row i needs every
-source but no other row.  Process r of a group of W owns a contiguous range of target rows (whole
-128-row tiles, as equal as the tiles allow), computes those rows on its GPU with the library's
-row-range product (rpb_mobility_apply_rows) and receives the other rows from the other processes
-by an all-gather of the row blocks (torch.distributed).  Every process then holds the same full U.
+The product U = M_tt F + M_tr T is a direct summation over all pairs (Sec. II.B).  Two ways of
+sharing it out:
 
-A SplitContext installs this as the context's product hook (rpb_set_product_hook), so every product of
-a time step -- the fused velocity, each Lanczos product of Sec. II.C and the two RFD products of
+  - by pairs (mode "pairs", PairSplit): the symmetric pass evaluates each unordered pair once, both of
+    its directions (M_ji = M_ij^T); process r of a group of W evaluates the r-th of W equal contiguous
+    runs of the triangle's (target tile, source tile) units with rpb_mobility_apply_part, which gives
+    a partial product over all rows, and an all-reduce sums the W partials.  The W processes share one
+    symmetric pass: the pair work per process is 1/W of the single-GPU product's.
+  - by target rows (mode "rows", RowSplit): process r owns a contiguous range of target rows (whole
+    128-row tiles), computes them with rpb_mobility_apply_rows (one-way kernels: every ordered pair,
+    twice the symmetric pass's pair evaluations) and an all-gather assembles the rows.
+
+A SplitContext installs either as the context's product hook (rpb_set_product_hook), so every product
+of a time step -- the fused velocity, each Lanczos product of Sec. II.C and the two RFD products of
 Sec. II.A -- is shared out, while the rest of the step (forces, noise, the Lanczos recurrence with its
 float64 Gram-Schmidt and tridiagonal square root, the drift and the update) runs unchanged in every
-process on the gathered, identical vectors.  No all-reduce is needed: the replicated float64 vector
-work is a few per cent of a step and keeps every process's state bitwise equal.
+process on the identical assembled vectors (an all-reduce and an all-gather give every process the
+same values), so every process's state stays bitwise equal.
 
-The gather uses the group's backend: NCCL on device tensors, or, with host_exchange=True, any backend
-(gloo) through host copies.  Only argument marshalling and data movement happen here; the arithmetic
-runs in the library's kernels.
+The exchange uses the group's backend: NCCL on device tensors, or, with host_exchange=True, any
+backend (gloo) through host copies.  Only argument marshalling and data movement happen here; the
+arithmetic runs in the library's kernels (the all-reduce's sum is the collective's).
 """
 import torch
 import torch.distributed as dist
@@ -81,6 +87,39 @@ class RowSplit:
         return self.gather(local, out)
 
 
+class PairSplit:
+    """Shares of the triangle's pairs (rpb_mobility_apply_part) and the all-reduce that sums them."""
+
+    def __init__(self, N, group=None, host_exchange=False):
+        self.N = int(N)
+        self.group = group
+        on = dist.is_available() and dist.is_initialized()
+        self.rank = dist.get_rank(group) if on else 0
+        self.world = dist.get_world_size(group) if on else 1
+        self.host_exchange = host_exchange
+
+    @property
+    def mine(self):
+        return (self.rank, self.world)
+
+    def reduce(self, share):
+        """share: this process's partial product, a (3N,) tensor, replaced in place by the sum over the group."""
+        if self.world == 1:
+            return share
+        if self.host_exchange:
+            h = share.cpu()
+            dist.all_reduce(h, group=self.group)
+            share.copy_(h)
+        else:
+            dist.all_reduce(share, group=self.group)
+        return share
+
+    def product(self, part_fn, pos, F, T, out):
+        """out = the full product, from part_fn(pos, F, T, part, nparts, out) -> this process's share in out."""
+        part_fn(pos, F, T, self.rank, self.world, out)
+        return self.reduce(out)
+
+
 class _DevPtr:
     """A float64 device vector at a raw address, for torch.as_tensor (no copy)."""
 
@@ -94,31 +133,42 @@ def _wrap(ptr, n):
 
 
 class SplitContext:
-    """A library context whose products are shared among the processes of a group by target rows.
+    """A library context whose products are shared among the processes of a group, by pairs (mode
+    "pairs", the default) or by target rows (mode "rows").
 
     The methods are those of rpb.Context (mobility_apply, lanczos_sqrt_apply, rfd_drift, ab_step, step,
     forces, philox_normal, ...): every process calls them with the same arguments and gets the same
     results.  rpb_run (graph replay) is not available with a shared product."""
 
-    def __init__(self, max_N, group=None, host_exchange=False, **ctx_kwargs):
+    MODES = ("pairs", "rows")
+
+    def __init__(self, max_N, group=None, host_exchange=False, mode="pairs", **ctx_kwargs):
+        if mode not in self.MODES:
+            raise ValueError(f"mode must be one of {self.MODES}")
         self.ctx = rpb.Context(max_N, **ctx_kwargs)
         self.group = group
         self.host_exchange = host_exchange
+        self.mode = mode
         self._split = {}
         self.error = None
         self.ctx.set_product_hook(self._product)
 
     def split(self, N):
         if N not in self._split:
-            self._split[N] = RowSplit(N, self.group, self.host_exchange)
+            cls = PairSplit if self.mode == "pairs" else RowSplit
+            self._split[N] = cls(N, self.group, self.host_exchange)
         return self._split[N]
 
     def _product(self, N, pos_p, F_p, T_p, U_p):
         try:
             n = 3 * N
             sp = self.split(N)
-            sp.product(lambda pos, F, T, a, b: self.ctx.mobility_apply_rows(pos, F, T, a, b), _wrap(pos_p, n),
-                       _wrap(F_p, n), _wrap(T_p, n), _wrap(U_p, n))
+            pos, F, T, U = _wrap(pos_p, n), _wrap(F_p, n), _wrap(T_p, n), _wrap(U_p, n)
+            if self.mode == "pairs":
+                sp.product(lambda p_, f_, t_, r, w, o: self.ctx.mobility_apply_part(p_, f_, t_, r, w, out=o), pos, F,
+                           T, U)
+            else:
+                sp.product(lambda p_, f_, t_, a, b: self.ctx.mobility_apply_rows(p_, f_, t_, a, b), pos, F, T, U)
             return rpb.RPB_OK
         except Exception as e:  # reported to the library as a failed product
             self.error = e

@@ -1,5 +1,6 @@
 // Prints the work lists of the symmetric pair pass (sym_schedule.h) as JSON for
-// tests/test_schedule_cpu.py.  usage: schedule_dump single N num_sms | schedule_dump batch N0 N1 ...
+// tests/test_schedule_cpu.py.  usage: schedule_dump single N num_sms | schedule_dump part N num_sms part
+// nparts | schedule_dump batch N0 N1 ... | schedule_dump noalloc max_N max_sms max_partial_elems fp64
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -36,6 +37,22 @@ int main(int argc, char **argv)
                 if (!ok && bad++ < 20) std::printf("%lld %d %d %lld\n", N, sms, splits, (long long)chunk);
             }
         std::printf(bad ? "bad\n" : "ok\n");
+        return 0;
+    }
+    if (argc >= 6 && std::strcmp(argv[1], "part") == 0) {
+        // part N num_sms part nparts: the schedule of one share of the triangle
+        std::vector<int> cta4, seg4, row_seg, col_start, col_rows;
+        int64_t u0, u1;
+        const long long N = std::atoll(argv[2]);
+        rpb::sym_part_units(N, tile, std::atoi(argv[4]), std::atoi(argv[5]), &u0, &u1);
+        rpb::sym_schedule_range(N, std::atoi(argv[3]), tile, u0, u1, cta4, seg4, row_seg, col_start, col_rows);
+        std::printf("{\"u0\": %lld, \"u1\": %lld, ", (long long)u0, (long long)u1);
+        dump("cta4", cta4);
+        dump("seg4", seg4);
+        dump("row_seg", row_seg);
+        dump("col_start", col_start);
+        dump("col_rows", col_rows, true);
+        std::printf("}\n");
         return 0;
     }
     if (argc >= 4 && std::strcmp(argv[1], "single") == 0) {

@@ -1,8 +1,9 @@
-"""Products shared by target rows among processes (split.py over rpb_mobility_apply_rows and the
-product hook), on the GPU.
+"""Products shared among processes (split.py over the product hook), on the GPU: by pairs
+(rpb_mobility_apply_part, the shares summed by an all-reduce) and by target rows
+(rpb_mobility_apply_rows, the rows all-gathered).
 
-Two processes on the same GPU form a gloo group and exchange their row blocks through host memory
-(no kernel of one process waits on the other's); every product of their time steps -- the fused
+Two processes on the same GPU form a gloo group and exchange their shares or row blocks through host
+memory (no kernel of one process waits on the other's); every product of their time steps -- the fused
 velocity, the Lanczos products and the two RFD products -- is shared out, the rest of the step runs in
 both.  Their states must stay equal to each other bit for bit, and match the single-process path and
 the FP64 oracle within the parity tolerances (FP64 1e-10 on the products and U^n; the increment
@@ -47,7 +48,7 @@ def _steps(c, N, precision, nsteps=2):
     return q.cpu().numpy(), U.cpu().numpy(), ms, P.cpu().numpy()
 
 
-def _worker(rank, world, port, N, precision, out):
+def _worker(rank, world, port, N, precision, mode, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     torch.cuda.set_device(0)
@@ -55,7 +56,7 @@ def _worker(rank, world, port, N, precision, out):
     try:
         from paper_1612_00474_gb300.split import SplitContext
 
-        sc = SplitContext(N, host_exchange=True, precision=precision, max_iter=32)
+        sc = SplitContext(N, host_exchange=True, mode=mode, precision=precision, max_iter=32)
         try:
             out[rank] = _steps(sc, N, precision) + (sc.split(N).mine,)
         finally:
@@ -65,8 +66,9 @@ def _worker(rank, world, port, N, precision, out):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("mode", ["pairs", "rows"])
 @pytest.mark.parametrize("N,precision", [(300, "fp64"), (700, "fp32")])
-def test_split_two_processes_one_gpu(gpu_lib, N, precision):
+def test_split_two_processes_one_gpu(gpu_lib, N, precision, mode):
     import oracle as O
 
     world = 2
@@ -74,7 +76,7 @@ def test_split_two_processes_one_gpu(gpu_lib, N, precision):
     mgr = ctx.Manager()
     out = mgr.dict()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, N, precision, out)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, N, precision, mode, out)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
@@ -103,15 +105,16 @@ def test_split_two_processes_one_gpu(gpu_lib, N, precision):
     assert np.max(np.abs(inputs.from_soa(P0, N) - ref)) / np.max(np.abs(ref)) <= tol
 
 
-def test_split_one_process_hook(gpu_lib):
-    """Without a process group the hook computes all rows itself: products equal the oracle's."""
+@pytest.mark.parametrize("mode", ["pairs", "rows"])
+def test_split_one_process_hook(gpu_lib, mode):
+    """Without a process group the hook computes the whole product itself: products equal the oracle's."""
     import oracle as O
     from paper_1612_00474_gb300.split import SplitContext
 
     N = 257
     pos = inputs.monolayer(N, seed=2)
     F, T = inputs.vectors(N, 3), inputs.vectors(N, 4)
-    sc = SplitContext(N, precision="fp64", max_iter=16)
+    sc = SplitContext(N, mode=mode, precision="fp64", max_iter=16)
     try:
         got = inputs.from_soa(sc.mobility_apply(_dev(pos), _dev(F), _dev(T)).cpu().numpy(), N)
         with pytest.raises(AttributeError):

@@ -2,7 +2,8 @@
 checked on the CPU: every unordered unit (target tile b, source tile t >= b) of the upper triangle is
 covered exactly once, the source-partial slots of the units t > b are distinct and dense, row
 segments are contiguous and in order, and (single suspension) the CTA runs have equal length up to
-the last; (batched) no unit crosses a suspension and a suspension's lists do not depend on its
+the last; (shares of the triangle among processes) the shares cover it once and read back exactly
+the partials they wrote; (batched) no unit crosses a suspension and a suspension's lists do not depend on its
 companions."""
 import json
 import os
@@ -66,6 +67,59 @@ def test_single_schedule(dump, N, sms):
     L = -(-units_n // min(units_n, 60 * sms))  # run length; at most 60 x SMs runs
     assert len(cta) == -(-units_n // L) and work[0] == L
     assert len(set(work[:-1])) <= 1 and work[-1] <= work[0]
+
+
+@pytest.mark.parametrize("N,sms,nparts", [(1000, 4, 2), (1000, 4, 3), (300, 152, 7), (65536, 152, 8),
+                                          (70000, 152, 3), (129, 152, 5)])
+def test_part_schedules_share_the_triangle(dump, N, sms, nparts):
+    """The shares of rpb_mobility_apply_part: nparts contiguous unit ranges of (nearly) equal size that
+    together cover every unit of the triangle exactly once; each share's CTA runs have equal length up
+    to the last; row_seg indexes its own segments; col_rows[t] = [r0, r1) is exactly the set of rows
+    r < t whose unit (r, t) the share holds (the reduce kernel reads those source partials and no
+    other), so that the shares' partial products add up to the whole product."""
+    nb = -(-N // TILE)
+    units_n = nb * (nb + 1) // 2
+    seen = {}
+    sizes = []
+    for p in range(nparts):
+        d = dump("part", N, sms, p, nparts)
+        sizes.append(d["u1"] - d["u0"])
+        segs = _segments(d)
+        mine = set()
+        for q, (b, t0, t1, _) in enumerate(segs):
+            assert 0 <= b <= t0 < t1 <= nb
+            assert d["row_seg"][b] <= q < d["row_seg"][b + 1]
+            for t in range(t0, t1):
+                assert (b, t) not in seen
+                seen[(b, t)] = p
+                mine.add((b, t))
+        # unit indices of the share: exactly [u0, u1) in row-major order
+        idx = sorted(b * nb - b * (b - 1) // 2 + (t - b) for b, t in mine)
+        assert idx == list(range(d["u0"], d["u1"]))
+        cr = d["col_rows"]
+        for t in range(nb):
+            rows = sorted(b for (b, tt) in mine if tt == t and b < t)
+            r0, r1 = cr[2 * t], cr[2 * t + 1]
+            assert rows == list(range(r0, r1)), (p, t, rows, r0, r1)
+        cta = [tuple(d["cta4"][4 * c:4 * c + 2]) for c in range(len(d["cta4"]) // 4)]
+        if segs:
+            assert cta[0][0] == 0 and cta[-1][1] == len(segs)
+            work = [sum(segs[q][2] - segs[q][1] for q in range(s0, s1)) for s0, s1 in cta]
+            assert len(set(work[:-1])) <= 1 and work[-1] <= work[0] and len(cta) <= 60 * sms
+        else:
+            assert cta == []
+    assert set(seen) == {(b, t) for b in range(nb) for t in range(b, nb)}
+    assert sum(sizes) == units_n and max(sizes) - min(sizes) <= 1
+
+
+def test_whole_triangle_is_share_zero_of_one(dump):
+    """The single-process schedule is share 0 of 1, and its col_rows read every row above the diagonal."""
+    for N in (256, 1000, 65536):
+        a, b = dump("single", N, 152), dump("part", N, 152, 0, 1)
+        for k in ("cta4", "seg4", "row_seg", "col_start"):
+            assert a[k] == b[k]
+        nb = -(-N // TILE)
+        assert b["col_rows"] == [x for t in range(nb) for x in ((0, t) if t > 0 else (0, 0))]
 
 
 SIZES = [300, 64, 2100, 1, 1025, 129, 128]
