@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="monolayer at N=1: skip the small and batched configurations measured after the headline")
     ap.add_argument("--periodic", action="store_true",
                     help="monolayer: pseudo-periodic boundaries with the monolayer's square as the unit cell")
     ap.add_argument("--split", choices=["replicas", "pairs", "rows"], default="replicas",
@@ -453,7 +455,7 @@ def run_ours(args, rank, world, local_rank):
                          "peak_basis": peak_basis,
                          "flops_per_launch": flops_tt,
                          "flops_per_pair": FLOPS_SYM / 2 if sym else FLOPS_TT,
-                         "traffic": SYM_TT_TRAFFIC_BYTES.get(N) if sym and not args.periodic else None,
+                         "traffic": SYM_TT_TRAFFIC_BYTES.get(N) if sym and not args.periodic and not shared else None,
                          "traffic_unit": "bytes per launch",
                          "fp32_ops": ops_view},
             "peaks": peaks,
@@ -464,10 +466,36 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks,
             "wall_s_timed": t_wall,
         }
+        if world == 1 and not args.no_secondary:
+            line["secondary"] = secondary_configs(args, local_rank)
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def secondary_configs(args, local_rank):
+    """The small (N = 256, FP64) and batched (512 suspensions) configurations measured in the same run
+    as the headline, after it (a few seconds each; their own workloads add the oracle timings)."""
+    sm = measure_small(local_rank, 20, 3)
+    bargs = argparse.Namespace(**vars(args))
+    bargs.delta = 5e-3 if args.precision == "fp32" else 1e-6
+    b = measure_batched(bargs, 0, 1, local_rank, None, 10, 3)
+    return {
+        "small": {"workload": "N=256 monolayer (seed 0), FP64 pairs, AB step dt=0.01, delta=1e-6, tol=1e-3",
+                  "us_per_step_rpb_ab_step": b_round(sm["gpu_us"]), "us_per_step_rpb_run": b_round(sm["graph_us"]),
+                  "lanczos_m": sm["ms_m"][-1], "clocks": sm["clocks"]},
+        "batched": {"workload": f"{b['B']} suspensions, N log-uniform in [64, 2048] (sum N = {sum(b['sizes'])}), "
+                                f"{args.precision} pairs, 10 graph-replayed AB steps",
+                    "instance_steps_per_s": b["B"] * 10 / b["total_s"], "gpairs_s": b["pairs"] / b["total_s"] / 1e9,
+                    "e2e_gpairs_s": b["e2e_pairs"] / b["e2e_s"] / 1e9,
+                    "loop_instance_steps_per_s": b["B"] / b["loop_s"], "tiles": b["tuned"]["best"],
+                    "unconverged_instance_steps": b["unconv"], "gpu_launches": b["launches"], "clocks": b["clocks"]},
+    }
+
+
+def b_round(x):
+    return round(float(x), 2)
 
 
 def _base_line(args, world, metric_value, unit, ms_per_step, dtype, config):
@@ -476,15 +504,14 @@ def _base_line(args, world, metric_value, unit, ms_per_step, dtype, config):
             "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
 
 
-def run_batched(args, rank, world, local_rank):
+def measure_batched(args, rank, world, local_rank, dist, steps, warmup):
     """512 independent suspensions, N log-uniform in [64, 2048] (seeds 0..511), advanced together by
-    rpb_batch_ab_step; compared with a loop over the single-suspension rpb_ab_step."""
+    rpb_batch_run (graph-replayed steps); the tile schedule from the batch tuner; the same timed end to
+    end from pinned host memory, and a loop over the single-suspension rpb_ab_step for comparison."""
     import torch
 
     from paper_1612_00474_gb300 import inputs, rpb
 
-    torch.cuda.set_device(local_rank)
-    dist = init_dist(world)
     B = args.B
     sizes = [int(n) for n in inputs.batch_sizes(B, seed=args.seed)]
     seeds = [args.seed + rank * B + k for k in range(B)]
@@ -496,7 +523,7 @@ def run_batched(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     tuned = bt.tune(q, reps=3)  # the tile schedule of this size mix, kept by the context
     step = 0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         bt.ab_step(q, U, [step] * B, seeds, **kw)
         step += 1
     torch.cuda.synchronize()
@@ -518,16 +545,15 @@ def run_batched(args, rank, world, local_rank):
     launches0 = rpb.launch_count()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    st, unconv = bt.run(q, U, [step] * B, seeds, nsteps=args.steps, lanczos_iters=args.lanczos_iters,
+    st, unconv = bt.run(q, U, [step] * B, seeds, nsteps=steps, lanczos_iters=args.lanczos_iters,
                         dt=args.dt, delta=args.delta, tol=args.tol)
     torch.cuda.synchronize()
     total_s = time.perf_counter() - t0
     clocks = clocks_stop(clk)
     launches = rpb.launch_count() - launches0
-    step += args.steps
-    ms = [total_s * 1e3 / args.steps] * args.steps
+    step += steps
     # pair evaluations: each instance's converged iteration count (m of the last step as the estimate)
-    pairs = args.steps * sum(float(N) * N * (3 + s["m"]) for N, s in zip(sizes, st))
+    pairs = steps * sum(float(N) * N * (3 + s["m"]) for N, s in zip(sizes, st))
     # end to end: the states come from pinned host memory and return to it around the same run
     hq = [t.cpu().pin_memory() for t in q]
     hU = [t.cpu().pin_memory() for t in U]
@@ -535,14 +561,14 @@ def run_batched(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for d_, h_ in zip(q + U, hq + hU):
         d_.copy_(h_, non_blocking=True)
-    st_e2e, _ = bt.run(q, U, [step] * B, seeds, nsteps=args.steps, lanczos_iters=args.lanczos_iters,
+    st_e2e, _ = bt.run(q, U, [step] * B, seeds, nsteps=steps, lanczos_iters=args.lanczos_iters,
                        dt=args.dt, delta=args.delta, tol=args.tol)
     for d_, h_ in zip(q + U, hq + hU):
         h_.copy_(d_, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_pairs = args.steps * sum(float(N) * N * (3 + s_["m"]) for N, s_ in zip(sizes, st_e2e))
-    step += args.steps
+    e2e_pairs = steps * sum(float(N) * N * (3 + s_["m"]) for N, s_ in zip(sizes, st_e2e))
+    step += steps
     # the same instances, one rpb_ab_step call each (one step of all B)
     ctx = rpb.Context(max_N=max(sizes), precision=args.precision, max_iter=64)
     torch.cuda.synchronize()
@@ -553,7 +579,19 @@ def run_batched(args, rank, world, local_rank):
     loop_s = time.perf_counter() - t0
     ctx.close()
     bt.close()
-    (total_s, loop_s), (pairs,) = aggregate(dist, [total_s, loop_s], [pairs], device="cuda")
+    return dict(B=B, sizes=sizes, total_s=total_s, loop_s=loop_s, pairs=pairs, e2e_s=e2e_s, e2e_pairs=e2e_pairs,
+                unconv=unconv, ms_call=ms_call, m_used=m_used, tuned=tuned, launches=int(launches), clocks=clocks)
+
+
+def run_batched(args, rank, world, local_rank):
+    """The batched workload (measure_batched) as its own bench line."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = init_dist(world)
+    r = measure_batched(args, rank, world, local_rank, dist, args.steps, args.warmup)
+    B, sizes = r["B"], r["sizes"]
+    (total_s, loop_s), (pairs,) = aggregate(dist, [r["total_s"], r["loop_s"]], [r["pairs"]], device="cuda")
     if rank == 0:
         inst_steps = B * args.steps * world / total_s
         line = _base_line(args, world, pairs / total_s / 1e9, "Gpairs/s", total_s * 1e3 / args.steps,
@@ -566,17 +604,18 @@ def run_batched(args, rank, world, local_rank):
                      "loop_instance_steps_per_s": B * world / loop_s,
                      "speedup_vs_loop": inst_steps / (B * world / loop_s),
                      "graph_run": {"steps": args.steps, "lanczos_iters_per_step": args.lanczos_iters,
-                                   "unconverged_instance_steps": unconv, "host_driven_step_ms": ms_call,
-                                   "max_m": m_used},
-                     "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": "Gpairs/s",
+                                   "unconverged_instance_steps": r["unconv"], "host_driven_step_ms": r["ms_call"],
+                                   "max_m": r["m_used"]},
+                     "e2e": {"value": r["e2e_pairs"] / r["e2e_s"] / 1e9, "unit": "Gpairs/s",
                              "h2d_bytes_per_step": 48.0 * sum(sizes) / args.steps,
                              "d2h_bytes_per_step": 48.0 * sum(sizes) / args.steps,
                              "note": "all instances' positions and U^{n-1} copied from pinned host memory before "
                                      "and back after one graph-replayed run of the timed steps"},
                      "cpu_baseline": cpu_baseline_line(args, 2048),
-                     "tiles": {"tuned": tuned["best"],
-                               "candidates_ms": [[c, round(t, 4)] for c, t in tuned["candidates"]]},
-                     "step_ms": [round(x, 3) for x in ms], "gpu_launches": int(launches), "clocks": clocks})
+                     "tiles": {"tuned": r["tuned"]["best"],
+                               "candidates_ms": [[c, round(t, 4)] for c, t in r["tuned"]["candidates"]]},
+                     "step_ms": [round(total_s * 1e3 / args.steps, 3)] * args.steps, "gpu_launches": r["launches"],
+                     "clocks": r["clocks"]})
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -852,19 +891,15 @@ def oracle_timing(threads, seconds, step_4096=True):
     return res
 
 
-def run_small(args, rank, world, local_rank):
+def measure_small(local_rank, steps, warmup):
     """The 256-sphere configuration (seed 0, FP64 pairs, dt = 0.01, delta = 1e-6, tol = 1e-3):
-    microseconds per AB step on the GPU through rpb_run (the step replayed from a CUDA graph, the
-    Lanczos stop decided on the device) and through rpb_ab_step (the host reads the Lanczos status back
-    after every iteration), beside the FP64 oracle's full step on all host cores and on one core (plus,
-    on both, one 4096-sphere step and a row sample of the 65536-sphere fused product)."""
+    microseconds per AB step on the GPU through rpb_ab_step (the host reads the Lanczos status back
+    after every iteration) and through rpb_run (the step replayed from a CUDA graph, the Lanczos stop
+    decided on the device)."""
     import torch
 
     from paper_1612_00474_gb300 import inputs, rpb
 
-    torch.cuda.set_device(local_rank)
-    if rank != 0:
-        return
     N, seed = 256, 0
     kw = dict(dt=0.01, delta=1e-6, tol=1e-3)
     pos0 = inputs.monolayer(N, seed=seed)
@@ -872,7 +907,7 @@ def run_small(args, rank, world, local_rank):
     q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
     U = torch.zeros_like(q)
     step = 0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.ab_step(q, U, step, seed, max_iter=64, **kw)
         step += 1
     stream = torch.cuda.current_stream()
@@ -880,7 +915,7 @@ def run_small(args, rank, world, local_rank):
     clk = clocks_start(local_rank)
     launches0 = rpb.launch_count()
     us, ms_m = [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         st = ctx.ab_step(q, U, step, seed, max_iter=64, **kw)
@@ -892,9 +927,9 @@ def run_small(args, rank, world, local_rank):
     launches_host = rpb.launch_count() - launches0
     # the same suspension, steps replayed from a CUDA graph (one capture per call, amortised over the
     # call's steps: the timed call makes K = max(steps, 50) of them)
-    ctx.run(q, U, step, seed, max(1, args.warmup), max_iter=64, **kw)
-    step += max(1, args.warmup)
-    K = max(args.steps, 50)
+    ctx.run(q, U, step, seed, max(1, warmup), max_iter=64, **kw)
+    step += max(1, warmup)
+    K = max(steps, 50)
     torch.cuda.synchronize()
     launches0 = rpb.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -907,6 +942,21 @@ def run_small(args, rank, world, local_rank):
     ctx.close()
     clocks = clocks_stop(clk)
     gpu_us = statistics.median(us)
+    return dict(N=N, seed=seed, us=us, ms_m=ms_m, gpu_us=gpu_us, graph_us=graph_us, K=K, st_run=st_run,
+                unconv=unconv, launches_host=launches_host, launches_run=launches_run, clocks=clocks)
+
+
+def run_small(args, rank, world, local_rank):
+    """The small workload (measure_small) as its own bench line, beside the FP64 oracle's full step on
+    all host cores and on one core (plus, on both, one 4096-sphere step and a row sample of the
+    65536-sphere fused product)."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    r = measure_small(local_rank, args.steps, args.warmup)
+    N, seed, gpu_us, graph_us, K = r["N"], r["seed"], r["gpu_us"], r["graph_us"], r["K"]
     best_us = min(gpu_us, graph_us)  # the faster of the host-driven and the graph-replayed step
     line = _base_line(args, 1, best_us, "us/step", best_us / 1e3, "f64",
                       {"workload": f"small: N={N} monolayer (seed {seed}), AB step dt=0.01, delta=1e-6, tol=1e-3, "
@@ -914,11 +964,11 @@ def run_small(args, rank, world, local_rank):
     line["higher_is_better"] = False
     line.update({"value_path": "rpb_ab_step (host-driven)" if gpu_us <= graph_us else "rpb_run (graph-replayed)",
                  "us_per_step": {"rpb_run": graph_us, "rpb_ab_step_median": gpu_us,
-                                 "rpb_ab_step_mean": statistics.mean(us)},
-                 "graph_run": {"steps": K, "last_m": st_run["m"], "unconverged_steps": unconv,
-                               "launches_per_step": launches_run / K},
-                 "lanczos_m": ms_m, "gpu_launches": int(launches_run),
-                 "host_driven_launches_per_step": launches_host / max(1, args.steps), "clocks": clocks})
+                                 "rpb_ab_step_mean": statistics.mean(r["us"])},
+                 "graph_run": {"steps": K, "last_m": r["st_run"]["m"], "unconverged_steps": r["unconv"],
+                               "launches_per_step": r["launches_run"] / K},
+                 "lanczos_m": r["ms_m"], "gpu_launches": int(r["launches_run"]),
+                 "host_driven_launches_per_step": r["launches_host"] / max(1, args.steps), "clocks": r["clocks"]})
     if not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         allc = oracle_timing(cores, 5.0)

@@ -180,7 +180,10 @@ int rpb_mobility_apply2(rpb_ctx *ctx, int64_t N, const double *pos, const double
  * tol <= 0, runs exactly max_iter iterations (for comparisons at equal m).  Stops early (exact
  * result) if the Krylov space becomes invariant.  max_iter must be in [1, context max_iter].
  * W = 0 gives g = 0, m = 0.  W, g: 3N; g must not alias W or pos.  iters_out, err_out: host
- * pointers (may be NULL).  Synchronises the stream once per iteration.  Returns RPB_ENOCONV
+ * pointers (may be NULL).  Waits on the host once per iteration for the stopping test (the
+ * tridiagonal step and its status copy run on a side stream of the context, ordered after the
+ * iteration's work by events; short products of the next iteration may already be enqueued then and
+ * are discarded at the stop), and orders the stream after that side stream before returning.  Returns RPB_ENOCONV
  * if tol > 0 and max_iter was reached without convergence (g is still written). */
 int rpb_lanczos_sqrt_apply(rpb_ctx *ctx, int64_t N, const double *pos, const double *W, double *g,
                            double tol, int max_iter, int *iters_out, double *err_out);
@@ -238,11 +241,13 @@ int rpb_step(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int64_t step,
 
 /* nsteps time steps of one suspension, as nsteps calls of rpb_step with step indices step, step + 1,
  * ... (Eq. AB or Eq. EM; Sec. II.A-C for the drift and the Lanczos square root), with the same results
- * bit for bit: the step is captured once into a CUDA graph and replayed nsteps times with no host
- * synchronisation in between.  Each Lanczos iteration after the first is a conditional node that
- * runs only while the stopping test of Sec. II.C (eps_m <= tol, or an invariant Krylov space) has not
- * been met, decided on the device by the previous iteration, so a replay runs the iterations a
- * host-driven step would, up to max_iter.  The step index keying the noise and the first-step flag
+ * bit for bit: the step is captured once as the body of a loop (WHILE) node of a CUDA graph and the
+ * graph is launched once, running nsteps steps with no host synchronisation in between.  Each
+ * Lanczos iteration after the first is a conditional node that runs only while the stopping test of
+ * Sec. II.C (eps_m <= tol, or an invariant Krylov space) has not been met, decided on the device by
+ * the previous iteration, so a replay runs the iterations a host-driven step would, up to max_iter;
+ * for short products the tridiagonal step of an iteration runs beside the next iteration's product
+ * (a graph branch; the product is unused after the last iteration).  The step index keying the noise and the first-step flag
  * (step == 0 starts with an Euler-Maruyama step) advance on the device.
  *   - The work runs on a stream the context creates on first use (with a few hundred bytes of
  *     device state), ordered after the context's stream; the context's stream is ordered after the
@@ -294,8 +299,8 @@ int rpb_batch_ab_step(rpb_batch *bt, int B, const int64_t *N, double *const *pos
                       int max_iter, const rpb_force_params *fp, rpb_step_stats *stats);
 
 /* nsteps AB steps of every instance (as repeated rpb_batch_ab_step) with one gather and one scatter
- * of the state, the step captured once into a CUDA graph and replayed nsteps times with no host
- * synchronisation in between.  Inside the graph each Lanczos iteration after the first is a
+ * of the state, the step captured once as the body of a loop (WHILE) node of a CUDA graph that is
+ * launched once, running nsteps steps with no host synchronisation in between.  Inside the graph each Lanczos iteration after the first is a
  * conditional node that runs while some instance is still active (decided on the device), up to
  * lanczos_iters iterations per step, with converged instances masked out (so lanczos_iters caps the
  * iteration count the tolerance needs; *unconverged, if not NULL, receives the number of

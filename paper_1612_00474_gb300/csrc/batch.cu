@@ -585,6 +585,8 @@ struct rpb_batch {
     // multi-step runs: a private stream to capture and replay the step graph on, joined to the
     // caller's stream by an event; a device counter of unconverged instance-steps
     cudaStream_t cap = nullptr;
+    cudaStream_t loop = nullptr;  // the WHILE node's body (a step) is captured here
+    int *d_left = nullptr;        // steps left in the run
     cudaEvent_t join = nullptr;
     unsigned long long *d_unconv = nullptr;
     unsigned long long *h_unconv = nullptr;
@@ -611,7 +613,7 @@ enum { V_POS, V_UP, V_F, V_T, V_UN, V_W, V_WT, V_G, V_DRIFT, V_PA, V_PB, V_WORK 
 static void batch_free(rpb_batch *bt)
 {
     void *dev[] = {bt->d_inst, bt->d_blocks, bt->d_inst_of, bt->d_active, bt->d_nactive, bt->src, bt->V, bt->lz, bt->red,
-                   bt->norm2};
+                   bt->norm2, bt->d_left};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (double *p : bt->vec)
@@ -626,6 +628,7 @@ static void batch_free(rpb_batch *bt)
     batch_sym_free(bt->sym);
     if (bt->join) cudaEventDestroy(bt->join);
     if (bt->cap) cudaStreamDestroy(bt->cap);
+    if (bt->loop) cudaStreamDestroy(bt->loop);
 }
 
 static int grid_for(int64_t n, int sms)
@@ -783,10 +786,18 @@ static int batch_lanczos(rpb_batch *bt, const double *pos, const double *W, doub
         if ((rc = cuda_fail(cudaStreamGetCaptureInfo(main_st, &cs, nullptr, &cg, nullptr, nullptr, nullptr),
                             "capture info")))
             return rc;
-        for (int k = 1; k < max_iter; ++k)
+        CondSet cs_all = {};
+        for (int k = 1; k < max_iter; ++k) {
             if ((rc = cuda_fail(cudaGraphConditionalHandleCreate(&hnd[k], cg, 0u, cudaGraphCondAssignDefault),
                                 "conditional handle")))
                 return rc;
+            cs_all.h[k - 1] = hnd[k];
+        }
+        // the iterations' conditions start at 0 in every step (the graph runs the step in a loop)
+        if (max_iter > 1) {
+            graph_reset_conds_kernel<<<1, 64, 0, main_st>>>(cs_all, max_iter - 1);
+            count_launches(1);
+        }
     }
     batch_dots_kernel<<<dim3(B, 1), kBThreads, 0, main_st>>>(W, 0, W, bt->d_inst, nullptr, total, B, bt->red);
     batch_norm_init_kernel<<<(B + 127) / 128, 128, 0, main_st>>>(bt->red, B, bt->lz, bt->lz_stride, L.status,
@@ -924,8 +935,9 @@ static int batch_read_stats(rpb_batch *bt, double tol, rpb_step_stats *stats)
     return noconv;
 }
 
-// nsteps AB steps of the batch: one gather, one CUDA graph of a step (fixed Lanczos iteration count,
-// converged instances masked) replayed nsteps times without host synchronisation, one scatter.
+// nsteps AB steps of the batch: one gather, one launch of a CUDA graph whose WHILE node runs a step
+// (fixed Lanczos iteration count, converged instances masked) nsteps times without host
+// synchronisation, one scatter.
 static int batch_run_impl(rpb_batch *bt, int B, const int64_t *N, double *const *pos, double *const *U_prev,
                           const int64_t *steps, const uint64_t *seeds, int nsteps, double dt, double delta, double tol,
                           int lanczos_iters, const rpb_force_params *fp, rpb_step_stats *stats, int64_t *unconverged)
@@ -941,16 +953,34 @@ static int batch_run_impl(rpb_batch *bt, int B, const int64_t *N, double *const 
     for (int k = 0; k < kMaxIter; ++k) bt->iter_launches[k] = 0;
     int per_step = 0;
     if (nsteps > 0) {
+        // one graph launch for all nsteps: a WHILE node whose body is a step, counted down on the device
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
+        graph_loop_init_kernel<<<1, 1, 0, st>>>(bt->d_left, nsteps);
+        count_launches(1);
         const uint64_t before = rpb_launch_count();
         if ((rc = cuda_fail(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return rc;
-        const int brc = batch_step_body(bt, dt, delta, tol, lanczos_iters, fp, true);
+        cudaGraphConditionalHandle loop_h = 0;
+        int brc = graph_begin_loop(st, bt->loop, &loop_h);
+        if (!brc) {
+            bt->stream = bt->loop;
+            brc = batch_step_body(bt, dt, delta, tol, lanczos_iters, fp, true);
+            if (!brc) {
+                graph_loop_tail_kernel<<<1, 1, 0, bt->loop>>>(bt->d_left, loop_h);
+                count_launches(1);
+                brc = cuda_fail(cudaGetLastError(), "loop kernel");
+            }
+            bt->stream = st;
+            cudaGraph_t loop_graph = nullptr;  // owned by the WHILE node
+            const cudaError_t el = cudaStreamEndCapture(bt->loop, &loop_graph);
+            if (!brc && el != cudaSuccess) brc = cuda_fail(el, "loop body capture end");
+        }
         const cudaError_t ec = cudaStreamEndCapture(st, &graph);
         per_step = (int)(rpb_launch_count() - before);
         count_launches(-per_step);  // captured, not executed (counted below from the runs)
         if (brc) {
             if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
             return brc;
         }
         if ((rc = cuda_fail(ec, "end capture"))) return rc;
@@ -958,7 +988,7 @@ static int batch_run_impl(rpb_batch *bt, int B, const int64_t *N, double *const 
             cudaGraphDestroy(graph);
             return rc;
         }
-        for (int s = 0; s < nsteps && !rc; ++s) rc = cuda_fail(cudaGraphLaunch(exec, st), "graph launch");
+        rc = cuda_fail(cudaGraphLaunch(exec, st), "graph launch");
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
         if (rc) return rc;
@@ -1056,6 +1086,8 @@ int rpb_batch_create(rpb_batch **out, const rpb_params *p, int64_t max_total_N, 
               cudaMalloc(&bt->d_unconv, sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&bt->h_unconv, sizeof(unsigned long long)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&bt->loop, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&bt->d_left, sizeof(int)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&bt->body, cudaStreamNonBlocking) == cudaSuccess &&
               cudaMalloc(&bt->d_iter_runs, kMaxIter * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&bt->h_iter_runs, kMaxIter * sizeof(unsigned long long)) == cudaSuccess &&

@@ -326,11 +326,18 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
         if ((rc = cuda_fail(cudaStreamGetCaptureInfo(main_st, &cs, nullptr, &cg, nullptr, nullptr, nullptr),
                             "capture info")))
             return rc;
+        CondSet cs_all = {};
         for (int k = 1; k < max_iter; ++k) {
             gr->iter_launches[k] = 0;
             if ((rc = cuda_fail(cudaGraphConditionalHandleCreate(&gr->hnd[k], cg, 0u, cudaGraphCondAssignDefault),
                                 "conditional handle")))
                 return rc;
+            cs_all.h[k - 1] = gr->hnd[k];
+        }
+        // the iterations' conditions start at 0 in every step (the graph may run the step in a loop)
+        if (max_iter > 1) {
+            graph_reset_conds_kernel<<<1, 64, 0, main_st>>>(cs_all, max_iter - 1);
+            count_launches(1);
         }
     }
     // Host-driven: the tridiagonal step of iteration k runs on a side stream while the context's
@@ -397,23 +404,42 @@ int lanczos_run(rpb_ctx *ctx, int64_t N, const double *pos, double *g, double to
         cudaStream_t st = ctx->stream;
         const uint64_t before = rpb_launch_count();
         const double *vk = V + (size_t)k * ld;
+        // graph branch: iteration k's tridiagonal step beside v_{k+1} and its product M v_{k+1}, which
+        // the body of iteration k + 1 then finds in w (discarded if iteration k stopped)
+        cudaStream_t side = k == 0 ? gr->side0 : gr->side;
+        const bool branch = speculate && gr->side0 != nullptr && gr->side != nullptr;
         rc = RPB_OK;
-        if (!(k == 0 && first_done)) rc = lanczos_product(ctx, N, pos, vk, w);
+        if (!(k == 0 && first_done) && !(branch && k >= 1)) rc = lanczos_product(ctx, N, pos, vk, w);
         if (!rc) {
             const int nv = k + 1;
             dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
             project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c1, nullptr);
             dots_kernel<<<dim3(G, nv), kBlasThreads, 0, st>>>(V, ld, n, w, red);
             project_out_kernel<<<G, kBlasThreads, 0, st>>>(V, ld, n, nv, red, G, w, lz + L.c2, red_norm);
+            count_launches(4);
             const bool has_next = k + 1 < max_iter;
-            lanczos_tail_kernel<<<1, 32, 0, st>>>(lz, L, k, tol, red_norm, G, has_next ? gr->hnd[k + 1] : 0ull,
-                                                  has_next ? 1 : 0, gr->state->iter_runs + k, &gr->state->m);
-            count_launches(5);
-            if (has_next) {  // v_{k+1} (unused when this iteration stopped)
-                scale_norm_kernel<<<G, kBlasThreads, 0, st>>>(w, n, red_norm, G, V + (size_t)(k + 1) * ld);
+            cudaStream_t tail_st = st;
+            if (branch && has_next &&
+                !(rc = cuda_fail(cudaEventRecord(gr->ev_fork, st), "event record")) &&
+                !(rc = cuda_fail(cudaStreamWaitEvent(side, gr->ev_fork, 0), "stream wait")))
+                tail_st = side;
+            if (!rc) {
+                lanczos_tail_kernel<<<1, 32, 0, tail_st>>>(lz, L, k, tol, red_norm, G,
+                                                           has_next ? gr->hnd[k + 1] : 0ull, has_next ? 1 : 0,
+                                                           gr->state->iter_runs + k, &gr->state->m);
                 count_launches(1);
             }
-            rc = cuda_fail(cudaGetLastError(), "lanczos kernels");
+            if (!rc && has_next) {  // v_{k+1} (unused when this iteration stopped)
+                scale_norm_kernel<<<G, kBlasThreads, 0, st>>>(w, n, red_norm, G, V + (size_t)(k + 1) * ld);
+                count_launches(1);
+                if (tail_st != st) {
+                    rc = lanczos_product(ctx, N, pos, V + (size_t)(k + 1) * ld, w);
+                    const int jrc = cuda_fail(cudaEventRecord(gr->ev_join, side), "event record");
+                    const int wrc = jrc ? jrc : cuda_fail(cudaStreamWaitEvent(st, gr->ev_join, 0), "stream wait");
+                    if (!rc) rc = wrc;
+                }
+            }
+            if (!rc) rc = cuda_fail(cudaGetLastError(), "lanczos kernels");
         }
         if (cond) {
             gr->iter_launches[k] = (int)(rpb_launch_count() - before);

@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_red
     const double k = si * scale;
     if (q == 0) {
         double ux = s[0][l], uy = s[1][l], uz = s[2][l];
-        if (!self_term)
+        if (!BATCH && !self_term)
             ;
         else if (T)
             self_velocity<true>(zc, si * F[i], si * F[N + i], si * F[2 * N + i], si * T[i], si * T[N + i], c, ux, uy,
@@ -733,7 +733,8 @@ __global__ void __launch_bounds__(BATCH ? 384 : 768, BATCH ? 5 : 2) pair_sym_red
         U[2 * N + i] = k * uz;
     } else if (NC == 6) {
         double ux = s[3 % NC][l], uy = s[4 % NC][l], uz = s[5 % NC][l];
-        if (self_term) self_velocity<false>(zc, si * P[i], si * P[N + i], si * P[2 * N + i], 0.0, 0.0, c, ux, uy, uz);
+        if (BATCH || self_term)
+            self_velocity<false>(zc, si * P[i], si * P[N + i], si * P[2 * N + i], 0.0, 0.0, c, ux, uy, uz);
         U2[i] = k * ux;
         U2[N + i] = k * uy;
         U2[2 * N + i] = k * uz;

@@ -186,7 +186,7 @@ struct RunState {
     unsigned int step;
     int first;
     int m;
-    int pad;
+    int left;  // steps left in the run
     unsigned long long unconv;
     unsigned long long iter_runs[kRunMaxIter];
 };
@@ -198,6 +198,12 @@ struct RunCtx;  // run.cu
 struct LzGraph {
     cudaStream_t body = nullptr;
     RunState *state = nullptr;
+    // a second branch inside an iteration: the tridiagonal step beside the next iteration's product
+    // (short products only; null: no branch).  A stream joined into a capture stays in it until the
+    // capture ends, so the first iteration (captured with the step) and the conditional bodies (each
+    // a capture of its own) fork onto different streams: side0 and side.
+    cudaStream_t side0 = nullptr, side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphConditionalHandle hnd[kRunMaxIter] = {};
     int iter_launches[kRunMaxIter] = {};  // kernels captured into iteration k's body
 };
@@ -288,6 +294,22 @@ int philox_impl(rpb_ctx *ctx, int64_t N, uint64_t seed, uint32_t step, uint32_t 
 // Open a conditional (IF) node after the work captured so far on `st` and start capturing its body on
 // `body`; the node runs its body when `h` was set non-zero during this launch of the graph.
 int graph_begin_if(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle h);
+int graph_begin_cond(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle h,
+                     cudaGraphConditionalNodeType type);
+// Adds a WHILE node (its handle created with the default value 1) after the capture dependencies of
+// st and begins capturing its body on `body`; the body ends with graph_loop_tail_kernel.
+int graph_begin_loop(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle *h);
+// The conditions of a set of conditional nodes, all set to 0 by graph_reset_conds_kernel: a condition
+// keeps its value from one pass of a loop body to the next (the default is applied only when the
+// graph is launched), so a body that decides its conditional nodes as it goes clears them first.
+struct CondSet {
+    cudaGraphConditionalHandle h[kRunMaxIter];
+};
+__global__ void graph_reset_conds_kernel(CondSet s, int n);
+// *left = n (before the loop's graph is launched)
+__global__ void graph_loop_init_kernel(int *left, int n);
+// End of one pass of a loop body: --*left, and the loop runs again while *left > 0.
+__global__ void graph_loop_tail_kernel(int *left, cudaGraphConditionalHandle h);
 // Host-side preparation a product at this N needs (the symmetric pass's schedule), done before a
 // stream capture so that the captured products find it in place.
 int pair_prepare(rpb_ctx *ctx, int64_t N);

@@ -1,11 +1,13 @@
 // run.cu -- many time steps of one suspension replayed from a CUDA graph (rpb_run).
 //
 // A step (forces, noise, the fused product, Lanczos M^{1/2} W of Sec. II.C, the RFD drift of
-// Sec. II.A and the update of Eq. AB) is captured once into a graph on a stream the context owns and
-// replayed nsteps times with no host synchronisation in between.  Each Lanczos iteration after the
-// first is a conditional (IF) node whose condition the previous iteration sets on the device from the
-// stopping test, so a replay runs exactly the iterations a host-driven step runs; the step index that
-// keys the noise and the first-step flag live on the device and advance at the end of each replay.
+// Sec. II.A and the update of Eq. AB) is captured once as the body of a WHILE node of a graph on a
+// stream the context owns, and the graph is launched once: the body runs nsteps times with no host
+// synchronisation in between, the last kernel of a step counting the steps down.  Each Lanczos
+// iteration after the first is a conditional (IF) node inside that body whose condition the previous
+// iteration sets on the device from the stopping test, so a replay runs exactly the iterations a
+// host-driven step runs; the step index that keys the noise and the first-step flag live on the device
+// and advance at the end of each step.
 // The kernels, their arguments and their order are those of rpb_step, so the results are the same
 // bit for bit.
 #include <new>
@@ -19,14 +21,52 @@ static_assert(kRunMaxIter == kMaxIter, "run state sized for the Lanczos dimensio
 
 struct RunCtx {
     cudaStream_t st = nullptr;    // capture and replay
-    cudaStream_t body = nullptr;  // conditional bodies are captured here
+    cudaStream_t loop = nullptr;  // the body of the loop over the steps is captured here
+    cudaStream_t body = nullptr;  // the Lanczos iterations' conditional bodies are captured here
+    cudaStream_t side0 = nullptr, side = nullptr;  // a second branch inside a Lanczos iteration (the tridiagonal
+                                                   // step): in the first iteration, in the conditional ones
     cudaEvent_t ev = nullptr;     // orders the run after the context's stream and back
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // fork and join of that branch in the capture
     RunState *state = nullptr;    // device
     RunState *h_state = nullptr;  // pinned host copy
     double *h_status = nullptr;   // pinned host copy of the Lanczos status words
 };
 
 int graph_begin_if(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle h)
+{
+    return graph_begin_cond(st, body, h, cudaGraphCondTypeIf);
+}
+
+__global__ void graph_reset_conds_kernel(CondSet s, int n)
+{
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cudaGraphSetConditional(s.h[k], 0u);
+}
+
+__global__ void graph_loop_init_kernel(int *left, int n)
+{
+    *left = n;
+}
+
+__global__ void graph_loop_tail_kernel(int *left, cudaGraphConditionalHandle h)
+{
+    const int l = *left - 1;
+    *left = l;
+    cudaGraphSetConditional(h, l > 0 ? 1u : 0u);
+}
+
+int graph_begin_loop(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle *h)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    int rc;
+    if ((rc = cuda_fail(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr), "capture info")) ||
+        (rc = cuda_fail(cudaGraphConditionalHandleCreate(h, g, 1u, cudaGraphCondAssignDefault), "loop handle")))
+        return rc;
+    return graph_begin_cond(st, body, *h, cudaGraphCondTypeWhile);
+}
+
+int graph_begin_cond(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle h,
+                     cudaGraphConditionalNodeType type)
 {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
@@ -39,7 +79,7 @@ int graph_begin_if(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandl
     cudaGraphNodeParams p = {};
     p.type = cudaGraphNodeTypeConditional;
     p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.type = type;
     p.conditional.size = 1;
     cudaGraphNode_t node = nullptr;
     if ((rc = cuda_fail(cudaGraphAddNode(&node, g, deps, edges, nd, &p), "conditional node")) ||
@@ -56,9 +96,10 @@ void run_free(rpb_ctx *ctx)
 {
     RunCtx *r = ctx->run;
     if (!r) return;
-    if (r->st) cudaStreamDestroy(r->st);
-    if (r->body) cudaStreamDestroy(r->body);
-    if (r->ev) cudaEventDestroy(r->ev);
+    for (cudaStream_t q : {r->st, r->loop, r->body, r->side0, r->side})
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : {r->ev, r->ev_fork, r->ev_join})
+        if (e) cudaEventDestroy(e);
     if (r->state) cudaFree(r->state);
     if (r->h_state) cudaFreeHost(r->h_state);
     if (r->h_status) cudaFreeHost(r->h_status);
@@ -78,8 +119,13 @@ static int run_setup(rpb_ctx *ctx)
     ctx->run = r;
     int rc;
     if ((rc = cuda_fail(cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking), "run stream")) ||
+        (rc = cuda_fail(cudaStreamCreateWithFlags(&r->loop, cudaStreamNonBlocking), "run loop stream")) ||
         (rc = cuda_fail(cudaStreamCreateWithFlags(&r->body, cudaStreamNonBlocking), "run body stream")) ||
-        (rc = cuda_fail(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming), "run event"))) {
+        (rc = cuda_fail(cudaStreamCreateWithFlags(&r->side0, cudaStreamNonBlocking), "run side stream")) ||
+        (rc = cuda_fail(cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking), "run side stream")) ||
+        (rc = cuda_fail(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming), "run event")) ||
+        (rc = cuda_fail(cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming), "run event")) ||
+        (rc = cuda_fail(cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming), "run event"))) {
         run_free(ctx);
         return rc;
     }
@@ -94,22 +140,28 @@ static int run_setup(rpb_ctx *ctx)
     return RPB_OK;
 }
 
-__global__ void run_init_kernel(RunState *s, unsigned int step)
+__global__ void run_init_kernel(RunState *s, unsigned int step, int nsteps)
 {
     s->step = step;
     s->first = step == 0u ? 1 : 0;
     s->m = 0;
+    s->left = nsteps;
     s->unconv = 0ull;
     for (int k = 0; k < kRunMaxIter; ++k) s->iter_runs[k] = 0ull;
 }
 
-// End of a replayed step: the next step's index, no longer a first step, and whether this step's
-// Lanczos stopped short of the tolerance (lanczos: the step ran the iteration; tol > 0).
-__global__ void run_advance_kernel(RunState *s, const double *__restrict__ status, int lanczos, double tol)
+// End of a replayed step: the next step's index, no longer a first step, whether this step's Lanczos
+// stopped short of the tolerance (lanczos: the step ran the iteration; tol > 0), and the loop over the
+// steps runs again while steps are left.
+__global__ void run_advance_kernel(RunState *s, const double *__restrict__ status, int lanczos, double tol,
+                                   cudaGraphConditionalHandle loop)
 {
     s->step += 1u;
     s->first = 0;
     if (lanczos && tol > 0.0 && status[ST_STOP] == 0.0) s->unconv += 1ull;
+    const int l = s->left - 1;
+    s->left = l;
+    cudaGraphSetConditional(loop, l > 0 ? 1u : 0u);
 }
 
 }  // namespace rpb
@@ -141,28 +193,38 @@ extern "C" int rpb_run(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int
     if ((rc = pair_prepare(ctx, N)) || (rc = cuda_fail(cudaEventRecord(r->ev, user), "event record")) ||
         (rc = cuda_fail(cudaStreamWaitEvent(r->st, r->ev, 0), "stream wait")))
         return rc;
-    run_init_kernel<<<1, 1, 0, r->st>>>(r->state, (unsigned int)step);
+    run_init_kernel<<<1, 1, 0, r->st>>>(r->state, (unsigned int)step, nsteps);
     count_launches(1);
     LzGraph gr;
     gr.body = r->body;
     gr.state = r->state;
+    gr.side0 = r->side0;
+    gr.side = r->side;
+    gr.ev_fork = r->ev_fork;
+    gr.ev_join = r->ev_join;
     const LzLayout L(ctx->max_iter);
     const double *status = ctx->ws.lz + L.status;
     const bool lanczos = ctx->p.kT > 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const uint64_t before = rpb_launch_count();
-    ctx->stream = r->st;
-    if ((rc = cuda_fail(cudaStreamBeginCapture(r->st, cudaStreamCaptureModeThreadLocal), "begin capture"))) {
-        ctx->stream = user;
-        return rc;
-    }
-    int brc = step_impl(ctx, N, pos, U_prev, (uint32_t)step, seed, dt, delta, tol, max_iter, fp, scheme, rfd, nullptr,
-                        &gr);
+    // the graph: one WHILE node whose body is a step (run_advance_kernel counts the steps down), so
+    // all nsteps run from one graph launch
+    if ((rc = cuda_fail(cudaStreamBeginCapture(r->st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return rc;
+    cudaGraphConditionalHandle loop_h = 0;
+    int brc = graph_begin_loop(r->st, r->loop, &loop_h);
     if (!brc) {
-        run_advance_kernel<<<1, 1, 0, r->st>>>(r->state, status, lanczos ? 1 : 0, tol);
-        count_launches(1);
-        brc = cuda_fail(cudaGetLastError(), "run kernels");
+        ctx->stream = r->loop;
+        brc = step_impl(ctx, N, pos, U_prev, (uint32_t)step, seed, dt, delta, tol, max_iter, fp, scheme, rfd, nullptr,
+                        &gr);
+        if (!brc) {
+            run_advance_kernel<<<1, 1, 0, r->loop>>>(r->state, status, lanczos ? 1 : 0, tol, loop_h);
+            count_launches(1);
+            brc = cuda_fail(cudaGetLastError(), "run kernels");
+        }
+        cudaGraph_t loop_graph = nullptr;  // owned by the WHILE node
+        const cudaError_t el = cudaStreamEndCapture(r->loop, &loop_graph);
+        if (!brc && el != cudaSuccess) brc = cuda_fail(el, "loop body capture end");
     }
     const cudaError_t ec = cudaStreamEndCapture(r->st, &graph);
     ctx->stream = user;
@@ -177,7 +239,7 @@ extern "C" int rpb_run(rpb_ctx *ctx, int64_t N, double *pos, double *U_prev, int
         cudaGraphDestroy(graph);
         return rc;
     }
-    for (int s = 0; s < nsteps && !rc; ++s) rc = cuda_fail(cudaGraphLaunch(exec, r->st), "graph launch");
+    rc = cuda_fail(cudaGraphLaunch(exec, r->st), "graph launch");
     if (!rc &&
         !(rc = cuda_fail(cudaMemcpyAsync(r->h_state, r->state, sizeof(RunState), cudaMemcpyDeviceToHost, r->st),
                          "run state copy")) &&

@@ -86,9 +86,17 @@ def test_part_shares_sum_to_product(gpu_lib, precision, N, torque, periodic, npa
         tol = 1e-10 if precision == "fp64" else 1e-5
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= tol
         assert np.max(np.abs(got - full_h)) / np.max(np.abs(full_h)) <= (1e-12 if precision == "fp64" else 2e-6)
-        if precision == "fp32" and not periodic and N >= 256:  # a symmetric share: pairs, not rows
-            s1 = inputs.from_soa(shares[-1].cpu().numpy(), N)
-            assert np.count_nonzero(np.abs(s1).sum(1)) > N // 2
+        if precision == "fp32" and N >= 256:  # symmetric shares: pairs of their units, both directions
+            nb = -(-N // 128)
+            units = [(b, t) for b in range(nb) for t in range(b, nb)]
+            for p in range(nparts):
+                mine = units[len(units) * p // nparts:len(units) * (p + 1) // nparts]
+                tiles = {b for b, _ in mine} | {t for _, t in mine}
+                want = {i for t in tiles for i in range(128 * t, min(N, 128 * (t + 1)))}
+                sp = inputs.from_soa(shares[p].cpu().numpy(), N)
+                have = set(np.flatnonzero(np.abs(sp).sum(1)).tolist())
+                if p != 0:  # share 0 also holds every sphere's self term
+                    assert have == want, (p, len(have), len(want))
         assert bool((ctx.mobility_apply_part(P, None, None, 0, nparts) == 0).all())
         L = gpu_lib.load()
         out = torch.empty(3 * N, dtype=torch.float64, device="cuda")

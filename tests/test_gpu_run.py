@@ -111,3 +111,16 @@ def test_run_against_oracle_n256(gpu_lib):
         assert np.max(np.abs((got_q - pos0) - (q2 - pos0))) / np.max(np.abs(q2 - pos0)) <= 1e-8
     finally:
         c.close()
+
+
+def test_run_with_falling_lanczos_dimension(gpu_lib):
+    """rpb_run runs all its steps from one graph launch (a loop node around the step), and a conditional
+    node's condition keeps its value from one pass of the loop to the next, so each step clears the
+    Lanczos iterations' conditions first: a step that stops earlier than the one before must not run
+    the later iterations again.  A run whose host-driven Lanczos dimension falls from one step to the
+    next is compared bit for bit."""
+    for seed in range(10):
+        ms = _compare(gpu_lib, 64, "fp64", nsteps=10, seed=seed)
+        if any(b < a for a, b in zip(ms, ms[1:])):
+            return
+    pytest.fail("no run with a falling Lanczos dimension among 10 seeds")
