@@ -91,7 +91,7 @@ def parse():
                     help="monolayer: block-diagonal Lanczos preconditioner (an option; the paper's runs use none)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", choices=["monolayer", "batched", "serving", "lanczos", "accuracy", "small",
-                                           "fingering"],
+                                           "fingering", "shares"],
                     default="monolayer")
     ap.add_argument("--acc-steps", type=int, default=10, help="accuracy: steps compared with the oracle")
     ap.add_argument("--lanczos-iters", type=int, default=12,
@@ -735,6 +735,60 @@ def run_serving(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_shares(args, rank, world, local_rank):
+    """The pair split's work per process, measured on one GPU: the translation-translation product of
+    the N-sphere monolayer cut into W shares of the symmetric pass's triangle (rpb_mobility_apply_part),
+    each share timed alone with CUDA events; the largest share against the whole product gives the
+    speedup W processes would reach on the pairs (the all-reduce of 3N doubles per product, which needs
+    several GPUs, is not in it)."""
+    import torch
+
+    from paper_1612_00474_gb300 import inputs, rpb
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    N = args.N
+    ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=16)
+    q = torch.tensor(inputs.to_soa(inputs.monolayer(N, seed=args.seed)), dtype=torch.float64, device="cuda")
+    F = ctx.philox_normal(N, args.seed, 0, 0)
+    out = torch.empty_like(q)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    clk = clocks_start(local_rank)
+    t_full = timed(lambda: ctx.mobility_apply(q, F, out=out))
+    rows = []
+    for W in (1, 2, 4, 8):
+        ts = [timed(lambda p=p: ctx.mobility_apply_part(q, F, None, p, W, out=out)) for p in range(W)]
+        rows.append({"W": W, "share_ms": [round(t, 4) for t in ts], "max_share_ms": max(ts),
+                     "speedup_on_pairs": t_full / max(ts), "efficiency": t_full / max(ts) / W})
+    clocks = clocks_stop(clk)
+    ctx.close()
+    best = rows[-1]
+    line = _base_line(args, 1, best["speedup_on_pairs"], "x", best["max_share_ms"],
+                      "f32" if args.precision == "fp32" else "f64",
+                      {"workload": f"pair split shares: N={N} monolayer, {args.precision} pairs, translation-"
+                                   f"translation product cut into W = 1, 2, 4, 8 shares, each timed alone on one GPU",
+                       "N": N})
+    line.update({"full_product_ms": t_full, "shares": rows, "clocks": clocks,
+                 "note": "value: the speedup of the pair work at W = 8 (all-reduce not included)"})
+    print(json.dumps(line), flush=True)
+
+
 def run_lanczos_sweep(args, rank, world, local_rank):
     """Lanczos iterations to reach eps <= 1e-3 and <= 1e-5 versus N, with the wall-corrected mobility
     and with the unbounded-domain mobility (Sec. II.C: screening by the wall keeps the iteration count
@@ -1146,6 +1200,8 @@ def main():
         run_small(args, rank, world, local_rank)
     elif args.workload == "fingering":
         run_fingering(args, rank, world, local_rank)
+    elif args.workload == "shares":
+        run_shares(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
