@@ -256,14 +256,22 @@ __global__ void __launch_bounds__(kPairThreads) batch_pair_f64_kernel(
 }
 
 // Forces of Sec. III within each instance (same screening as the single-suspension kernel).
+// Pairs farther apart than 2a + kFarB b, whose repulsion is below e^-kFarB U0/b (~2e-9 U0/b), take it
+// in float32 (IEEE square root and division, expf: a relative error of a few 1e-6 on a term that small
+// is below 1e-14 U0/b) and are summed in float32 before their total joins the float64 sum; nearer
+// pairs are evaluated in float64.  The two kinds are queued apart so that a warp runs the float64 loop
+// only as long as its longest near queue (a float64 warp instruction costs the same whatever the
+// number of active lanes).
+constexpr float kFarB = 20.f;
+
 __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restrict__ pos, const InstDesc *__restrict__ inst,
                                                            const BlockDesc *__restrict__ blocks, int64_t total, double a,
                                                            double weight, double U0, double b, float cut2,
-                                                           double *__restrict__ F)
+                                                           float near2, double *__restrict__ F)
 {
-    // the screen and the near-pair evaluation of forces_kernel, within the block's own instance: the
-    // float32 screen takes two sources per lane (packed), near pairs are queued per thread and
-    // evaluated in float64 together, in index order
+    // the screen of forces_kernel, within the block's own instance: the float32 screen takes two
+    // sources per lane (packed); near pairs are queued from the front of one array, far pairs from its
+    // back, and each kind is evaluated together, in index order
     __shared__ float4 sp[64];
     __shared__ float2 sz[64];
     const BlockDesc bd = blocks[blockIdx.x];
@@ -280,12 +288,14 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
     }
     const float xf = (float)xi, yf = (float)yi, zf = (float)zi;
     const double f0 = U0 / b, inv_b = 1.0 / b;
+    const float f0f = (float)f0, inv_bf = (float)inv_b, two_af = (float)(2.0 * a);
     double fx = 0.0, fy = 0.0, fz = 0.0;
+    float gx = 0.f, gy = 0.f, gz = 0.f;  // far pairs
     constexpr int kQ = 32;
     int queue[kQ];
-    int nq = 0;
+    int nn = 0, nf = 0;  // near pairs at queue[0 .. nn), far pairs at queue[kQ - nf .. kQ)
     auto flush = [&]() {
-        for (int q = 0; q < nq; ++q) {
+        for (int q = 0; q < nn; ++q) {
             const int64_t j = d.off + queue[q];
             const double dx = xi - pos[j], dy = yi - pos[total + j], dz = zi - pos[2 * total + j];
             const double m = steric_pair_factor(dx * dx + dy * dy + dz * dz, 2.0 * a, f0, inv_b);
@@ -293,7 +303,17 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
             fy += m * dy;
             fz += m * dz;
         }
-        nq = 0;
+        for (int q = kQ - nf; q < kQ; ++q) {
+            const int64_t j = d.off + queue[q];
+            const float dx = (float)(xi - pos[j]), dy = (float)(yi - pos[total + j]), dz = (float)(zi - pos[2 * total + j]);
+            const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            const float m = f0f * expf((two_af - r) * inv_bf) / r;
+            gx = fmaf(m, dx, gx);
+            gy = fmaf(m, dy, gy);
+            gz = fmaf(m, dz, gz);
+        }
+        nn = 0;
+        nf = 0;
     };
     float *fxy = reinterpret_cast<float *>(sp);
     float *fz2 = reinterpret_cast<float *>(sz);
@@ -317,12 +337,18 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
             if (d2.x < cut2 || d2.y < cut2) {
                 const int j0 = base + 2 * k;
                 if (d2.x < cut2 && j0 != il && j0 < d.N) {
-                    queue[nq++] = j0;
-                    if (nq == kQ) flush();
+                    if (d2.x < near2)
+                        queue[nn++] = j0;
+                    else
+                        queue[kQ - ++nf] = j0;
+                    if (nn + nf == kQ) flush();
                 }
                 if (d2.y < cut2 && j0 + 1 != il && j0 + 1 < d.N) {
-                    queue[nq++] = j0 + 1;
-                    if (nq == kQ) flush();
+                    if (d2.y < near2)
+                        queue[nn++] = j0 + 1;
+                    else
+                        queue[kQ - ++nf] = j0 + 1;
+                    if (nn + nf == kQ) flush();
                 }
             }
         }
@@ -331,9 +357,9 @@ __global__ void __launch_bounds__(128) batch_forces_kernel(const double *__restr
     flush();
     if (valid) {
         fz += (zi < a ? f0 : f0 * exp(-(zi - a) / b)) - weight;
-        F[i] = fx;
-        F[total + i] = fy;
-        F[2 * total + i] = fz;
+        F[i] = fx + (double)gx;
+        F[total + i] = fy + (double)gy;
+        F[2 * total + i] = fz + (double)gz;
     }
 }
 
@@ -892,8 +918,9 @@ static int batch_step_body(rpb_batch *bt, double dt, double delta, double tol, i
     int rc;
     const double a = bt->p.a;
     const double rcut = (2.0 * a + kForceCutoffB * fp->b) * 1.01 + 0.01 * a;
+    const double rnear = 2.0 * a + (double)kFarB * fp->b;
     batch_forces_kernel<<<bt->nblocks, 128, 0, st>>>(v[V_POS], bt->d_inst, bt->d_blocks, total, a, fp->weight, fp->U0,
-                                                     fp->b, (float)(rcut * rcut), v[V_F]);
+                                                     fp->b, (float)(rcut * rcut), (float)(rnear * rnear), v[V_F]);
     batch_fill3_kernel<<<ge, 256, 0, st>>>(v[V_T], total, fp->torque[0], fp->torque[1], fp->torque[2]);
     count_launches(2);
     if ((rc = batch_product(bt, v[V_POS], v[V_F], v[V_T], v[V_UN], nullptr))) return rc;
