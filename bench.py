@@ -100,6 +100,9 @@ def parse():
     ap.add_argument("--hg", type=float, default=1.5, help="fingering: gravitational height h_g / a")
     ap.add_argument("--fing-steps", type=int, default=2500, help="fingering: steps of each run (0.016 s each)")
     ap.add_argument("--sample-every", type=int, default=10, help="fingering: steps between front spectra")
+    ap.add_argument("--realizations", type=int, default=1,
+                    help="fingering: independent realizations (initial state and noise seeds seed, seed + 1, ...); "
+                         "t* and t1/2 come from their mean band power")
     ap.add_argument("--requests", type=int, default=500, help="serving: number of requests")
     ap.add_argument("--serial-sample-s", type=float, default=60.0,
                     help="serving: seconds of real serial FP64 service measured on a sample of the requests")
@@ -1100,9 +1103,22 @@ def front_band_power(p, frac=0.7):
     return float(np.sum(np.abs(nk) ** 2))
 
 
+def _half_time(times, power):
+    """First time the series reaches half its maximum (linear interpolation between samples): a
+    companion of t* that does not depend on the noisy top of a plateau."""
+    k = int(np.argmax(power))
+    half = 0.5 * power[k]
+    jh = next(j for j, v in enumerate(power) if v >= half)
+    if jh == 0:
+        return times[0]
+    return times[jh - 1] + (half - power[jh - 1]) / (power[jh] - power[jh - 1]) * (times[jh] - times[jh - 1])
+
+
 def run_fingering(args, rank, world, local_rank):
     """Roller fingering run: the same N = 32768 strip advanced deterministically (kT = 0) and with
-    Brownian motion, the front's band power sampled along the way; t* is the time of its maximum."""
+    Brownian motion, the front's band power sampled along the way; t* is the time of its maximum.
+    With several realizations (the paper averages four), each starts from its own initial state and
+    noise, and t* and t1/2 are taken on the mean band power."""
     import torch
 
     from paper_1612_00474_gb300 import inputs, rpb
@@ -1114,48 +1130,60 @@ def run_fingering(args, rank, world, local_rank):
     N, hg, U0, b = args.N, args.hg, 4.0, 0.1
     weight = 1.0 / (hg - 1.0)
     torque = (0.0, units["torque"], 0.0)
-    pos0 = fingering_initial(N, hg, U0, b, args.seed)
+    R = max(1, args.realizations)
     runs = {}
     clk = clocks_start(local_rank)
+    h_edges = np.linspace(0.0, 12.0, 49)
+    x_edges = np.arange(-100.0, 1501.0, 20.0)
+
+    def sample(p):
+        return (front_band_power(p), np.histogram(p[:, 2], h_edges)[0], np.histogram(p[:, 0], x_edges)[0],
+                float(p[:, 2].mean()), float(np.mean(np.sort(p[:, 0])[int(0.3 * N):])))
+
     for name, kT in (("deterministic", 0.0), ("stochastic", 1.0)):
         ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=64, kT=kT)
-        q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
-        U = torch.zeros_like(q)
-        h_edges = np.linspace(0.0, 12.0, 49)
-        x_edges = np.arange(-100.0, 1501.0, 20.0)
-
-        def sample(p):
-            return (front_band_power(p), np.histogram(p[:, 2], h_edges)[0], np.histogram(p[:, 0], x_edges)[0],
-                    float(p[:, 2].mean()), float(np.mean(np.sort(p[:, 0])[int(0.3 * N):])))
-
-        times, samples, ms = [0.0], [sample(pos0)], []
-        t0 = time.perf_counter()
-        for step in range(args.fing_steps):
-            st = ctx.ab_step(q, U, step, args.seed, dt=units["dt"], delta=args.delta, tol=args.tol, max_iter=64,
-                             weight=weight, U0=U0, b=b, torque=torque)
-            ms.append(st["m"])
-            if (step + 1) % args.sample_every == 0:
-                times.append((step + 1) * FING_DT_S)
-                samples.append(sample(inputs.from_soa(q.cpu().numpy(), N)))
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+        per, ms, wall = [], [], 0.0
+        times = [0.0]
+        for r in range(R):
+            seed = args.seed + r
+            pos0 = fingering_initial(N, hg, U0, b, seed)
+            q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
+            U = torch.zeros_like(q)
+            samples = [sample(pos0)]
+            ts = [0.0]
+            t0 = time.perf_counter()
+            for step in range(args.fing_steps):
+                st = ctx.ab_step(q, U, step, seed, dt=units["dt"], delta=args.delta, tol=args.tol, max_iter=64,
+                                 weight=weight, U0=U0, b=b, torque=torque)
+                ms.append(st["m"])
+                if (step + 1) % args.sample_every == 0:
+                    ts.append((step + 1) * FING_DT_S)
+                    samples.append(sample(inputs.from_soa(q.cpu().numpy(), N)))
+            torch.cuda.synchronize()
+            wall += time.perf_counter() - t0
+            times = ts
+            per.append(samples)
         ctx.close()
-        power = [s_[0] for s_ in samples]
+        power = np.mean([[s_[0] for s_ in smp] for smp in per], axis=0).tolist()
         k = int(np.argmax(power))
-        # first time the band power reaches half its maximum (linear interpolation between samples):
-        # a companion of t* that does not depend on the noisy top of a plateau
-        half = 0.5 * power[k]
-        jh = next(j for j, v in enumerate(power) if v >= half)
-        t_half = times[jh] if jh == 0 else times[jh - 1] + (half - power[jh - 1]) / (power[jh] - power[jh - 1]) * (
-            times[jh] - times[jh - 1])
         every = max(1, len(times) // 80)
-        runs[name] = {"t_star_s": times[k], "t_star_at_end_of_run": k == len(power) - 1, "t_half_s": t_half,
-                      "steps_per_s": args.fing_steps / wall, "lanczos_m_mean": float(np.mean(ms)),
-                      "P_h_at_t_star": {"edges_a": h_edges.tolist(), "counts": samples[k][1].tolist()},
-                      "rho_x_at_t_star": {"edges_a": x_edges.tolist(), "counts": samples[k][2].tolist()},
-                      "P_h_initial": samples[0][1].tolist(),
-                      "series": [{"t_s": round(t, 3), "band_power": round(s_[0], 1), "mean_h": round(s_[3], 3),
-                                  "front_x": round(s_[4], 2)} for t, s_ in zip(times, samples)][::every]}
+        mean_h = np.mean([[s_[3] for s_ in smp] for smp in per], axis=0)
+        front = np.mean([[s_[4] for s_ in smp] for smp in per], axis=0)
+        Ph = np.sum([smp[k][1] for smp in per], axis=0)
+        rx = np.sum([smp[k][2] for smp in per], axis=0)
+        runs[name] = {"t_star_s": times[k], "t_star_at_end_of_run": k == len(power) - 1,
+                      "t_half_s": _half_time(times, power),
+                      "per_realization": [{"seed": args.seed + r,
+                                           "t_star_s": times[int(np.argmax([s_[0] for s_ in smp]))],
+                                           "t_half_s": _half_time(times, [s_[0] for s_ in smp])}
+                                          for r, smp in enumerate(per)],
+                      "steps_per_s": R * args.fing_steps / wall, "lanczos_m_mean": float(np.mean(ms)),
+                      "P_h_at_t_star": {"edges_a": h_edges.tolist(), "counts": Ph.tolist()},
+                      "rho_x_at_t_star": {"edges_a": x_edges.tolist(), "counts": rx.tolist()},
+                      "P_h_initial": np.sum([smp[0][1] for smp in per], axis=0).tolist(),
+                      "series": [{"t_s": round(t, 3), "band_power": round(pw, 1), "mean_h": round(float(h), 3),
+                                  "front_x": round(float(fx), 2)}
+                                 for t, pw, h, fx in zip(times, power, mean_h, front)][::every]}
     clocks = clocks_stop(clk)
     paper = FING_T_STAR_PAPER.get(round(hg, 1))
     det, sto = runs["deterministic"]["t_star_s"], runs["stochastic"]["t_star_s"]
@@ -1163,7 +1191,8 @@ def run_fingering(args, rank, world, local_rank):
                       "f32" if args.precision == "fp32" else "f64",
                       {"workload": f"roller fingering: N={N} strip 60a x 4915a, h_g={hg}a, U0=4kT, b=0.1a, "
                                    f"torque 8 pi eta a^3 omega (omega=62.8 rad/s), dt=0.016 s, "
-                                   f"{args.fing_steps} steps per run, {args.precision} pairs", "N": N})
+                                   f"{args.fing_steps} steps per run, {R} realization(s), {args.precision} pairs",
+                       "N": N, "realizations": R})
     hd, hs = runs["deterministic"]["t_half_s"], runs["stochastic"]["t_half_s"]
     line.update({"fingering": {"t_star_s": {"deterministic": det, "stochastic": sto},
                                "ratio_stochastic_over_deterministic": sto / det if det > 0 else None,
