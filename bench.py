@@ -55,10 +55,10 @@ FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25  # dense FP64 rate of a GB300 (vector pipe), for context
 # DRAM bytes (read + write) of one launch of the symmetric translation-translation kernel at
 # N = 65536, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the
-# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command): 4.92 MB read (the
-# packed sources), 165.19 MB written (segment and source-column partials leaving L2).  Valid for this
-# kernel build only: reset to {} when the kernel changes.
-SYM_TT_TRAFFIC_BYTES = {65536: 4.916e6 + 165.190e6}
+# default workload (profiles/pair_f32x2_sym_kernel_n32768.md gives the command), mean of two launches:
+# 3.71 MB read (the packed sources), 165.20 MB written (segment and source-column partials leaving
+# L2).  Valid for this kernel build only: reset to {} when the kernel changes.
+SYM_TT_TRAFFIC_BYTES = {65536: 3.711e6 + 165.199e6}
 SM_MAX_MHZ = 2070.0
 
 
