@@ -42,6 +42,9 @@ extern "C" {
 #define RPB_ENOMEM 2    /* device allocation failed in rpb_create */
 #define RPB_ECUDA 3     /* a CUDA runtime call or kernel launch failed (message has the CUDA error) */
 #define RPB_ENOCONV 4   /* Lanczos reached max_iter with eps > tol: results are still written */
+#define RPB_ETIMEOUT 5  /* a bounded device-side wait expired.  Reserved: no kernel of this library waits
+                           on another (the Lanczos stop and the step loop are graph conditions, the
+                           stages plain stream order), so no call returns it */
 
 #define RPB_FP64 0      /* pair arithmetic in float64 */
 #define RPB_FP32 1      /* pair arithmetic in float32 (hi/lo split positions, compensated tile sums,

@@ -14,7 +14,7 @@ import os
 
 from . import build as _build
 
-RPB_OK, RPB_EINVAL, RPB_ENOMEM, RPB_ECUDA, RPB_ENOCONV = 0, 1, 2, 3, 4
+RPB_OK, RPB_EINVAL, RPB_ENOMEM, RPB_ECUDA, RPB_ENOCONV, RPB_ETIMEOUT = 0, 1, 2, 3, 4, 5
 RPB_FP64, RPB_FP32 = 0, 1
 PRECISIONS = {"fp64": RPB_FP64, "fp32": RPB_FP32}
 

@@ -44,3 +44,11 @@ def test_monolayer_generator_properties():
     assert np.array_equal(p, inputs.monolayer(500, seed=1))
     sizes = inputs.batch_sizes(512)
     assert sizes.min() >= 64 and sizes.max() <= 2048
+
+
+def test_error_codes_match_header():
+    src = open(os.path.join(ROOT, "include", "rpb.h")).read()
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (RPB_(?:OK|E[A-Z]+)) (\d+)", src)}
+    assert set(codes) == {"RPB_OK", "RPB_EINVAL", "RPB_ENOMEM", "RPB_ECUDA", "RPB_ENOCONV", "RPB_ETIMEOUT"}
+    for name, value in codes.items():
+        assert getattr(rpb, name) == value, name
