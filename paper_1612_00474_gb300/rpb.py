@@ -375,8 +375,8 @@ class Context:
 
     def run(self, pos, U_prev, step, seed, nsteps, scheme="AB", rfd="centred", dt=0.01, delta=1e-6, tol=1e-3,
             max_iter=None, weight=1.0, U0=1.0, b=0.1, torque=(0.0, 1.0, 0.0), raise_on_noconv=True):
-        """nsteps time steps in place, replayed from a CUDA graph with the Lanczos stop decided on the
-        device (rpb_run); the same results as nsteps calls of step().  Returns (last step's statistics,
+        """nsteps time steps in place from one launch of a CUDA graph (a loop node around the step) with
+        the Lanczos stop decided on the device (rpb_run); the same results as nsteps calls of step().  Returns (last step's statistics,
         number of steps whose Lanczos did not converge)."""
         n = pos.numel()
         fp = _force_params(weight, U0, b, torque)
