@@ -100,6 +100,10 @@ def parse():
     ap.add_argument("--hg", type=float, default=1.5, help="fingering: gravitational height h_g / a")
     ap.add_argument("--fing-steps", type=int, default=2500, help="fingering: steps of each run (0.016 s each)")
     ap.add_argument("--sample-every", type=int, default=10, help="fingering: steps between front spectra")
+    ap.add_argument("--equilibrate-s", type=float, default=0.0,
+                    help="fingering: seconds of Brownian dynamics without torque in the 60a x 4915a cell with "
+                         "pseudo-periodic boundaries before each realization (an equilibrium sample of the "
+                         "two-periodic suspension, as the paper's initial states); 0: sequential addition only")
     ap.add_argument("--realizations", type=int, default=1,
                     help="fingering: independent realizations (initial state and noise seeds seed, seed + 1, ...); "
                          "t* and t1/2 come from their mean band power")
@@ -1140,13 +1144,36 @@ def run_fingering(args, rank, world, local_rank):
         return (front_band_power(p), np.histogram(p[:, 2], h_edges)[0], np.histogram(p[:, 0], x_edges)[0],
                 float(p[:, 2].mean()), float(np.mean(np.sort(p[:, 0])[int(0.3 * N):])))
 
+    # initial states: sequential addition, then (optionally) Brownian dynamics without torque in the
+    # pseudo-periodic cell, folded back into it -- a sample of the two-periodic suspension's equilibrium
+    inits, eq_info = [], []
+    neq = int(round(args.equilibrate_s / FING_DT_S))
+    ctx_eq = None
+    if neq > 0:
+        ctx_eq = rpb.Context(max_N=N, precision=args.precision, max_iter=64, kT=1.0)
+        ctx_eq.set_periodic(FING_LX, FING_LY)
+    for r in range(R):
+        p0 = fingering_initial(N, hg, U0, b, args.seed + r)
+        if ctx_eq is not None:
+            q = torch.tensor(inputs.to_soa(p0), dtype=torch.float64, device="cuda")
+            U = torch.zeros_like(q)
+            ctx_eq.run(q, U, 0, args.seed + 1000 + r, neq, dt=units["dt"], delta=args.delta, tol=args.tol,
+                       max_iter=64, weight=weight, U0=U0, b=b, torque=(0.0, 0.0, 0.0))
+            p1 = inputs.from_soa(q.cpu().numpy(), N)
+            p1[:, 0] = np.mod(p1[:, 0], FING_LX)
+            p1[:, 1] = np.mod(p1[:, 1], FING_LY)
+            eq_info.append({"mean_h_before": float(p0[:, 2].mean()), "mean_h_after": float(p1[:, 2].mean())})
+            p0 = p1
+        inits.append(p0)
+    if ctx_eq is not None:
+        ctx_eq.close()
     for name, kT in (("deterministic", 0.0), ("stochastic", 1.0)):
         ctx = rpb.Context(max_N=N, precision=args.precision, max_iter=64, kT=kT)
         per, ms, wall = [], [], 0.0
         times = [0.0]
         for r in range(R):
             seed = args.seed + r
-            pos0 = fingering_initial(N, hg, U0, b, seed)
+            pos0 = inits[r]
             q = torch.tensor(inputs.to_soa(pos0), dtype=torch.float64, device="cuda")
             U = torch.zeros_like(q)
             samples = [sample(pos0)]
@@ -1191,8 +1218,11 @@ def run_fingering(args, rank, world, local_rank):
                       "f32" if args.precision == "fp32" else "f64",
                       {"workload": f"roller fingering: N={N} strip 60a x 4915a, h_g={hg}a, U0=4kT, b=0.1a, "
                                    f"torque 8 pi eta a^3 omega (omega=62.8 rad/s), dt=0.016 s, "
-                                   f"{args.fing_steps} steps per run, {R} realization(s), {args.precision} pairs",
-                       "N": N, "realizations": R})
+                                   f"{args.fing_steps} steps per run, {R} realization(s), {args.precision} pairs, "
+                                   f"initial states: sequential addition"
+                                   + (f" then {args.equilibrate_s:g} s of torque-free Brownian dynamics in the "
+                                      f"pseudo-periodic cell" if neq > 0 else ""),
+                       "N": N, "realizations": R, "equilibrate_s": args.equilibrate_s})
     hd, hs = runs["deterministic"]["t_half_s"], runs["stochastic"]["t_half_s"]
     line.update({"fingering": {"t_star_s": {"deterministic": det, "stochastic": sto},
                                "ratio_stochastic_over_deterministic": sto / det if det > 0 else None,
@@ -1200,7 +1230,7 @@ def run_fingering(args, rank, world, local_rank):
                                "t_half_ratio": hs / hd if hd > 0 else None,
                                "paper_t_star_s": ({"deterministic": paper[0], "stochastic": paper[1],
                                                    "ratio": paper[1] / paper[0]} if paper else None),
-                               "reduced_units": units, "runs": runs},
+                               "reduced_units": units, "equilibration": eq_info, "runs": runs},
                  "clocks": clocks})
     print(json.dumps(line), flush=True)
 
