@@ -10,6 +10,7 @@ increment split into the parts the tolerances of the method's readings apply to.
     the Brownian increment g at 1e-10, the drift at its a/delta-amplified bound (reported), and the
     increment without the drift (dt (3/2 U^n - 1/2 U^{n-1}) + sqrt(2 kT dt) g) at 1e-10.
   - The FP32 path's drift (delta = 5e-3 a) against the FP64 oracle's (delta = 1e-6 a), reported.
+  - The pair split at N = 65536: four shares of the symmetric pass's triangle add up to the product.
 """
 import numpy as np
 import pytest
@@ -150,3 +151,27 @@ def test_fp32_drift_against_fp64_oracle_drift(gpu_lib):
           f"change between the two deltas {oracle_l2:.2e} (2-norm)")
     assert err <= 1e-3
     assert fine_l2 <= 0.05
+
+
+def test_pair_shares_n65536(gpu_lib):
+    """The pair split at the benchmark's size: four shares of the symmetric pass's triangle
+    (rpb_mobility_apply_part) add up to the whole product (float32 partial sums in another order:
+    2e-6), and on sampled rows to the FP64 oracle's product (1e-5)."""
+    N, W = 65536, 4
+    pos = inputs.monolayer(N, seed=0)
+    F = inputs.vectors(N, 9)
+    ctx = gpu_lib.Context(max_N=N, precision="fp32", max_iter=16)
+    try:
+        P, Fd = dev(pos), dev(F)
+        full = ctx.mobility_apply(P, Fd)
+        total = torch.zeros_like(full)
+        for p in range(W):
+            total += ctx.mobility_apply_part(P, Fd, None, p, W)
+        torch.cuda.synchronize()
+        full, total = host(full, N), host(total, N)
+    finally:
+        ctx.close()
+    assert maxrel(total, full) <= 2e-6
+    rows = np.concatenate([np.random.default_rng(2).choice(N, 16, replace=False), [0, 128, N - 1]])
+    ref = np.concatenate([O.mobility_apply(pos, F, None, rows=(r, r + 1)) for r in rows])
+    assert maxrel(total[rows], ref) <= 1e-5
