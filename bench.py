@@ -747,7 +747,8 @@ def run_shares(args, rank, world, local_rank):
     the N-sphere monolayer cut into W shares of the symmetric pass's triangle (rpb_mobility_apply_part),
     each share timed alone with CUDA events; the largest share against the whole product gives the
     speedup W processes would reach on the pairs (the all-reduce of 3N doubles per product, which needs
-    several GPUs, is not in it)."""
+    several GPUs, is not in it).  The row split's largest share (rpb_mobility_apply_rows) is timed
+    beside it."""
     import torch
 
     from paper_1612_00474_gb300 import inputs, rpb
@@ -779,10 +780,15 @@ def run_shares(args, rank, world, local_rank):
     clk = clocks_start(local_rank)
     t_full = timed(lambda: ctx.mobility_apply(q, F, out=out))
     rows = []
+    from paper_1612_00474_gb300.split import row_ranges
     for W in (1, 2, 4, 8):
         ts = [timed(lambda p=p: ctx.mobility_apply_part(q, F, None, p, W, out=out)) for p in range(W)]
+        # the row split's largest share for comparison: one-way kernels over its target rows
+        r0, r1 = max(row_ranges(N, W), key=lambda ab: ab[1] - ab[0])
+        t_rows = timed(lambda: ctx.mobility_apply_rows(q, F, None, r0, r1))
         rows.append({"W": W, "share_ms": [round(t, 4) for t in ts], "max_share_ms": max(ts),
-                     "speedup_on_pairs": t_full / max(ts), "efficiency": t_full / max(ts) / W})
+                     "speedup_on_pairs": t_full / max(ts), "efficiency": t_full / max(ts) / W,
+                     "row_split_max_share_ms": t_rows, "row_split_speedup": t_full / t_rows})
     clocks = clocks_stop(clk)
     ctx.close()
     best = rows[-1]
