@@ -100,6 +100,9 @@ def parse():
     ap.add_argument("--hg", type=float, default=1.5, help="fingering: gravitational height h_g / a")
     ap.add_argument("--fing-steps", type=int, default=2500, help="fingering: steps of each run (0.016 s each)")
     ap.add_argument("--sample-every", type=int, default=10, help="fingering: steps between front spectra")
+    ap.add_argument("--fing-dt", type=float, default=0.016,
+                    help="fingering: time step in seconds (the paper's 0.016 s = tau_U / 2; it reports 0.008 s "
+                         "giving essentially the same results)")
     ap.add_argument("--equilibrate-s", type=float, default=0.0,
                     help="fingering: seconds of Brownian dynamics without torque in the 60a x 4915a cell with "
                          "pseudo-periodic boundaries before each realization (an equilibrium sample of the "
@@ -1060,10 +1063,10 @@ FING_KMIN_UM, FING_KMAX_UM = 2.0e-3, 0.26
 FING_T_STAR_PAPER = {1.5: (9.4, 11.8), 3.5: (17.3, 26.9), 6.1: (32.6, 42.9)}  # (deterministic, stochastic) s
 
 
-def fingering_units():
-    """Reduced units a = eta = kT = 1: time unit eta a^3 / kT."""
+def fingering_units(dt_s=FING_DT_S):
+    """Reduced units a = eta = kT = 1: time unit eta a^3 / kT; dt_s: the time step in seconds."""
     tau0 = FING_ETA * FING_A_M ** 3 / FING_KT
-    return dict(tau0=tau0, dt=FING_DT_S / tau0, torque=8.0 * math.pi * FING_OMEGA * tau0)
+    return dict(tau0=tau0, dt=dt_s / tau0, dt_s=dt_s, torque=8.0 * math.pi * FING_OMEGA * tau0)
 
 
 def fingering_initial(N, hg, U0, b, seed):
@@ -1113,6 +1116,20 @@ def front_band_power(p, frac=0.7):
     return float(np.sum(np.abs(nk) ** 2))
 
 
+def front_band_power_cycles(p, frac=0.7, bins=1 << 17):
+    """The same band read in cycles per micrometre (k = 1/lambda, modes n / L_y with L_y in um inside
+    [2e-3, 0.26]: wavelengths down to 5.9a instead of 37a), from an FFT of the front's y positions
+    binned into `bins` bins of the strip's period (the sum over spheres of e^{-2 pi i n y / L_y} is
+    periodic in y, so y is folded into [0, L_y); the binning changes |n(k)| by under 1e-4 here)."""
+    y = p[np.argsort(p[:, 0])[int((1.0 - frac) * len(p)):], 1]
+    L_um = FING_LY * FING_A_M * 1e6
+    n = np.arange(1, bins // 2)
+    sel = n[(n / L_um >= FING_KMIN_UM) & (n / L_um <= FING_KMAX_UM)]
+    idx = np.minimum((np.mod(y, FING_LY) / FING_LY * bins).astype(np.int64), bins - 1)
+    f = np.fft.rfft(np.bincount(idx, minlength=bins).astype(np.float64))
+    return float(np.sum(np.abs(f[sel]) ** 2))
+
+
 def _half_time(times, power):
     """First time the series reaches half its maximum (linear interpolation between samples): a
     companion of t* that does not depend on the noisy top of a plateau."""
@@ -1136,7 +1153,7 @@ def run_fingering(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     if rank != 0:
         return
-    units = fingering_units()
+    units = fingering_units(args.fing_dt)
     N, hg, U0, b = args.N, args.hg, 4.0, 0.1
     weight = 1.0 / (hg - 1.0)
     torque = (0.0, units["torque"], 0.0)
@@ -1148,12 +1165,12 @@ def run_fingering(args, rank, world, local_rank):
 
     def sample(p):
         return (front_band_power(p), np.histogram(p[:, 2], h_edges)[0], np.histogram(p[:, 0], x_edges)[0],
-                float(p[:, 2].mean()), float(np.mean(np.sort(p[:, 0])[int(0.3 * N):])))
+                float(p[:, 2].mean()), float(np.mean(np.sort(p[:, 0])[int(0.3 * N):])), front_band_power_cycles(p))
 
     # initial states: sequential addition, then (optionally) Brownian dynamics without torque in the
     # pseudo-periodic cell, folded back into it -- a sample of the two-periodic suspension's equilibrium
     inits, eq_info = [], []
-    neq = int(round(args.equilibrate_s / FING_DT_S))
+    neq = int(round(args.equilibrate_s / units["dt_s"]))
     ctx_eq = None
     if neq > 0:
         ctx_eq = rpb.Context(max_N=N, precision=args.precision, max_iter=64, kT=1.0)
@@ -1190,7 +1207,7 @@ def run_fingering(args, rank, world, local_rank):
                                  weight=weight, U0=U0, b=b, torque=torque)
                 ms.append(st["m"])
                 if (step + 1) % args.sample_every == 0:
-                    ts.append((step + 1) * FING_DT_S)
+                    ts.append((step + 1) * units["dt_s"])
                     samples.append(sample(inputs.from_soa(q.cpu().numpy(), N)))
             torch.cuda.synchronize()
             wall += time.perf_counter() - t0
@@ -1198,7 +1215,9 @@ def run_fingering(args, rank, world, local_rank):
             per.append(samples)
         ctx.close()
         power = np.mean([[s_[0] for s_ in smp] for smp in per], axis=0).tolist()
+        power_c = np.mean([[s_[5] for s_ in smp] for smp in per], axis=0).tolist()
         k = int(np.argmax(power))
+        kc = int(np.argmax(power_c))
         every = max(1, len(times) // 80)
         mean_h = np.mean([[s_[3] for s_ in smp] for smp in per], axis=0)
         front = np.mean([[s_[4] for s_ in smp] for smp in per], axis=0)
@@ -1206,6 +1225,8 @@ def run_fingering(args, rank, world, local_rank):
         rx = np.sum([smp[k][2] for smp in per], axis=0)
         runs[name] = {"t_star_s": times[k], "t_star_at_end_of_run": k == len(power) - 1,
                       "t_half_s": _half_time(times, power),
+                      "cycles_reading": {"t_star_s": times[kc], "t_star_at_end_of_run": kc == len(power_c) - 1,
+                                         "t_half_s": _half_time(times, power_c)},
                       "per_realization": [{"seed": args.seed + r,
                                            "t_star_s": times[int(np.argmax([s_[0] for s_ in smp]))],
                                            "t_half_s": _half_time(times, [s_[0] for s_ in smp])}
@@ -1214,23 +1235,25 @@ def run_fingering(args, rank, world, local_rank):
                       "P_h_at_t_star": {"edges_a": h_edges.tolist(), "counts": Ph.tolist()},
                       "rho_x_at_t_star": {"edges_a": x_edges.tolist(), "counts": rx.tolist()},
                       "P_h_initial": np.sum([smp[0][1] for smp in per], axis=0).tolist(),
-                      "series": [{"t_s": round(t, 3), "band_power": round(pw, 1), "mean_h": round(float(h), 3),
-                                  "front_x": round(float(fx), 2)}
-                                 for t, pw, h, fx in zip(times, power, mean_h, front)][::every]}
+                      "series": [{"t_s": round(t, 3), "band_power": round(pw, 1), "band_power_cycles": round(pc, 1),
+                                  "mean_h": round(float(h), 3), "front_x": round(float(fx), 2)}
+                                 for t, pw, pc, h, fx in zip(times, power, power_c, mean_h, front)][::every]}
     clocks = clocks_stop(clk)
     paper = FING_T_STAR_PAPER.get(round(hg, 1))
     det, sto = runs["deterministic"]["t_star_s"], runs["stochastic"]["t_star_s"]
     line = _base_line(args, 1, runs["stochastic"]["steps_per_s"], "steps/s", 1e3 / runs["stochastic"]["steps_per_s"],
                       "f32" if args.precision == "fp32" else "f64",
                       {"workload": f"roller fingering: N={N} strip 60a x 4915a, h_g={hg}a, U0=4kT, b=0.1a, "
-                                   f"torque 8 pi eta a^3 omega (omega=62.8 rad/s), dt=0.016 s, "
+                                   f"torque 8 pi eta a^3 omega (omega=62.8 rad/s), dt={units['dt_s']:g} s, "
                                    f"{args.fing_steps} steps per run, {R} realization(s), {args.precision} pairs, "
                                    f"initial states: sequential addition"
                                    + (f" then {args.equilibrate_s:g} s of torque-free Brownian dynamics in the "
                                       f"pseudo-periodic cell" if neq > 0 else ""),
                        "N": N, "realizations": R, "equilibrate_s": args.equilibrate_s})
     hd, hs = runs["deterministic"]["t_half_s"], runs["stochastic"]["t_half_s"]
+    cdet, csto = runs["deterministic"]["cycles_reading"]["t_star_s"], runs["stochastic"]["cycles_reading"]["t_star_s"]
     line.update({"fingering": {"t_star_s": {"deterministic": det, "stochastic": sto},
+                               "t_star_s_cycles_reading": {"deterministic": cdet, "stochastic": csto},
                                "ratio_stochastic_over_deterministic": sto / det if det > 0 else None,
                                "t_half_s": {"deterministic": hd, "stochastic": hs},
                                "t_half_ratio": hs / hd if hd > 0 else None,
