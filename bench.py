@@ -62,7 +62,7 @@ SYM_TT_TRAFFIC_BYTES = {65536: 3.711e6 + 165.199e6}
 SM_MAX_MHZ = 2070.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -117,7 +117,7 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: device-memory budget for resident state")
     ap.add_argument("--max-batch", type=int, default=256, help="serving: requests per batched step")
     ap.add_argument("--max-spheres", type=int, default=262144, help="serving: spheres per batched step")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def cell_side(N, phi=0.4):
@@ -1264,12 +1264,19 @@ def run_fingering(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
+def resolve_defaults(args):
+    """Workload-dependent defaults: the suspension size (65536 for the monolayer, the reference arm and
+    the bound of the Lanczos sweep; 4096 for the accuracy comparison with the oracle; 32768 for the
+    fingering strip) and the RFD length (1e-6 a for float64 products, 5e-3 a for float32, Sec. II.A)."""
     if args.N is None:
         args.N = {"accuracy": 4096, "fingering": 32768}.get(args.workload, 65536)
     if args.delta is None:
         args.delta = 1e-6 if args.precision == "fp64" else 5e-3
+    return args
+
+
+def main():
+    args = resolve_defaults(parse())
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

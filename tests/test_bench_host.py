@@ -42,3 +42,18 @@ def test_half_time_interpolates():
     t = [0.0, 1.0, 2.0, 3.0]
     assert bench._half_time(t, [0.0, 2.0, 6.0, 10.0]) == 1.75  # half of 10 between 2 (t=1) and 6 (t=2)
     assert bench._half_time(t, [8.0, 9.0, 10.0, 7.0]) == 0.0
+
+
+def test_workload_defaults():
+    """Each workload gets its own suspension size unless --N is given (the accuracy comparison runs the
+    FP64 oracle step by step, which at the monolayer's 65536 spheres would take hours), and the RFD
+    length follows the pair precision (Sec. II.A's delta ~ eps^(1/3) a)."""
+    r = bench.resolve_defaults
+    assert r(bench.parse([])).N == 65536
+    assert r(bench.parse(["--workload", "accuracy"])).N == 4096
+    assert r(bench.parse(["--workload", "fingering"])).N == 32768
+    assert r(bench.parse(["--workload", "accuracy", "--N", "1024"])).N == 1024
+    assert r(bench.parse(["--impl", "reference"])).N == 65536
+    assert r(bench.parse([])).delta == 5e-3
+    assert r(bench.parse(["--precision", "fp64"])).delta == 1e-6
+    assert r(bench.parse(["--delta", "1e-4"])).delta == 1e-4
